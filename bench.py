@@ -1,0 +1,363 @@
+#!/usr/bin/env python
+"""Throughput of the Lippmann-Schwinger corrector solve on GB300.
+
+Metric: voxel-CG-iterations per second, sum over solves of N^3 x (CG
+iterations), divided by the device time of the whole job.  One step computes
+the full 6x6 effective stiffness C* of a 128^3 two-phase elastic sphere
+packing (radius 8 voxels, volume fraction 0.3, seed 1411; matrix E=1 nu=0.3,
+inclusions E=10 nu=0.2; reference medium mu0 = mu_min/2, nu0 = 0.3) with the
+FP64 solver, once with the filtered and once with the truncated Green
+operator: 12 CG solves to relative residual 1e-10.
+
+Also reported: an end-to-end number through the C ABI with the phase map in
+pinned host memory (host->device copy and the C* readback inside the timed
+region), the mixed-precision solver on the same workload with its C* error
+against the FP64 result, the roofline of the dominant pass (per-pass CUDA
+events recorded live on the solve stream), the GPU clocks sampled during the
+timed region, and the FP64 CPU oracle timed on a bounded sample.
+
+--impl reference times the CPU oracle alone (the reference arm).
+Multi-GPU (torchrun): every rank solves its own copy of the workload
+(independent replicas, no data-path collective); value = all voxel-iterations
+/ the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "voxel-CG-iterations/s of LS solve, mixed+batched vs FP64 plain at 1e-8 C* error"
+UNIT = "voxel-iterations/s"
+N = 128
+TOL = 1e-10
+
+
+def k_mu(E, nu):
+    return E / (3.0 * (1.0 - 2.0 * nu)), E / (2.0 * (1.0 + nu))
+
+
+def workload():
+    from paper_1411_0330_gb300 import microstructures as ms
+    ph, cen, r = ms.sphere_microstructure(N, 8.0, 0.3, seed=1411)
+    mods = np.array([k_mu(1.0, 0.3), k_mu(10.0, 0.2)])
+    return ph, mods, len(cen)
+
+
+def config(nspheres, frac):
+    return {"workload": f"{N}^3 isotropic elasticity, {nspheres} RSA spheres r=8 vox, f={frac:.4f}, seed 1411, "
+                        f"E 1/10 nu 0.3/0.2, mu0=mu_min/2 nu0=0.3, CG rel.res {TOL:g}, 6 Mandel loads, "
+                        f"filtered + truncated Gamma (12 solves per step)",
+            "grid": [N, N, N], "components": 6, "loads_per_step": 12, "tol": TOL,
+            "l2": "working set 686 MB per handle > 129 MB L2 (no flush needed)"}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- roofline bookkeeping
+def pass_traffic(kind, V, c, nx, nxh, ncoef, b):
+    """Algorithmic bytes of one launch of a pass over the whole field (b = bytes per real)."""
+    cV = c * V
+    half = nxh / nx  # complex half-spectrum elements per real element
+    if kind == "x_forward":      # read x, r, p; write x, p; write the half spectrum
+        return cV * (5 * b + 2 * b * half)
+    if kind in ("y_forward", "y_inverse"):
+        return cV * 4 * b * half
+    if kind == "z_gamma":        # spectrum in and out + the symmetric Gamma table
+        return cV * 4 * b * half + V * ncoef * b * half
+    if kind == "x_inverse_local":  # spectrum, p in; q out; phase byte per element
+        return cV * (2 * b * half + 2 * b + 1)
+    if kind == "cg_update":      # r, q in; r out
+        return cV * 3 * b
+    raise KeyError(kind)
+
+
+def pass_flops(kind, V, c, nx, ny, nz, nxh):
+    """Conventional FFT flop count 5 n log2 n per complex length-n transform, plus the
+    arithmetic of the fused epilogues."""
+    lg = lambda n: np.log2(n) if n > 1 else 0.0
+    if kind == "x_forward":
+        return c * nz * ny / 2 * 5 * nx * lg(nx) + c * V * 4 + c * nz * ny / 2 * nxh * 8
+    if kind in ("y_forward", "y_inverse"):
+        return c * nz * nxh * 5 * ny * lg(ny)
+    if kind == "z_gamma":
+        return 2 * c * ny * nxh * 5 * nz * lg(nz) + ny * nz * nxh * (2 * c * c - 2 * c + 2 * c) * 2
+    if kind == "x_inverse_local":
+        return c * nz * ny / 2 * 5 * nx * lg(nx) + c * V * 6
+    if kind == "cg_update":
+        return c * V * 4
+    raise KeyError(kind)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": d.get("hbm_gbs", 6780.0), "source": "measured", "sm_max_mhz": d.get("sm_max_mhz", 2070.0)}
+    return {"hbm_gbs": 6800.0, "source": "fallback", "sm_max_mhz": 2070.0}
+
+
+# ----------------------------------------------------------------- CPU oracle sample
+def oracle_sample(ph, mods, iters=2):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
+    `iters` CG iterations of one 128^3 solve (filtered Gamma, shear load)."""
+    import oracle
+    oracle.build()
+    P = oracle.Problem(ph, mods, physics=oracle.ELASTIC, green=oracle.FILTERED)
+    load = np.zeros(6)
+    load[5] = 1.0
+    t0 = time.perf_counter()
+    try:
+        oracle.solve(P, load, tol=1e-30, maxit=iters, solver=oracle.SOLVER_CG)
+    except oracle.OracleError as e:
+        if e.code != 5:  # not converged is expected for a bounded sample
+            raise
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": ph.size * iters / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{iters} CG iterations of one {N}^3 filtered solve (shear load), {dt:.1f} s"}
+
+
+# ----------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    ph, mods, nsph = workload()
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        pass
+    vals = []
+    for _ in range(args.steps):
+        vals.append(oracle_sample(ph, mods, iters=1))
+    v = float(np.median([x["value"] for x in vals]))
+    cb = dict(vals[0])
+    cb["value"] = v
+    cb["sample"] = f"1 CG iteration of one {N}^3 filtered solve per step, {args.steps} steps"
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ph.size / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": config(nsph, float(ph.mean())), "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- main arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="lsh", choices=["lsh", "reference"])
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    from paper_1411_0330_gb300 import lsh
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ph, mods, nsph = workload()
+    ph_dev = torch.from_numpy(ph).to(dev)
+    handles = [lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=g) for g in (lsh.FILTERED, lsh.TRUNCATED)]
+    V = ph.size
+
+    def step():
+        its, res = 0, []
+        for h in handles:
+            A, infos = h.effective(tol=TOL)
+            its += sum(i["iters"] for i in infos)
+            res.append((A, infos))
+        return its, res
+
+    for _ in range(args.warmup):
+        step()
+    for h in handles:
+        h.profile_read(reset=True)
+        h.profile_enable(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    total_its = 0
+    last = None
+    for _ in range(args.steps):
+        its, last = step()
+        total_its += its
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    if world > 1:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    profs = [h.profile_read(reset=True) for h in handles]
+    for h in handles:
+        h.profile_enable(False)
+    t = torch.tensor([ms, float(total_its) * V], dtype=torch.float64, device=dev)
+    if world > 1:
+        tmax = t.clone()
+        dist.all_reduce(tmax[:1], op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum[1:], op=dist.ReduceOp.SUM)
+        ms_max, vox_its = float(tmax[0]), float(tsum[1])
+    else:
+        ms_max, vox_its = ms, float(total_its) * V
+    value = vox_its / (ms_max / 1e3)
+    launches = sum(p["launches"] for p in profs)
+
+    # roofline of the dominant pass, from the live per-pass events
+    peaks = load_peaks()
+    nxh = N // 2 + 1
+    tot = {k: sum(p["pass_ms"][k] for p in profs) for k in lsh.PASS_NAMES}
+    cnt = {k: sum(p["pass_launches"][k] for p in profs) for k in lsh.PASS_NAMES}
+    dom = max(tot, key=tot.get)
+    avg_ms = tot[dom] / max(cnt[dom], 1)
+    byts = pass_traffic(dom, V, 6, N, nxh, 21, 8)
+    fl = pass_flops(dom, V, 6, N, N, N, nxh)
+    achieved = byts / (avg_ms / 1e3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": dom,
+                "avg_launch_ms": avg_ms, "algorithmic_bytes_per_launch": byts,
+                "fp64_gflops_achieved": fl / (avg_ms / 1e3) / 1e9,
+                "peak_source": peaks["source"] + " hbm_gbs (copy)",
+                "pass_share": {k: tot[k] / max(sum(tot.values()), 1e-30) for k in tot},
+                "pass_avg_ms": {k: tot[k] / max(cnt[k], 1) for k in tot}}
+
+    # end to end through the C ABI: host phase map in, C* out, every step
+    e2e = None
+    if rank == 0 or world > 1:
+        ph_pinned = torch.from_numpy(ph).pin_memory()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e2e_its = 0
+        for _ in range(args.steps):
+            for h in handles:
+                h.set_microstructure(ph_pinned)  # host -> device inside the call
+                A, infos = h.effective(tol=TOL)  # C* back on the host
+                e2e_its += sum(i["iters"] for i in infos)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        e2e = {"value": e2e_its * V / dt, "unit": UNIT, "h2d_bytes_per_step": 2 * V,
+               "d2h_bytes_per_step": 2 * 36 * 8}
+
+    # mixed precision on the same workload (filtered + truncated)
+    mixed = None
+    if not args.no_mixed:
+        mh = [lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=g, precision=lsh.MIXED)
+              for g in (lsh.FILTERED, lsh.TRUNCATED)]
+        for h in mh:
+            h.effective(tol=TOL)
+        torch.cuda.synchronize()
+        m0 = torch.cuda.Event(enable_timing=True)
+        m1 = torch.cuda.Event(enable_timing=True)
+        m0.record(stream)
+        mits, outer, a64, errs = 0, 0, 0, []
+        for _ in range(args.steps):
+            for h, (Aref, _) in zip(mh, last):
+                A, infos = h.effective(tol=TOL)
+                mits += sum(i["iters"] for i in infos)
+                outer += sum(i["outer"] for i in infos)
+                a64 += sum(i["applies64"] for i in infos)
+                errs.append(float(np.abs(A - Aref).max() / np.abs(Aref).max()))
+        m1.record(stream)
+        torch.cuda.synchronize()
+        mms = m0.elapsed_time(m1)
+        fp64_equiv = total_its / args.steps * args.steps * V / (mms / 1e3)
+        mixed = {"value_raw": mits * V / (mms / 1e3), "value_fp64_equivalent": fp64_equiv,
+                 "ms_per_step": mms / args.steps, "inner_iterations_per_step": mits / args.steps,
+                 "outer_steps_per_step": outer / args.steps, "fp64_applies_per_step": a64 / args.steps,
+                 "c_star_max_rel_err_vs_fp64": max(errs), "speedup_vs_fp64": ms_max / mms}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = oracle_sample(ph, mods, iters=2)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": config(nsph, float(ph.mean())), "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clocks,
+                "iterations_per_step": total_its / args.steps,
+                "c_star_filtered_1111_1212": [float(last[0][0][0, 0]), float(last[0][0][5, 5] / 2)],
+                "mixed": mixed}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

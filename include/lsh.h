@@ -1,0 +1,185 @@
+/*
+ * lsh.h -- C ABI of liblsh, a GB300 (sm_103a) implementation of the
+ * matrix-free Lippmann-Schwinger (LS) solver of Brisard & Legoll, "Periodic
+ * homogenization using the Lippmann-Schwinger formalism" (arXiv:1411.0330).
+ *
+ * The library solves the Galerkin-discretised LS equation, Sec. 3, Eq. (13):
+ * for every voxel beta of the set I0 where A_beta != A0,
+ *
+ *     (A_beta - A0)^{-1} tau_beta + DFT^{-1}[ Gamma^h_k tau^_k ]_beta = p,
+ *
+ * tau = 0 off I0, with the truncated (Sec. 3.2.1, Eqs. (14)-(15)) or the
+ * filtered (Sec. 3.2.2) discrete Green operator Gamma^h, by conjugate
+ * gradients (Sec. 5), and returns the effective tensor
+ * A*_h p = A0 p + h^d sum_beta tau_beta (Eq. (tau_Astar), Theorem 13).
+ *
+ * Conventions shared by every entry point
+ *  - Grid: dim = 2 or 3, n[i] cells along axis i, V = n0 n1 (n2) voxels.
+ *    A field is component-major, [c][n2][n1][n0] with axis 0 fastest.
+ *  - Components: scalar problems (conductivity) have c = dim components, one
+ *    per axis.  Isotropic elasticity (dim 3) has c = 6 Mandel components
+ *    (11, 22, 33, sqrt2*23, sqrt2*13, sqrt2*12), so that the Euclidean dot of
+ *    two 6-vectors is the double contraction of the tensors.
+ *  - Memory: "device" pointers are CUDA device memory of the current device,
+ *    "host" pointers are ordinary host memory.  The library never allocates
+ *    device memory: everything it needs lives in the caller's workspace
+ *    (see lsh_workspace_size).  Inputs given at setup are copied into that
+ *    workspace, so the caller may free them afterwards.
+ *  - Streams: all device work of a handle is issued on the stream given at
+ *    setup.  Entry points returning host results synchronise that stream.
+ *  - Errors: every entry point returns an lsh_status; none aborts, throws or
+ *    traps.  A handle is not thread-safe; distinct handles are independent.
+ */
+#ifndef LSH_H
+#define LSH_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LSH_OK = 0,
+  LSH_ERR_INVALID_ARG = 1,          /* null pointer, bad enum, inconsistent sizes        */
+  LSH_ERR_UNSUPPORTED_SIZE = 2,     /* a grid length with a prime factor > 7, or too big */
+  LSH_ERR_REFERENCE_INDEFINITE = 3, /* A0 is not symmetric positive definite            */
+  LSH_ERR_SINGULAR_CONTRAST = 4,    /* A_beta - A0 is neither zero nor invertible       */
+  LSH_ERR_BREAKDOWN = 5,            /* CG found (p, K p) = 0 or a non-finite scalar     */
+  LSH_ERR_NOT_CONVERGED = 6,        /* tolerance not met within the iteration limits    */
+  LSH_ERR_WORKSPACE = 7,            /* workspace too small or misaligned (256 B)        */
+  LSH_ERR_CUDA = 8,                 /* a CUDA runtime call failed                       */
+  LSH_ERR_UNSUPPORTED = 9           /* valid request this build does not implement      */
+} lsh_status;
+
+enum { LSH_SCALAR = 0, LSH_ELASTIC_ISO = 1 };
+enum { LSH_GREEN_TRUNCATED = 0, LSH_GREEN_FILTERED = 1 };
+/* Arithmetic of the solve.  LSH_FP64: every step in double precision.
+ * LSH_MIXED: FFTs, Gamma apply and CG vectors in single precision, inner
+ * products and CG scalars in double, wrapped in iterative refinement whose
+ * residual b - K x is computed with the double-precision operator. */
+enum { LSH_FP64 = 0, LSH_MIXED = 1 };
+enum { LSH_F64 = 0, LSH_F32 = 1 }; /* element type of fields passed to lsh_apply */
+enum { LSH_SOLVER_AUTO = 0, LSH_SOLVER_CG = 1 };
+
+/* Problem description (Sec. 2.2 and Sec. 3).  All pointers are read during
+ * lsh_setup only. */
+typedef struct lsh_problem {
+  int dim;                     /* 2 or 3                                                  */
+  int n[3];                    /* cells per axis; n[2] ignored (treated as 1) for dim 2   */
+  int physics;                 /* LSH_SCALAR or LSH_ELASTIC_ISO (requires dim 3)          */
+  int green;                   /* LSH_GREEN_TRUNCATED or LSH_GREEN_FILTERED               */
+  int precision;               /* LSH_FP64 or LSH_MIXED                                   */
+  int nphase;                  /* 1..256                                                  */
+  const double *phase_moduli;  /* host.  Scalar: dim*dim row-major conductivity per phase
+                                  (must be diagonal in this build).  Elastic: (bulk K,
+                                  shear mu) per phase.                                    */
+  const double *ref_moduli;    /* host, same format as one phase: the reference medium A0
+                                  (Sec. 2.2.2).  NULL selects half the softest phase:
+                                  elastic mu0 = min(mu)/2, nu0 = 0.3; scalar a0 I with a0 =
+                                  min diagonal entry / 2 (not allowed with `scale`).      */
+  const unsigned char *phase;  /* phase id per voxel, V bytes; device or host memory      */
+  int phase_on_host;           /* nonzero: `phase` (and `scale`) are host pointers        */
+  const float *scale;          /* optional per-voxel factor s: A_beta = s_beta A_phase;
+                                  V floats, or NULL                                       */
+} lsh_problem;
+
+typedef struct lsh_solve_opts {
+  double tol;        /* stop when ||b - K tau||_2 <= tol ||b||_2 (Sec. 5 uses 1e-5)    */
+  int maxit;         /* iteration limit (FP64 CG iterations, or inner iterations summed) */
+  int solver;        /* LSH_SOLVER_AUTO or LSH_SOLVER_CG                                 */
+  double inner_tol;  /* LSH_MIXED: relative residual reduction of each inner solve
+                        (<= 0 selects 1e-4)                                              */
+  int max_outer;     /* LSH_MIXED: refinement steps (<= 0 selects 30)                    */
+  int check_every;   /* iterations between host convergence checks (<= 0 selects 8)     */
+  int warm_start;    /* lsh_solve: tau holds the initial guess on entry                  */
+} lsh_solve_opts;
+
+typedef struct lsh_solve_info {
+  int iters;      /* CG iterations (summed over inner solves for LSH_MIXED)             */
+  int outer;      /* refinement steps (LSH_MIXED), 0 otherwise                           */
+  int applies64;  /* applications of the double-precision operator                      */
+  int status;     /* lsh_status of this solve                                            */
+  double relres;  /* ||b - K tau|| / ||b|| at exit (recursive residual for FP64 CG,
+                     true double-precision residual for LSH_MIXED)                      */
+} lsh_solve_info;
+
+typedef struct lsh_handle lsh_handle;
+
+/* Bytes of device workspace lsh_setup needs for this problem. */
+lsh_status lsh_workspace_size(const lsh_problem *prob, size_t *bytes);
+
+/* Validate the problem (Eq. (hyp2): A_beta - A0 zero or invertible; A0 SPD),
+ * copy the microstructure into `workspace` (device, >= lsh_workspace_size
+ * bytes, 256-byte aligned, caller-owned, must outlive the handle), build the
+ * FFT plans, twiddles and the per-frequency Gamma^h table, and return a
+ * handle.  `stream` is a cudaStream_t (NULL = legacy default stream). */
+lsh_status lsh_setup(const lsh_problem *prob, void *workspace, size_t bytes, void *stream,
+                     lsh_handle **out);
+
+/* Replace the phase map (and scale field, if the problem has one) of an
+ * existing handle: same grid, phases and reference medium.  Host or device
+ * pointers per `on_host`.  Asynchronous for device inputs. */
+lsh_status lsh_set_microstructure(lsh_handle *h, const unsigned char *phase, const float *scale,
+                                  int on_host);
+
+/* y = K x with K = P (M + Gamma) P the operator of Eq. (13) (M_beta =
+ * (A_beta - A0)^{-1} of Eq. (7), P the projection on I0: values of x off I0
+ * are ignored and y is zero there).  x, y: device, c*V elements of `dtype`
+ * (LSH_F64, or LSH_F32 for LSH_MIXED handles), layout [c][n2][n1][n0].
+ * Asynchronous. */
+lsh_status lsh_apply(lsh_handle *h, int dtype, const void *x, void *y);
+
+/* Solve Eq. (13) for one macroscopic load p (host, c doubles; Mandel
+ * components for elasticity).  tau: device, c*V doubles, receives the
+ * polarisation (initial guess on entry when opts->warm_start).  Synchronous.
+ * Returns LSH_ERR_NOT_CONVERGED (tau holds the last iterate) if the
+ * tolerance is not met. */
+lsh_status lsh_solve(lsh_handle *h, const double *load, double *tau, const lsh_solve_opts *opts,
+                     lsh_solve_info *info);
+
+/* Effective tensor from c solves with the unit loads e_j (Sec. 2.1 and
+ * Theorem 13): Astar[i*c + j] = e_i . A*_h e_j (host, c*c doubles).
+ * tau_all: optional device buffer of c*c*V doubles receiving the c
+ * polarisations (load-major), NULL to skip.  infos: optional host array of
+ * c lsh_solve_info.  Synchronous. */
+lsh_status lsh_effective(lsh_handle *h, const lsh_solve_opts *opts, double *Astar, double *tau_all,
+                         lsh_solve_info *infos);
+
+/* Gradient of sum_ij W_ij e_i.A*_h e_j with respect to the per-voxel scale
+ * s_beta of a problem with a scale field: g_beta = h^d sum_ij W_ij
+ * eps_i,beta . A_phase(beta) eps_j,beta with eps_j = (A_beta - A0)^{-1}
+ * tau_j,beta (the derivative of the symmetric system of Eq. (13)).
+ * tau_all: device, c*c*V doubles from lsh_effective.  W: host, c*c.
+ * grad: device, V doubles.  Asynchronous. */
+lsh_status lsh_effective_grad(lsh_handle *h, const double *tau_all, const double *W, double *grad);
+
+/* Diagnostics (no counterpart in the paper): kernel launches issued by the
+ * handle, and, when enabled, the device time of each pass of the CG
+ * iteration measured with CUDA events recorded on the handle's stream
+ * between consecutive launches.  Pass kinds: 0 x-forward (with the CG
+ * prologue), 1 y-forward, 2 z-forward + Gamma^h product + z-inverse,
+ * 3 y-inverse, 4 x-inverse (with local term and (p, Kp)), 5 CG update. */
+typedef struct lsh_profile {
+  long long launches;          /* kernels launched since the last reset            */
+  long long timed_iters;       /* CG iterations covered by pass_ms                 */
+  double pass_ms[6];           /* summed device milliseconds per pass kind        */
+  long long pass_launches[6];  /* launches that did work, per pass kind           */
+} lsh_profile;
+
+/* Enable (nonzero) or disable per-pass event timing.  Host memory only. */
+lsh_status lsh_profile_enable(lsh_handle *h, int enable);
+
+/* Copy the counters into `out` (host); reset them when `reset` is nonzero. */
+lsh_status lsh_profile_read(lsh_handle *h, lsh_profile *out, int reset);
+
+/* Release the handle (host memory only; the workspace stays the caller's). */
+void lsh_destroy(lsh_handle *h);
+
+/* Static description of a status code. */
+const char *lsh_status_string(lsh_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LSH_H */

@@ -1,0 +1,198 @@
+// fft.cuh -- batched in-place mixed-radix FFT of lines held in shared memory.
+//
+// Forward transforms are decimation-in-frequency (DIF): natural-order input,
+// digit-reversed output.  Inverse transforms are decimation-in-time (DIT):
+// digit-reversed input, natural-order output, unnormalised.  Because the
+// Green-operator product between them is per frequency, the spectrum is never
+// permuted: the kernels only need the frequency k stored at each position.
+//
+// Stage s of a DIF with radix r acts on spans of length L (L = n for the
+// first stage, divided by r after each stage), m = L / r.  For j < m:
+//   y_p = (sum_q a_q w_r^{pq}) w_L^{pj},  a_q = x[j + q m],  y_p -> x[j + p m],
+// with w_N = exp(-2 i pi / N).  The frequency k of an n-point transform ends up
+// at position pos(k) = sum_s d_s m_s, where k = d_1 + r_1 (d_2 + r_2 (...)).
+// The DIT stage is the exact inverse of the DIF stage up to the factor r.
+//
+// All threads of the block cooperate; each stage ends with __syncthreads().
+// Twiddles come from a per-axis table tw[t] = exp(-2 i pi t / n), t < n.
+#pragma once
+
+#include "common.cuh"
+
+namespace lsh {
+
+template <typename T, int R, bool INV> struct Dft;
+
+template <typename T, bool INV> struct Dft<T, 2, INV> {
+  static __device__ __forceinline__ void run(C2<T>* a, const C2<T>*, int) {
+    C2<T> t = a[1];
+    a[1] = csub<T>(a[0], t);
+    a[0] = cadd<T>(a[0], t);
+  }
+};
+
+template <typename T, bool INV> struct Dft<T, 4, INV> {
+  static __device__ __forceinline__ void run(C2<T>* a, const C2<T>*, int) {
+    C2<T> t0 = cadd<T>(a[0], a[2]), t1 = csub<T>(a[0], a[2]);
+    C2<T> t2 = cadd<T>(a[1], a[3]), t3 = csub<T>(a[1], a[3]);
+    C2<T> r3 = INV ? cmul_pi<T>(t3) : cmul_mi<T>(t3);  // w_4^{1} t3
+    a[0] = cadd<T>(t0, t2);
+    a[2] = csub<T>(t0, t2);
+    a[1] = cadd<T>(t1, r3);
+    a[3] = csub<T>(t1, r3);
+  }
+};
+
+template <typename T, bool INV> struct Dft<T, 8, INV> {
+  static __device__ __forceinline__ void run(C2<T>* a, const C2<T>* tw, int n) {
+    const T h = (T)0.70710678118654752440084436210484903928;  // 1/sqrt(2)
+    C2<T> e[4] = {a[0], a[2], a[4], a[6]};
+    C2<T> o[4] = {a[1], a[3], a[5], a[7]};
+    Dft<T, 4, INV>::run(e, tw, n);
+    Dft<T, 4, INV>::run(o, tw, n);
+    // o_p *= w_8^p
+    C2<T> o1 = o[1], o3 = o[3];
+    if (!INV) {
+      o[1] = mkc<T>((o1.x + o1.y) * h, (o1.y - o1.x) * h);
+      o[2] = cmul_mi<T>(o[2]);
+      o[3] = mkc<T>((o3.y - o3.x) * h, -(o3.x + o3.y) * h);
+    } else {
+      o[1] = mkc<T>((o1.x - o1.y) * h, (o1.x + o1.y) * h);
+      o[2] = cmul_pi<T>(o[2]);
+      o[3] = mkc<T>(-(o3.x + o3.y) * h, (o3.x - o3.y) * h);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+      a[p] = cadd<T>(e[p], o[p]);
+      a[p + 4] = csub<T>(e[p], o[p]);
+    }
+  }
+};
+
+template <typename T, bool INV> struct Dft<T, 3, INV> {
+  static __device__ __forceinline__ void run(C2<T>* a, const C2<T>*, int) {
+    const T s3 = (T)0.86602540378443864676372317075293618347;  // sqrt(3)/2
+    C2<T> s = cadd<T>(a[1], a[2]), d = csub<T>(a[1], a[2]);
+    C2<T> m = mkc<T>(a[0].x - (T)0.5 * s.x, a[0].y - (T)0.5 * s.y);
+    C2<T> rd = INV ? cmul_pi<T>(d) : cmul_mi<T>(d);  // +-i d
+    a[0] = cadd<T>(a[0], s);
+    a[1] = mkc<T>(m.x + s3 * rd.x, m.y + s3 * rd.y);
+    a[2] = mkc<T>(m.x - s3 * rd.x, m.y - s3 * rd.y);
+  }
+};
+
+template <typename T, bool INV> struct Dft<T, 5, INV> {
+  static __device__ __forceinline__ void run(C2<T>* a, const C2<T>*, int) {
+    const T c1 = (T)0.30901699437494742410229341718281905886;   // cos(2pi/5)
+    const T c2 = (T)-0.80901699437494742410229341718281905886;  // cos(4pi/5)
+    const T s1 = (T)0.95105651629515357211643933337938214340;   // sin(2pi/5)
+    const T s2 = (T)0.58778525229247312916870595463907276860;   // sin(4pi/5)
+    C2<T> p14 = cadd<T>(a[1], a[4]), m14 = csub<T>(a[1], a[4]);
+    C2<T> p23 = cadd<T>(a[2], a[3]), m23 = csub<T>(a[2], a[3]);
+    C2<T> b1 = mkc<T>(a[0].x + c1 * p14.x + c2 * p23.x, a[0].y + c1 * p14.y + c2 * p23.y);
+    C2<T> b2 = mkc<T>(a[0].x + c2 * p14.x + c1 * p23.x, a[0].y + c2 * p14.y + c1 * p23.y);
+    C2<T> u1 = mkc<T>(s1 * m14.x + s2 * m23.x, s1 * m14.y + s2 * m23.y);
+    C2<T> u2 = mkc<T>(s2 * m14.x - s1 * m23.x, s2 * m14.y - s1 * m23.y);
+    // forward: y1 = b1 - i u1, y4 = b1 + i u1, y2 = b2 - i u2, y3 = b2 + i u2
+    C2<T> iu1 = INV ? cmul_pi<T>(u1) : cmul_mi<T>(u1);
+    C2<T> iu2 = INV ? cmul_pi<T>(u2) : cmul_mi<T>(u2);
+    a[0] = mkc<T>(a[0].x + p14.x + p23.x, a[0].y + p14.y + p23.y);
+    a[1] = cadd<T>(b1, iu1);
+    a[4] = csub<T>(b1, iu1);
+    a[2] = cadd<T>(b2, iu2);
+    a[3] = csub<T>(b2, iu2);
+  }
+};
+
+// Direct DFT for the remaining small prime (7), from the twiddle table.
+template <typename T, bool INV> struct Dft<T, 7, INV> {
+  static __device__ __forceinline__ void run(C2<T>* a, const C2<T>* tw, int n) {
+    const int st = n / 7;
+    C2<T> y[7];
+#pragma unroll
+    for (int p = 0; p < 7; ++p) {
+      C2<T> s = a[0];
+#pragma unroll
+      for (int q = 1; q < 7; ++q) {
+        C2<T> w = tw[((p * q) % 7) * st];
+        s = cadd<T>(s, INV ? cmulc<T>(a[q], w) : cmul<T>(a[q], w));
+      }
+      y[p] = s;
+    }
+#pragma unroll
+    for (int p = 0; p < 7; ++p) a[p] = y[p];
+  }
+};
+
+template <typename T, int R, bool INV>
+__device__ __forceinline__ void butterfly(C2<T>* base, int m, int te, const C2<T>* tw, int n) {
+  C2<T> a[R];
+#pragma unroll
+  for (int q = 0; q < R; ++q) a[q] = base[q * m];
+  if (!INV) {
+    Dft<T, R, false>::run(a, tw, n);
+    if (te != 0) {
+#pragma unroll
+      for (int p = 1; p < R; ++p) a[p] = cmul<T>(a[p], tw[p * te]);
+    }
+  } else {
+    if (te != 0) {
+#pragma unroll
+      for (int p = 1; p < R; ++p) a[p] = cmulc<T>(a[p], tw[p * te]);
+    }
+    Dft<T, R, true>::run(a, tw, n);
+  }
+#pragma unroll
+  for (int q = 0; q < R; ++q) base[q * m] = a[q];
+}
+
+// One stage over `nlines` lines of length n (line stride ls, element stride 1).
+template <typename T, bool INV>
+__device__ __forceinline__ void fft_stage(C2<T>* buf, int nlines, int ls, int n, int r, int L, const C2<T>* tw) {
+  const int m = L / r, nb = n / r, total = nb * nlines, tws = n / L;
+  const bool jmajor = m >= 16;
+  for (int w = threadIdx.x; w < total; w += blockDim.x) {
+    int line, b;
+    if (jmajor) {
+      line = w / nb;
+      b = w - line * nb;
+    } else {
+      b = w / nlines;
+      line = w - b * nlines;
+    }
+    const int sp = b / m, j = b - sp * m;
+    C2<T>* base = buf + line * ls + sp * L + j;
+    const int te = j * tws;
+    switch (r) {
+      case 8: butterfly<T, 8, INV>(base, m, te, tw, n); break;
+      case 4: butterfly<T, 4, INV>(base, m, te, tw, n); break;
+      case 2: butterfly<T, 2, INV>(base, m, te, tw, n); break;
+      case 3: butterfly<T, 3, INV>(base, m, te, tw, n); break;
+      case 5: butterfly<T, 5, INV>(base, m, te, tw, n); break;
+      default: butterfly<T, 7, INV>(base, m, te, tw, n); break;
+    }
+  }
+}
+
+// Forward (DIF) or inverse (DIT) transform of nlines lines; ends synchronised.
+template <typename T, bool INV>
+__device__ void fft_lines(C2<T>* buf, int nlines, int ls, const Plan1D& pl, const C2<T>* tw) {
+  const int n = pl.n;
+  if (!INV) {
+    int L = n;
+    for (int s = 0; s < pl.nst; ++s) {
+      fft_stage<T, false>(buf, nlines, ls, n, pl.radix[s], L, tw);
+      L /= pl.radix[s];
+      __syncthreads();
+    }
+  } else {
+    int L = 1;
+    for (int s = pl.nst - 1; s >= 0; --s) {
+      L *= pl.radix[s];
+      fft_stage<T, true>(buf, nlines, ls, n, pl.radix[s], L, tw);
+      __syncthreads();
+    }
+  }
+}
+
+}  // namespace lsh

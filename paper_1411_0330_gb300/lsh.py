@@ -1,0 +1,305 @@
+"""ctypes binding of liblsh (include/lsh.h): argument marshalling only.
+
+Every step of the Lippmann-Schwinger solve runs in the CUDA library; this
+module only converts arguments, allocates the device workspace with torch
+(PyTorch is used for device memory and streams) and turns status codes into
+exceptions.  There is no CPU fallback: constructing a Handle raises if the
+library cannot be loaded or CUDA is unavailable.
+
+Field layout: torch tensors of shape (c, n2, n1, n0) (3D) or (c, n1, n0)
+(2D), contiguous, on the handle's device; Mandel components for elasticity.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+SCALAR, ELASTIC = 0, 1
+TRUNCATED, FILTERED = 0, 1
+FP64, MIXED = 0, 1
+F64, F32 = 0, 1
+SOLVER_AUTO, SOLVER_CG = 0, 1
+
+OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_REFERENCE_INDEFINITE, ERR_SINGULAR_CONTRAST, \
+    ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_WORKSPACE, ERR_CUDA, ERR_UNSUPPORTED = range(10)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LSHError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        msg = _lib.lsh_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} (status {status})")
+        self.status = status
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n", ctypes.c_int * 3), ("physics", ctypes.c_int),
+                ("green", ctypes.c_int), ("precision", ctypes.c_int), ("nphase", ctypes.c_int),
+                ("phase_moduli", ctypes.POINTER(ctypes.c_double)),
+                ("ref_moduli", ctypes.POINTER(ctypes.c_double)),
+                ("phase", ctypes.c_void_p), ("phase_on_host", ctypes.c_int),
+                ("scale", ctypes.c_void_p)]
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("solver", ctypes.c_int),
+                ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("check_every", ctypes.c_int),
+                ("warm_start", ctypes.c_int)]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("applies64", ctypes.c_int),
+                ("status", ctypes.c_int), ("relres", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "outer": self.outer, "applies64": self.applies64,
+                "status": self.status, "relres": self.relres}
+
+
+class _Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong), ("timed_iters", ctypes.c_longlong),
+                ("pass_ms", ctypes.c_double * 6), ("pass_launches", ctypes.c_longlong * 6)]
+
+
+PASS_NAMES = ["x_forward", "y_forward", "z_gamma", "y_inverse", "x_inverse_local", "cg_update"]
+
+EXPORTS = ["lsh_workspace_size", "lsh_setup", "lsh_set_microstructure", "lsh_apply", "lsh_solve",
+           "lsh_effective", "lsh_effective_grad", "lsh_profile_enable", "lsh_profile_read", "lsh_destroy",
+           "lsh_status_string"]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(build_if_missing: bool = True):
+    """Load liblsh.so (building it with nvcc if it is missing and allowed)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.LIB
+            if not os.path.exists(path):
+                if not build_if_missing:
+                    raise OSError(f"liblsh.so not built ({path})")
+                _build.build()
+            lib = ctypes.CDLL(path)
+            P = ctypes.POINTER(_Problem)
+            vp = ctypes.c_void_p
+            dp = ctypes.POINTER(ctypes.c_double)
+            lib.lsh_status_string.restype = ctypes.c_char_p
+            lib.lsh_status_string.argtypes = [ctypes.c_int]
+            lib.lsh_workspace_size.argtypes = [P, ctypes.POINTER(ctypes.c_size_t)]
+            lib.lsh_setup.argtypes = [P, vp, ctypes.c_size_t, vp, ctypes.POINTER(vp)]
+            lib.lsh_set_microstructure.argtypes = [vp, vp, vp, ctypes.c_int]
+            lib.lsh_apply.argtypes = [vp, ctypes.c_int, vp, vp]
+            lib.lsh_solve.argtypes = [vp, dp, vp, ctypes.POINTER(_Opts), ctypes.POINTER(_Info)]
+            lib.lsh_effective.argtypes = [vp, ctypes.POINTER(_Opts), dp, vp, ctypes.POINTER(_Info)]
+            lib.lsh_effective_grad.argtypes = [vp, vp, dp, vp]
+            lib.lsh_profile_enable.argtypes = [vp, ctypes.c_int]
+            lib.lsh_profile_read.argtypes = [vp, ctypes.POINTER(_Profile), ctypes.c_int]
+            lib.lsh_destroy.argtypes = [vp]
+            lib.lsh_destroy.restype = None
+            _lib = lib
+    return _lib
+
+
+def _check(status: int, what: str, allow=()):
+    if status != OK and status not in allow:
+        raise LSHError(status, what)
+    return status
+
+
+def _problem_struct(phase_ptr, on_host, shape, physics, green, precision, moduli, ref, scale_ptr):
+    s = _Problem()
+    dim = len(shape)
+    s.dim = dim
+    n = list(reversed(shape)) + [1] * (3 - dim)
+    s.n = (ctypes.c_int * 3)(*n)
+    s.physics, s.green, s.precision = physics, green, precision
+    s.nphase = moduli.shape[0]
+    s.phase_moduli = moduli.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    s.ref_moduli = ref.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if ref is not None else \
+        ctypes.POINTER(ctypes.c_double)()
+    s.phase = phase_ptr
+    s.phase_on_host = 1 if on_host else 0
+    s.scale = scale_ptr
+    return s
+
+
+def _opts(tol, maxit, solver, inner_tol, max_outer, check_every, warm_start=False):
+    return _Opts(tol, maxit, solver, inner_tol, max_outer, check_every, 1 if warm_start else 0)
+
+
+def workspace_size(shape, phase_moduli, physics=SCALAR, green=TRUNCATED, precision=FP64, ref=None,
+                   has_scale=False) -> int:
+    """Workspace bytes for a problem (host-only computation; no GPU needed)."""
+    lib = load_library()
+    mods = np.ascontiguousarray(phase_moduli, dtype=np.float64)
+    refa = None if ref is None else np.ascontiguousarray(ref, dtype=np.float64)
+    dummy = ctypes.c_void_p(1)
+    s = _problem_struct(dummy, True, tuple(shape), physics, green, precision, mods, refa,
+                        ctypes.c_void_p(1) if has_scale else None)
+    out = ctypes.c_size_t(0)
+    _check(lib.lsh_workspace_size(ctypes.byref(s), ctypes.byref(out)), "lsh_workspace_size")
+    return out.value
+
+
+class Handle:
+    """One corrector problem on one GPU (Sec. 2.2 / Sec. 3 of the paper).
+
+    phase: uint8 torch tensor (device or CPU) or numpy array, shape (n2, n1, n0) or (n1, n0).
+    phase_moduli: scalar -> (nphase, d, d) diagonal conductivities; elastic -> (nphase, 2) (K, mu).
+    ref: reference medium in the same format as one phase, or None (half the softest phase).
+    scale: optional per-voxel float32 factor s (A_beta = s_beta A_phase).
+    """
+
+    def __init__(self, phase, phase_moduli, physics=SCALAR, green=TRUNCATED, precision=FP64, ref=None,
+                 scale=None, device=None, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("liblsh needs a CUDA device; no CPU fallback exists")
+        self._torch = torch
+        self.lib = load_library()
+        self.device = torch.device(device if device is not None else "cuda", )
+        if self.device.index is None:
+            self.device = torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        if isinstance(phase, np.ndarray):
+            phase_t = torch.from_numpy(np.ascontiguousarray(phase, dtype=np.uint8))
+        else:
+            phase_t = phase.contiguous()
+            if phase_t.dtype != torch.uint8:
+                raise TypeError("phase must be uint8")
+        self.shape = tuple(phase_t.shape)
+        self.dim = len(self.shape)
+        self.physics = physics
+        self.precision = precision
+        self.c = 6 if physics == ELASTIC else self.dim
+        self.V = int(np.prod(self.shape))
+        self.moduli = np.ascontiguousarray(phase_moduli, dtype=np.float64)
+        self.ref = None if ref is None else np.ascontiguousarray(ref, dtype=np.float64)
+        on_host = phase_t.device.type == "cpu"
+        scale_t = None
+        if scale is not None:
+            scale_t = torch.as_tensor(scale, dtype=torch.float32)
+            scale_t = scale_t.contiguous() if not on_host else scale_t.cpu().contiguous()
+            if not on_host:
+                scale_t = scale_t.to(self.device)
+        self.has_scale = scale_t is not None
+        s = _problem_struct(ctypes.c_void_p(phase_t.data_ptr()), on_host, self.shape, physics, green, precision,
+                            self.moduli, self.ref, ctypes.c_void_p(scale_t.data_ptr()) if scale_t is not None else None)
+        nbytes = ctypes.c_size_t(0)
+        _check(self.lib.lsh_workspace_size(ctypes.byref(s), ctypes.byref(nbytes)), "lsh_workspace_size")
+        self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            _check(self.lib.lsh_setup(ctypes.byref(s), ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
+                                      ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "lsh_setup")
+        self._h = h
+
+    # ------------------------------------------------------------------ helpers
+    @property
+    def field_shape(self):
+        return (self.c,) + self.shape
+
+    def _field(self, x, dtype):
+        t = self._torch
+        if not isinstance(x, t.Tensor):
+            x = t.as_tensor(np.asarray(x), dtype=dtype)
+        x = x.to(device=self.device, dtype=dtype).contiguous()
+        if tuple(x.shape) != self.field_shape:
+            x = x.reshape(self.field_shape)
+        return x
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.lib.lsh_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------ API
+    def set_microstructure(self, phase, scale=None):
+        t = self._torch
+        if isinstance(phase, np.ndarray):
+            phase = t.from_numpy(np.ascontiguousarray(phase, dtype=np.uint8))
+        on_host = phase.device.type == "cpu"
+        phase = phase.contiguous()
+        sp = None
+        if scale is not None:
+            scale = t.as_tensor(scale, dtype=t.float32)
+            scale = scale.cpu().contiguous() if on_host else scale.to(self.device).contiguous()
+            sp = ctypes.c_void_p(scale.data_ptr())
+        _check(self.lib.lsh_set_microstructure(self._h, ctypes.c_void_p(phase.data_ptr()), sp, 1 if on_host else 0),
+               "lsh_set_microstructure")
+
+    def apply(self, x, out=None, dtype=None):
+        """y = K x, the operator of Eq. (13) with the projection on I0."""
+        t = self._torch
+        dtype = dtype or (x.dtype if isinstance(x, t.Tensor) and x.dtype in (t.float32, t.float64) else t.float64)
+        x = self._field(x, dtype)
+        y = out if out is not None else t.empty_like(x)
+        _check(self.lib.lsh_apply(self._h, F64 if dtype == t.float64 else F32, ctypes.c_void_p(x.data_ptr()),
+                                  ctypes.c_void_p(y.data_ptr())), "lsh_apply")
+        return y
+
+    def solve(self, load, tau=None, tol=1e-10, maxit=10000, solver=SOLVER_AUTO, inner_tol=0.0, max_outer=0,
+              check_every=0, warm_start=False, raise_on_fail=True):
+        """Solve Eq. (13) for the macroscopic load p (c values).  Returns (tau, info dict)."""
+        t = self._torch
+        ld = np.ascontiguousarray(load, dtype=np.float64)
+        if tau is None:
+            tau = t.zeros(self.field_shape, dtype=t.float64, device=self.device)
+        info = _Info()
+        o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every, warm_start)
+        st = self.lib.lsh_solve(self._h, ld.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                ctypes.c_void_p(tau.data_ptr()), ctypes.byref(o), ctypes.byref(info))
+        _check(st, "lsh_solve", allow=() if raise_on_fail else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+        return tau, info.as_dict()
+
+    def effective(self, tol=1e-10, maxit=10000, solver=SOLVER_AUTO, inner_tol=0.0, max_outer=0, check_every=0,
+                  return_tau=False, tau_out=None, raise_on_fail=True):
+        """A*_h (c x c numpy, A[i, j] = e_i . A*_h e_j) and per-load info dicts."""
+        t = self._torch
+        A = np.zeros(self.c * self.c)
+        infos = (_Info * self.c)()
+        tau_all = tau_out
+        if return_tau and tau_all is None:
+            tau_all = t.empty((self.c,) + self.field_shape, dtype=t.float64, device=self.device)
+        o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every)
+        st = self.lib.lsh_effective(self._h, ctypes.byref(o), A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    ctypes.c_void_p(tau_all.data_ptr()) if tau_all is not None else None, infos)
+        _check(st, "lsh_effective", allow=() if raise_on_fail else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+        out = (A.reshape(self.c, self.c), [i.as_dict() for i in infos])
+        return out + (tau_all,) if tau_all is not None else out
+
+    def profile_enable(self, enable=True):
+        _check(self.lib.lsh_profile_enable(self._h, 1 if enable else 0), "lsh_profile_enable")
+
+    def profile_read(self, reset=False):
+        p = _Profile()
+        _check(self.lib.lsh_profile_read(self._h, ctypes.byref(p), 1 if reset else 0), "lsh_profile_read")
+        return {"launches": p.launches, "timed_iters": p.timed_iters,
+                "pass_ms": {n: p.pass_ms[i] for i, n in enumerate(PASS_NAMES)},
+                "pass_launches": {n: p.pass_launches[i] for i, n in enumerate(PASS_NAMES)}}
+
+    def effective_grad(self, tau_all, W, out=None):
+        """d(sum_ij W_ij e_i.A*_h e_j)/d s_beta for the per-voxel scale field."""
+        t = self._torch
+        w = np.ascontiguousarray(W, dtype=np.float64)
+        g = out if out is not None else t.empty(self.shape, dtype=t.float64, device=self.device)
+        _check(self.lib.lsh_effective_grad(self._h, ctypes.c_void_p(tau_all.data_ptr()),
+                                           w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                           ctypes.c_void_p(g.data_ptr())), "lsh_effective_grad")
+        return g

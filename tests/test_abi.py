@@ -1,0 +1,99 @@
+"""The C-ABI library loads and exports every entry point of include/lsh.h, and its
+host-only validation (workspace sizing) behaves; no GPU calls."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_1411_0330_gb300 import lsh
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1411_0330_gb300 import build
+    build.build()
+    return lsh.load_library(build_if_missing=False)
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "lsh.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(lsh_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 9
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(lsh.EXPORTS)
+
+
+def test_status_strings(lib):
+    for s in range(10):
+        assert lib.lsh_status_string(s)
+    assert lib.lsh_status_string(0) == b"ok"
+
+
+K1, MU1 = 0.8333333333333334, 0.38461538461538464
+K2, MU2 = 5.555555555555555, 4.166666666666667
+EL = np.array([[K1, MU1], [K2, MU2]])
+
+
+def test_workspace_size_scales(lib):
+    s64 = lsh.workspace_size((64, 64, 64), EL, physics=lsh.ELASTIC, green=lsh.FILTERED)
+    s128 = lsh.workspace_size((128, 128, 128), EL, physics=lsh.ELASTIC, green=lsh.FILTERED)
+    assert 7.5 < s128 / s64 < 8.5
+    # four FP64 fields + spectrum + table at 128^3: between 0.5 and 1 GB
+    assert 0.5e9 < s128 < 1.0e9
+    mixed = lsh.workspace_size((128, 128, 128), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
+    assert mixed > s128
+
+
+@pytest.mark.parametrize("shape", [(32, 32), (7, 5), (12, 10, 6), (1, 3, 4), (48, 96, 32), (256, 256, 256)])
+def test_supported_sizes(lib, shape):
+    d = len(shape)
+    assert lsh.workspace_size(shape, np.array([np.eye(d), 3 * np.eye(d)])) > 0
+
+
+@pytest.mark.parametrize("shape", [(11, 8), (8, 8, 13)])
+def test_unsupported_prime_factor(lib, shape):
+    d = len(shape)
+    with pytest.raises(lsh.LSHError) as e:
+        lsh.workspace_size(shape, np.array([np.eye(d)]))
+    assert e.value.status == lsh.ERR_UNSUPPORTED_SIZE
+
+
+def test_invalid_arguments(lib):
+    with pytest.raises(lsh.LSHError) as e:  # elasticity needs dim 3
+        lsh.workspace_size((8, 8), EL, physics=lsh.ELASTIC)
+    assert e.value.status == lsh.ERR_INVALID_ARG
+    with pytest.raises(lsh.LSHError) as e:  # non-diagonal conductivity
+        lsh.workspace_size((8, 8), np.array([[[2.0, 0.5], [0.5, 1.0]]]))
+    assert e.value.status == lsh.ERR_UNSUPPORTED
+    with pytest.raises(lsh.LSHError) as e:  # reference not positive definite
+        lsh.workspace_size((8, 8), np.array([np.eye(2)]), ref=-np.eye(2))
+    assert e.value.status == lsh.ERR_REFERENCE_INDEFINITE
+    with pytest.raises(lsh.LSHError) as e:  # A - A0 singular but nonzero
+        lsh.workspace_size((8, 8), np.array([np.diag([1.0, 2.0])]), ref=np.eye(2))
+    assert e.value.status == lsh.ERR_SINGULAR_CONTRAST
+    with pytest.raises(lsh.LSHError) as e:  # scale field requires an explicit reference
+        lsh.workspace_size((8, 8, 8), EL, physics=lsh.ELASTIC, has_scale=True)
+    assert e.value.status == lsh.ERR_INVALID_ARG
+
+
+def test_product_sources_do_not_use_the_oracle():
+    """Nothing in the product package includes, imports or links oracle/."""
+    pkg = os.path.join(ROOT, "paper_1411_0330_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in txt and "from oracle" not in txt, f
+                assert "lsh_oracle" not in txt, f

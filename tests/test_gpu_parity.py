@@ -1,0 +1,238 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: the spec bar is a relative error <= 1e-10 on A*/C* for the
+FP64 solver and <= 1e-8 for the mixed-precision solver; single operator
+applications in FP64 must agree to 1e-12 of the output's max norm (a few
+hundred ulps of FFT rounding), FP32 applications to 2e-5.
+"""
+import numpy as np
+import pytest
+
+from helpers import iso_mandel, k_mu
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_1411_0330_gb300 import lsh  # noqa: E402
+from paper_1411_0330_gb300 import microstructures as ms  # noqa: E402
+
+KM, MUM = k_mu(1.0, 0.3)
+KI, MUI = k_mu(10.0, 0.2)
+EL = np.array([[KM, MUM], [KI, MUI]])
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def _scalar_mods(d, seed, nphase=3):
+    rng = np.random.default_rng(seed)
+    return np.array([np.diag(rng.uniform(1.0, 10.0, d)) for _ in range(nphase)])
+
+
+APPLY_CASES = [
+    # (numpy shape (n2, n1, n0) or (n1, n0), physics, green)
+    ((32, 32), 0, 0),
+    ((12, 10), 0, 1),
+    ((9, 15), 0, 0),      # odd lengths, radices 3 and 5
+    ((14, 7), 0, 1),      # radix 7
+    ((10, 12, 16), 0, 1),
+    ((8, 8, 8), 1, 0),
+    ((8, 8, 8), 1, 1),
+    ((6, 10, 12), 1, 1),  # ragged kx tiles, radix 3 and 5
+    ((5, 7, 9), 1, 0),    # all odd
+    ((1, 6, 8), 1, 1),    # degenerate axis
+    ((24, 20, 18), 1, 1),
+]
+
+
+@pytest.mark.parametrize("shape,physics,green", APPLY_CASES)
+def test_apply_matches_oracle(shape, physics, green):
+    rng = np.random.default_rng(hash((shape, physics, green)) % 2**32)
+    d = len(shape)
+    if physics == 1:
+        ph = (rng.random(shape) < 0.4).astype(np.uint8)
+        mods = EL
+    else:
+        ph = rng.integers(0, 3, shape).astype(np.uint8)
+        mods = _scalar_mods(d, 3)
+    P = oracle.Problem(ph, mods, physics=physics, green=green)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=green)
+    x = rng.standard_normal(P.field_shape)
+    y = h.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    yo = oracle.apply(P, x)
+    assert rel(y, yo) < 1e-12
+
+
+def test_apply_with_inactive_voxels_and_reference():
+    """Voxels whose phase equals A0 are outside I0: the output vanishes there."""
+    ph = np.zeros((12, 16), np.uint8)
+    ph[3:9, 4:11] = 1
+    mods = np.array([np.eye(2) * 2.0, np.eye(2) * 7.0])
+    ref = np.eye(2) * 2.0
+    P = oracle.Problem(ph, mods, green=1, ref=ref)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.FILTERED, ref=ref)
+    x = np.random.default_rng(1).standard_normal(P.field_shape)
+    y = h.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    assert np.all(y[:, ph == 0] == 0)
+    assert rel(y, oracle.apply(P, x)) < 1e-12
+
+
+@pytest.mark.parametrize("green", [0, 1])
+def test_apply_fp32_mixed_handle(green):
+    rng = np.random.default_rng(5)
+    ph = (rng.random((16, 12, 20)) < 0.3).astype(np.uint8)
+    P = oracle.Problem(ph, EL, physics=1, green=green)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=green, precision=lsh.MIXED)
+    x = rng.standard_normal(P.field_shape)
+    y32 = h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy()
+    y64 = h.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    yo = oracle.apply(P, x)
+    assert rel(y64, yo) < 1e-12
+    assert rel(y32, yo) < 2e-5
+
+
+def test_config1_square_inclusion_indefinite_reference():
+    """32 x 32, k = 1 / 10, k0 = (1 + 10)/2 (indefinite operator), truncated Gamma,
+    loads e1, e2, rel. residual 1e-10: A* against the oracle's MINRES solution."""
+    ph = ms.square_inclusion(32)
+    mods = np.array([np.eye(2), 10 * np.eye(2)])
+    ref = 5.5 * np.eye(2)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.TRUNCATED, ref=ref)
+    A, infos = h.effective(tol=1e-10)
+    Ao, _ = oracle.effective(oracle.Problem(ph, mods, green=0, ref=ref), tol=1e-13)
+    assert rel(A, Ao) < 1e-10, (A, Ao, infos)
+    assert abs(A[0, 1]) < 1e-10 and abs(A[0, 0] - A[1, 1]) < 1e-10
+
+
+@pytest.mark.parametrize("green", [0, 1])
+def test_effective_spheres_fp64(green):
+    ph, _, _ = ms.sphere_microstructure(16, 2.0, 0.3, seed=1411)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=green)
+    A, infos = h.effective(tol=1e-12)
+    Ao, info_o = oracle.effective(oracle.Problem(ph, EL, physics=1, green=green), tol=1e-13)
+    assert rel(A, Ao) < 1e-10
+    assert np.allclose(A, A.T, atol=1e-10 * np.abs(A).max())
+    for i, inf in enumerate(infos):
+        assert inf["status"] == 0 and inf["relres"] <= 1e-12
+        assert abs(inf["iters"] - info_o[i, 0]) <= 3
+
+
+@pytest.mark.parametrize("green", [0, 1])
+def test_effective_mixed_precision(green):
+    ph, _, _ = ms.sphere_microstructure(16, 2.0, 0.3, seed=1412)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=green, precision=lsh.MIXED)
+    A, infos = h.effective(tol=1e-10)
+    Ao, _ = oracle.effective(oracle.Problem(ph, EL, physics=1, green=green), tol=1e-13)
+    assert rel(A, Ao) < 1e-8, rel(A, Ao)
+    for inf in infos:
+        assert inf["status"] == 0 and inf["relres"] <= 1e-10 and inf["outer"] >= 1
+
+
+def test_high_contrast_mixed():
+    ph, _, _ = ms.sphere_microstructure(16, 2.0, 0.3, seed=3)
+    mods = np.array([[KM, MUM], list(k_mu(1000.0, 0.2))])
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
+    A, infos = h.effective(tol=1e-10, maxit=20000)
+    Ao, _ = oracle.effective(oracle.Problem(ph, mods, physics=1, green=1), tol=1e-13, maxit=20000)
+    assert rel(A, Ao) < 1e-8, rel(A, Ao)
+
+
+def test_uniform_medium_and_empty_I0():
+    K1, mu1 = k_mu(2.0, 0.25)
+    ph = np.zeros((8, 8, 8), np.uint8)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), np.array([[K1, mu1]]), physics=lsh.ELASTIC, green=lsh.FILTERED,
+                   ref=np.array([0.4, 0.2]))
+    A, infos = h.effective(tol=1e-14)
+    assert np.allclose(A, iso_mandel(K1, mu1), atol=1e-13)
+    assert all(i["iters"] <= 2 for i in infos)
+    # A_phase == A0 everywhere: I0 empty, tau = 0, A* = A0, no iteration
+    h0 = lsh.Handle(torch.from_numpy(ph).cuda(), np.array([[K1, mu1]]), physics=lsh.ELASTIC,
+                    green=lsh.FILTERED, ref=np.array([K1, mu1]))
+    A0, infos0 = h0.effective(tol=1e-10, return_tau=False)
+    assert np.allclose(A0, iso_mandel(K1, mu1), atol=1e-14)
+    assert all(i["iters"] == 0 for i in infos0)
+
+
+def test_solve_warm_start_and_determinism():
+    ph, _, _ = ms.sphere_microstructure(16, 2.0, 0.25, seed=9)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED)
+    load = np.array([0.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    t1, i1 = h.solve(load, tol=1e-11)
+    t2, i2 = h.solve(load, tol=1e-11)
+    assert torch.equal(t1, t2) and i1 == i2
+    t3, i3 = h.solve(load, tau=t1.clone(), tol=1e-11, warm_start=True)
+    assert i3["iters"] <= 1
+    to, _, _ = oracle.solve(oracle.Problem(ph, EL, physics=1, green=1), load, tol=1e-13)
+    assert rel(t1.cpu().numpy(), to) < 1e-9
+
+
+def test_set_microstructure_matches_fresh_handle():
+    ph1, _, _ = ms.sphere_microstructure(16, 2.0, 0.2, seed=21)
+    ph2, _, _ = ms.sphere_microstructure(16, 2.0, 0.3, seed=22)
+    h = lsh.Handle(torch.from_numpy(ph1).cuda(), EL, physics=lsh.ELASTIC, green=lsh.TRUNCATED)
+    h.set_microstructure(ph2)  # from host memory
+    A, _ = h.effective(tol=1e-12)
+    Ao, _ = oracle.effective(oracle.Problem(ph2, EL, physics=1, green=0), tol=1e-13)
+    assert rel(A, Ao) < 1e-10
+
+
+def test_scale_gradient_matches_oracle():
+    rng = np.random.default_rng(4)
+    n = 6
+    ph = (rng.random((n, n, n)) < 0.4).astype(np.uint8)
+    s = rng.uniform(0.5, 2.0, (n, n, n)).astype(np.float32)
+    ref = np.array([0.25 * KM, 0.25 * MUM])
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, ref=ref,
+                   scale=torch.from_numpy(s).cuda())
+    A, infos, tau = h.effective(tol=1e-13, return_tau=True)
+    W = np.zeros((6, 6)); W[0, 0] = 1.0; W[5, 5] = 0.5
+    g = h.effective_grad(tau, W).cpu().numpy()
+    P = oracle.Problem(ph, EL, physics=1, green=1, ref=ref, scale=s.astype(np.float64))
+    Ao, _, tau_o = oracle.effective(P, tol=1e-13, return_tau=True)
+    go = oracle.scale_gradient(P, tau_o, W)
+    assert rel(A, Ao) < 1e-10
+    assert rel(tau.cpu().numpy(), tau_o) < 1e-9
+    assert rel(g, go) < 1e-9
+
+
+# ------------------------------------------------------------------ full size (128^3, the benchmark's workload)
+@pytest.fixture(scope="module")
+def spheres128():
+    ph, cen, r = ms.sphere_microstructure(128, 8.0, 0.3, seed=1411)
+    return ph
+
+
+@pytest.mark.parametrize("green", [0, 1])
+def test_full_size_apply_matches_oracle(spheres128, green):
+    ph = spheres128
+    rng = np.random.default_rng(128)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=green)
+    x = rng.standard_normal((6,) + ph.shape)
+    y = h.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+    yo = oracle.apply(oracle.Problem(ph, EL, physics=1, green=green), x)
+    assert rel(y, yo) < 1e-12
+
+
+def test_full_size_solve_properties(spheres128):
+    """128^3 FP64, filtered Gamma: the GPU polarisation satisfies the oracle's Eq. (13)
+    to the requested tolerance, and C* is symmetric and between C0 and Voigt."""
+    ph = spheres128
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED)
+    A, infos, tau = h.effective(tol=1e-10, return_tau=True)
+    P = oracle.Problem(ph, EL, physics=1, green=1)
+    for j in (0, 5):
+        t = tau[j].cpu().numpy()
+        r = oracle.apply(P, t)
+        b = np.zeros_like(t)
+        b[j] = 1.0
+        assert np.linalg.norm(b - r) / np.linalg.norm(b) < 2e-10
+    assert np.allclose(A, A.T, atol=1e-9 * np.abs(A).max())
+    C0 = iso_mandel(*P.ref)
+    f = ph.mean()
+    Cv = (1 - f) * iso_mandel(KM, MUM) + f * iso_mandel(KI, MUI)
+    assert np.linalg.eigvalsh(A - C0).min() > 0 and np.linalg.eigvalsh(Cv - A).min() > 0
