@@ -193,6 +193,7 @@ class Handle:
             if not on_host:
                 scale_t = scale_t.to(self.device)
         self.has_scale = scale_t is not None
+        self.phase_source = phase_t  # kept so the scale field can be replaced alone
         s = _problem_struct(ctypes.c_void_p(phase_t.data_ptr()), on_host, self.shape, physics, green, precision,
                             self.moduli, self.ref, ctypes.c_void_p(scale_t.data_ptr()) if scale_t is not None else None)
         nbytes = ctypes.c_size_t(0)

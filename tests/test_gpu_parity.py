@@ -114,12 +114,13 @@ def test_effective_spheres_fp64(green):
     ph, _, _ = ms.sphere_microstructure(16, 2.0, 0.3, seed=1411)
     h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=green)
     A, infos = h.effective(tol=1e-12)
-    Ao, info_o = oracle.effective(oracle.Problem(ph, EL, physics=1, green=green), tol=1e-13)
+    Ao, info_o = oracle.effective(oracle.Problem(ph, EL, physics=1, green=green), tol=1e-12)
     assert rel(A, Ao) < 1e-10
     assert np.allclose(A, A.T, atol=1e-10 * np.abs(A).max())
     for i, inf in enumerate(infos):
         assert inf["status"] == 0 and inf["relres"] <= 1e-12
-        assert abs(inf["iters"] - info_o[i, 0]) <= 3
+        # same algorithm, same tolerance: iteration counts agree up to rounding
+        assert abs(inf["iters"] - info_o[i, 0]) <= 2
 
 
 @pytest.mark.parametrize("green", [0, 1])
@@ -236,3 +237,41 @@ def test_full_size_solve_properties(spheres128):
     f = ph.mean()
     Cv = (1 - f) * iso_mandel(KM, MUM) + f * iso_mandel(KI, MUI)
     assert np.linalg.eigvalsh(A - C0).min() > 0 and np.linalg.eigvalsh(Cv - A).min() > 0
+
+
+def test_autograd_effective_tensor_gradient():
+    """torch.autograd over the C ABI: d(C*_1111 + C*_1212)/ds against the oracle's gradient
+    and central differences of the oracle's dense solves."""
+    from paper_1411_0330_gb300.autograd import effective_tensor
+    rng = np.random.default_rng(12)
+    n = 4
+    ph = (rng.random((n, n, n)) < 0.4).astype(np.uint8)
+    s0 = rng.uniform(0.5, 2.0, (n, n, n)).astype(np.float32)
+    ref = np.array([0.25 * KM, 0.25 * MUM])
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, ref=ref,
+                   scale=torch.from_numpy(s0).cuda())
+    s = torch.from_numpy(s0).cuda().requires_grad_(True)
+    A = effective_tensor(s, h, tol=1e-13)
+    obj = A[0, 0] + 0.5 * A[5, 5]  # C*_1111 + C*_1212 in Mandel components
+    obj.backward()
+    g = s.grad.double().cpu().numpy()
+    P = oracle.Problem(ph, EL, physics=1, green=1, ref=ref, scale=s0.astype(np.float64))
+    _, _, tau_o = oracle.effective(P, tol=1e-13, return_tau=True)
+    W = np.zeros((6, 6)); W[0, 0] = 1.0; W[5, 5] = 0.5
+    go = oracle.scale_gradient(P, tau_o, W)
+    assert rel(g, go) < 1e-8
+
+    def obj_dense(sc):
+        Pp = oracle.Problem(ph, EL, physics=1, green=1, ref=ref, scale=sc)
+        C0 = iso_mandel(*ref)
+        t0 = oracle.dense_solve(Pp, np.eye(6)[0])
+        t5 = oracle.dense_solve(Pp, np.eye(6)[5])
+        return C0[0, 0] + t0[0].mean() + 0.5 * (C0[5, 5] + t5[5].mean())
+
+    hstep = 1e-6
+    for idx in [(0, 0, 0), (1, 2, 3), (3, 1, 2)]:
+        sp = s0.astype(np.float64); sm = sp.copy()
+        sp[idx] += hstep
+        sm[idx] -= hstep
+        fd = (obj_dense(sp) - obj_dense(sm)) / (2 * hstep)
+        assert abs(g[idx] - fd) <= 1e-6 * abs(fd) + 1e-10
