@@ -78,10 +78,14 @@ typedef struct lsh_problem {
                                   (Sec. 2.2.2).  NULL selects half the softest phase:
                                   elastic mu0 = min(mu)/2, nu0 = 0.3; scalar a0 I with a0 =
                                   min diagonal entry / 2 (not allowed with `scale`).      */
-  const unsigned char *phase;  /* phase id per voxel, V bytes; device or host memory      */
+  const unsigned char *phase;  /* phase id per voxel, nbatch*V bytes (microstructure-major);
+                                  device or host memory                                   */
   int phase_on_host;           /* nonzero: `phase` (and `scale`) are host pointers        */
   const float *scale;          /* optional per-voxel factor s: A_beta = s_beta A_phase;
-                                  V floats, or NULL                                       */
+                                  nbatch*V floats, or NULL                                */
+  int nbatch;                  /* microstructures sharing grid, phases and A0 (<= 1: one) */
+  int max_systems;             /* systems (microstructure x load) solved simultaneously;
+                                  bounds the workspace.  <= 0: nbatch * c                 */
 } lsh_problem;
 
 typedef struct lsh_solve_opts {
@@ -125,33 +129,37 @@ lsh_status lsh_set_microstructure(lsh_handle *h, const unsigned char *phase, con
 
 /* y = K x with K = P (M + Gamma) P the operator of Eq. (13) (M_beta =
  * (A_beta - A0)^{-1} of Eq. (7), P the projection on I0: values of x off I0
- * are ignored and y is zero there).  x, y: device, c*V elements of `dtype`
- * (LSH_F64, or LSH_F32 for LSH_MIXED handles), layout [c][n2][n1][n0].
- * Asynchronous. */
+ * are ignored and y is zero there), for every microstructure of the batch.
+ * x, y: device, nbatch*c*V elements of `dtype` (LSH_F64, or LSH_F32 for
+ * LSH_MIXED handles), layout [nbatch][c][n2][n1][n0].  Asynchronous. */
 lsh_status lsh_apply(lsh_handle *h, int dtype, const void *x, void *y);
 
 /* Solve Eq. (13) for one macroscopic load p (host, c doubles; Mandel
- * components for elasticity).  tau: device, c*V doubles, receives the
- * polarisation (initial guess on entry when opts->warm_start).  Synchronous.
- * Returns LSH_ERR_NOT_CONVERGED (tau holds the last iterate) if the
- * tolerance is not met. */
+ * components for elasticity) on every microstructure of the batch.  tau:
+ * device, nbatch*c*V doubles, receives the polarisations (initial guesses on
+ * entry when opts->warm_start).  info: host array of nbatch entries or NULL.
+ * Synchronous.  Returns LSH_ERR_NOT_CONVERGED (tau holds the last iterate)
+ * if the tolerance is not met. */
 lsh_status lsh_solve(lsh_handle *h, const double *load, double *tau, const lsh_solve_opts *opts,
                      lsh_solve_info *info);
 
 /* Effective tensor from c solves with the unit loads e_j (Sec. 2.1 and
- * Theorem 13): Astar[i*c + j] = e_i . A*_h e_j (host, c*c doubles).
- * tau_all: optional device buffer of c*c*V doubles receiving the c
- * polarisations (load-major), NULL to skip.  infos: optional host array of
- * c lsh_solve_info.  Synchronous. */
+ * Theorem 13), for every microstructure b of the batch:
+ * Astar[(b*c + i)*c + j] = e_i . A*_h e_j (host, nbatch*c*c doubles).  All
+ * nbatch*c systems run together (in waves of max_systems).  tau_all:
+ * optional device buffer of nbatch*c*c*V doubles receiving the polarisations
+ * [b][load j][component][voxel], NULL to skip.  infos: optional host array
+ * of nbatch*c lsh_solve_info.  Synchronous. */
 lsh_status lsh_effective(lsh_handle *h, const lsh_solve_opts *opts, double *Astar, double *tau_all,
                          lsh_solve_info *infos);
 
 /* Gradient of sum_ij W_ij e_i.A*_h e_j with respect to the per-voxel scale
- * s_beta of a problem with a scale field: g_beta = h^d sum_ij W_ij
- * eps_i,beta . A_phase(beta) eps_j,beta with eps_j = (A_beta - A0)^{-1}
- * tau_j,beta (the derivative of the symmetric system of Eq. (13)).
- * tau_all: device, c*c*V doubles from lsh_effective.  W: host, c*c.
- * grad: device, V doubles.  Asynchronous. */
+ * s_beta (A_beta = s_beta A_phase; s = 1 without a scale field), for every
+ * microstructure: g_beta = h^d sum_ij W_ij eps_i,beta . A_phase(beta)
+ * eps_j,beta with eps_j = (A_beta - A0)^{-1} tau_j,beta (the derivative of
+ * the symmetric system of Eq. (13)).  tau_all: device, nbatch*c*c*V doubles
+ * from lsh_effective.  W: host, c*c.  grad: device, nbatch*V doubles.
+ * Synchronous. */
 lsh_status lsh_effective_grad(lsh_handle *h, const double *tau_all, const double *W, double *grad);
 
 /* Diagnostics (no counterpart in the paper): kernel launches issued by the

@@ -53,6 +53,29 @@ struct SolverState {
   unsigned int counter[4];  // last-block counters, reset by the last block
 };
 
+// Per-thread accumulator for inner products.  FP64 fields: plain double sum.
+// FP32 fields: Kahan-compensated float sum (the FP64 pipe of GB300 is 64x
+// slower than the FP32 one), handed to the FP64 block / grid reduction.
+template <typename T> struct Acc;
+template <> struct Acc<double> {
+  double s = 0.0;
+  __device__ __forceinline__ void add(double v) { s += v; }
+  __device__ __forceinline__ double get() const { return s; }
+};
+template <> struct Acc<float> {
+  float s = 0.0f, c = 0.0f;
+  __device__ __forceinline__ void add(float v) {
+    const float y = v - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+  }
+  __device__ __forceinline__ double get() const { return (double)s - (double)c; }
+};
+
+// a / d with a shift when d is a power of two (d is uniform across the block).
+__device__ __forceinline__ int fdiv(int a, int d) { return (d & (d - 1)) == 0 ? (a >> (__ffs(d) - 1)) : a / d; }
+
 // FFT plan of one axis: length n = product of the radices, DIF stage order.
 #define LSH_MAX_STAGES 8
 struct Plan1D {
@@ -109,20 +132,28 @@ __device__ __forceinline__ double gather_partials(const double* partials, unsign
   return s;
 }
 
-// Two-value variants (used where two inner products share one pass).
-__device__ __forceinline__ bool publish_partial2(double* partials, double v0, double v1, unsigned int* counter) {
-  __shared__ int is_last2;
-  const unsigned int nb = gridDim.x * gridDim.y * gridDim.z;
-  const unsigned int b = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+// Variants for a reduction over `nb` blocks of one system out of many in the
+// grid: block `b` (0..nb-1 within its system) publishes to partials[b].
+__device__ __forceinline__ bool publish_partial_sys(double* partials, unsigned int b, unsigned int nb, double v,
+                                                    unsigned int* counter) {
+  __shared__ int is_last_sys;
   if (threadIdx.x == 0) {
-    partials[2 * b] = v0;
-    partials[2 * b + 1] = v1;
+    partials[b] = v;
     __threadfence();
     unsigned int t = atomicAdd(counter, 1u);
-    is_last2 = (t == nb - 1);
+    is_last_sys = (t == nb - 1);
   }
   __syncthreads();
-  return is_last2 != 0;
+  return is_last_sys != 0;
+}
+
+__device__ __forceinline__ double gather_partials_sys(const double* partials, unsigned int nb, unsigned int* counter) {
+  __threadfence();
+  double s = 0.0;
+  for (unsigned int i = threadIdx.x; i < nb; i += blockDim.x) s += __ldcg(partials + i);
+  s = block_sum(s);
+  if (threadIdx.x == 0) *counter = 0u;
+  return s;
 }
 
 }  // namespace lsh

@@ -148,19 +148,20 @@ __device__ __forceinline__ void butterfly(C2<T>* base, int m, int te, const C2<T
 
 // One stage over `nlines` lines of length n (line stride ls, element stride 1).
 template <typename T, bool INV>
-__device__ __forceinline__ void fft_stage(C2<T>* buf, int nlines, int ls, int n, int r, int L, const C2<T>* tw) {
+__device__ __forceinline__ void fft_stage(C2<T>* __restrict__ buf, int nlines, int ls, int n, int r, int L,
+                                          const C2<T>* __restrict__ tw) {
   const int m = L / r, nb = n / r, total = nb * nlines, tws = n / L;
   const bool jmajor = m >= 16;
   for (int w = threadIdx.x; w < total; w += blockDim.x) {
     int line, b;
     if (jmajor) {
-      line = w / nb;
+      line = fdiv(w, nb);
       b = w - line * nb;
     } else {
-      b = w / nlines;
+      b = fdiv(w, nlines);
       line = w - b * nlines;
     }
-    const int sp = b / m, j = b - sp * m;
+    const int sp = fdiv(b, m), j = b - sp * m;
     C2<T>* base = buf + line * ls + sp * L + j;
     const int te = j * tws;
     switch (r) {

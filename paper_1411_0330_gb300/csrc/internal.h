@@ -8,38 +8,49 @@
 namespace lsh {
 
 // Everything an operator pass needs, passed by value to the kernels.
+//
+// A launch covers S independent systems (one microstructure, one load each)
+// that share the grid, the reference medium, the twiddles and the Gamma^h
+// table.  Fields are stored system-major: [S][c][nz][ny][nx] (real) and
+// [S][c][nz][ny][nxh] (half spectrum), so the rows of all systems are one
+// contiguous range; each x-pass block works inside one system (RY divides the
+// rows of a system) which keeps the per-system reductions block-aligned.
 template <typename T> struct OpArgs {
   int nx, ny, nz, nxh, c;
-  long long V;     // voxels
-  int nrows;       // c * nz * ny rows of length nx
-  int RY;          // rows per block in the x passes (even)
-  int TY, TZ;      // kx columns per block in the y / z passes
-  int lsx, lsy, lsz;  // shared-memory line strides (complex elements)
+  long long V;       // voxels per system
+  int S;             // systems in this launch
+  int sys0;          // global index of system 0 of this launch
+  int sys_per_ms;    // systems per microstructure (phase map index = (sys0 + s) / sys_per_ms)
+  int rps;           // rows per system: c * nz * ny
+  int bps;           // x-pass blocks per system: rps / RY
+  int RY;            // rows per block in the x passes
+  int TY, TZ;        // kx columns per block in the y / z passes
+  int lsx, lsy, lsz; // shared-memory line strides (complex elements)
   Plan1D px, py, pz;
   const C2<T>* twx;
   const C2<T>* twy;
   const C2<T>* twz;
-  const int* posx;  // frequency kx -> position after the x DIF
-  C2<T>* H;         // half spectrum [c][nz][ny][nxh] (y, z in digit-reversed positions)
-  const T* gtab;    // Gamma^h (internal basis, scaled by 1/V): [ncoef][nz][ny][nxh]
+  const int* posx;   // frequency kx -> position after the x DIF
+  C2<T>* H;          // half spectrum (y, z in digit-reversed positions)
+  const T* gtab;     // Gamma^h (internal basis, scaled by 1/V): [ncoef][nz][ny][nxh]
   int ncoef;
   // local term M_beta = (A_beta - A0)^{-1}, diagonal in the internal basis
-  const unsigned char* phase;  // per voxel
-  const float* scale;          // per voxel or null
+  const unsigned char* phase;  // [nbatch][V]
+  const float* scale;          // [nbatch][V] or null
   const unsigned char* act;    // per phase: 1 if A_phase != A0 (voxel in I0)
   const T* mtab;               // per phase * c: diagonal of M (no scale field)
   const T* modtab;             // per phase * c: diagonal of A_phase (scale field)
   T ref[6];                    // diagonal of A0 (internal basis)
-  T load[6];                   // macroscopic load (internal basis), residual mode
+  const T* loads;              // [S][6] macroscopic load per system (internal basis)
 };
 
-// Thread-block sizes and tile shapes, chosen at setup.
+// Thread-block sizes and tile shapes, chosen at setup for one system count.
 struct LaunchCfg {
   int threads;
-  int RY, TY, TZ;
+  int RY, TY, TZ, VEC;
   size_t smem_x, smem_y, smem_z;
-  int grid_x, grid_yx, grid_yy, grid_zx, grid_zy;
-  int grid_ew;  // elementwise kernels
+  int grid_x, grid_yx, grid_yy, grid_zx, grid_zy, grid_zz;
+  int ew_per_sys;  // blocks per system of the elementwise kernels
 };
 
 template <typename T>
@@ -53,30 +64,30 @@ template <typename T>
 void launch_xinv(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* xin, T* out, SolverState* st,
                  double* partials, cudaStream_t s);
 template <typename T>
-void launch_cg_update(T* r, const T* q, long long n, SolverState* st, double* partials, int grid, cudaStream_t s);
+void launch_cg_update(T* r, const T* q, long long n, int S, SolverState* st, double* partials, int G, cudaStream_t s);
 template <typename T>
-void launch_cg_finalize(T* x, const T* p, long long n, const SolverState* st, int grid, cudaStream_t s);
+void launch_cg_finalize(T* x, const T* p, long long n, int S, const SolverState* st, int G, cudaStream_t s);
 template <typename T>
-void launch_cg_begin(const T* r, long long n, SolverState* st, double* partials, double tol, double bb_given,
-                     int grid, cudaStream_t s);
+void launch_cg_begin(const T* r, long long n, int S, SolverState* st, double* partials, double tol,
+                     const double* bb_given, int G, cudaStream_t s);
 template <typename T>
-void launch_fill_rhs(const OpArgs<T>& a, T* r, T* x, int grid, cudaStream_t s);
+void launch_fill_rhs(const OpArgs<T>& a, T* r, T* x, int G, cudaStream_t s);
 template <typename T>
-void launch_rotate(const T* in, T* out, long long V, int to_internal, int grid, cudaStream_t s);
+void launch_rotate(const T* in, T* out, long long V, int nsys, int to_internal, cudaStream_t s);
 template <typename T>
-void launch_comp_sums(const T* x, int c, long long V, double* partials, int nblk, double* out, cudaStream_t s);
+void launch_comp_sums(const T* x, int c, long long V, int S, double* partials, int nblk, double* out, cudaStream_t s);
 template <typename T>
 void launch_gamma_table(const OpArgs<T>& a, int dim, int physics, int green, const double* ref_mandel,
                         const int* kofy, const int* kofz, cudaStream_t s);
-void launch_d2f_begin(const double* r64, float* r32, float* x32, long long n, SolverState* st, double* partials,
-                      double tol, int grid, cudaStream_t s);
-void launch_f2d_axpy(double* x64, const float* x32, long long n, int grid, cudaStream_t s);
-void launch_scan_phase(const unsigned char* phase, long long V, const unsigned char* act, int nphase,
-                       SolverState* st, double* partials, int grid, cudaStream_t s);
+void launch_d2f_begin(const double* r64, float* r32, float* x32, long long n, int S, SolverState* st,
+                      double* partials, double tol, const unsigned char* active, int G, cudaStream_t s);
+void launch_f2d_axpy(double* x64, const float* x32, long long n, cudaStream_t s);
+void launch_scan_phase(const unsigned char* phase, long long V, int B, const unsigned char* act, int nphase,
+                       SolverState* st, double* partials, int G, cudaStream_t s);
 void launch_scale_grad(const double* tau_all, const double* W, const unsigned char* phase, const float* scale,
-                       const double* modtab, const double* ref, int c, int elastic, long long V, double* grad,
-                       int grid, cudaStream_t s);
+                       const double* modtab, const double* ref, int c, int elastic, long long V, int B,
+                       double* grad, cudaStream_t s);
 
-template <typename T> void set_smem_attrs(const LaunchCfg& L);
+template <typename T> void set_smem_attrs();
 
 }  // namespace lsh

@@ -2,7 +2,7 @@
 //
 // One application of the Lippmann-Schwinger operator of Eq. (13),
 //   K x = P (M x + DFT^{-1}[Gamma^h_k DFT(x)_k]),
-// is five passes over a half spectrum H[c][nz][ny][nx/2+1]:
+// is five passes over a half spectrum H[S][c][nz][ny][nx/2+1]:
 //   xfwd   rows along x: two real rows packed as one complex line, DIF, split
 //          into the two Hermitian half rows (fused CG prologue p = r + beta p,
 //          x += alpha p_old);
@@ -14,84 +14,138 @@
 // Fields use an internal component basis in which M_beta is diagonal (for
 // isotropic elasticity: hydrostatic, two deviatoric normal and three shear
 // Mandel components), so every component plane is independent outside zgamma.
+// Every pass handles S independent systems at once (batched loads and
+// microstructures); each system has its own CG state and reductions.
+#include <algorithm>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "internal.h"
-
-#include <algorithm>
 
 namespace lsh {
 
 static constexpr int kThreads = 256;
 
-// Local coefficient m = (A_beta - A0)^{-1} of component `comp` at voxel `vox`.
+template <typename T, int VEC> struct VecOf;
+template <> struct VecOf<float, 4> { typedef float4 type; };
+template <> struct VecOf<double, 2> { typedef double2 type; };
+
+template <typename T, int VEC> __device__ __forceinline__ void vload(const T* __restrict__ p, T* v) {
+  if constexpr (VEC == 1) {
+    v[0] = p[0];
+  } else {
+    typedef typename VecOf<T, VEC>::type V;
+    const V w = *reinterpret_cast<const V*>(p);
+    const T* q = reinterpret_cast<const T*>(&w);
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) v[u] = q[u];
+  }
+}
+template <typename T, int VEC> __device__ __forceinline__ void vstore(T* __restrict__ p, const T* v) {
+  if constexpr (VEC == 1) {
+    p[0] = v[0];
+  } else {
+    typedef typename VecOf<T, VEC>::type V;
+    V w;
+    T* q = reinterpret_cast<T*>(&w);
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) q[u] = v[u];
+    *reinterpret_cast<V*>(p) = w;
+  }
+}
+
+// Local coefficient m = (A_beta - A0)^{-1} of component `comp` at voxel index
+// `pv` of the stacked phase map; *active = voxel in I0.
 template <typename T>
-__device__ __forceinline__ T local_coef(const OpArgs<T>& a, long long vox, int comp, int* active) {
-  const int ph = a.phase[vox];
+__device__ __forceinline__ T local_coef(const OpArgs<T>& a, long long pv, int comp, int* active) {
+  const int ph = a.phase[pv];
   *active = a.act[ph];
   if (a.scale == nullptr) return a.mtab[ph * a.c + comp];
-  const T s = (T)a.scale[vox];
+  const T s = (T)a.scale[pv];
   return (T)1 / (s * a.modtab[ph * a.c + comp] - a.ref[comp]);
 }
 
 // ------------------------------------------------------------------ x forward
-// MODE 0: input field `in`, masked by I0.  MODE 1: CG prologue.
-template <typename T, int MODE>
-__global__ void __launch_bounds__(kThreads) k_xfwd(OpArgs<T> a, const T* __restrict__ in, T* x, const T* r, T* p,
-                                                   const SolverState* st) {
-  if (MODE == 1 && st->done) return;
+// MODE 0: input field `in` (masked by I0).  MODE 1: CG prologue.
+// Each thread handles VEC consecutive x of a row pair and writes complete
+// complex values of the packed line Z = row_even + i row_odd.
+template <typename T, int MODE, int VEC>
+__global__ void __launch_bounds__(kThreads) k_xfwd(OpArgs<T> a, const T* __restrict__ in, T* __restrict__ x,
+                                                   const T* __restrict__ r, T* __restrict__ p,
+                                                   const SolverState* __restrict__ st) {
+  const int s = blockIdx.x / a.bps;
+  if (MODE == 1 && st[s].done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* Z = tw + a.nx;
-  int* pos = reinterpret_cast<int*>(Z + (a.RY >> 1) * a.lsx);
+  int* pos = reinterpret_cast<int*>(Z + ((a.RY + 1) >> 1) * a.lsx);
   const int nx = a.nx;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     tw[i] = a.twx[i];
     pos[i] = a.posx[i];
   }
-  const int row0 = blockIdx.x * a.RY;
-  const int nr = min(a.RY, a.nrows - row0);
+  const int rloc = (blockIdx.x - s * a.bps) * a.RY;  // first row inside the system
+  const int nr = a.RY;
   const int npair = (nr + 1) >> 1;
-  const int rows_per_comp = a.nz * a.ny;
+  const long long row0 = (long long)s * a.rps + rloc;  // global row
   T alpha = 0, beta = 0;
   int k = 0;
   if (MODE == 1) {
-    k = st->iter;
-    alpha = (T)st->alpha;
-    beta = (T)st->beta;
+    k = st[s].iter;
+    alpha = (T)st[s].alpha;
+    beta = (T)st[s].beta;
   }
-  const long long gbase = (long long)row0 * nx;
-  for (int idx = threadIdx.x; idx < nr * nx; idx += blockDim.x) {
-    const int row = idx / nx, xx = idx - row * nx;
-    const long long g = gbase + idx;
-    T v;
-    if (MODE == 0) {
-      const int comp = (row0 + row) / rows_per_comp;
-      const long long vox = g - (long long)comp * a.V;
-      v = a.act[a.phase[vox]] ? in[g] : (T)0;
-    } else {
-      if (k == 0) {
-        v = r[g];
-        p[g] = v;
+  const int nxv = nx / VEC;
+  const int rows_per_comp = a.nz * a.ny;
+  const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V;
+  for (int idx = threadIdx.x; idx < npair * nxv; idx += blockDim.x) {
+    const int lp = fdiv(idx, nxv);
+    const int xx = (idx - lp * nxv) * VEC;
+    T v0[VEC], v1[VEC];
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      T* v = h2 ? v1 : v0;
+      const int row = 2 * lp + h2;
+      if (row >= nr) {
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) v[u] = (T)0;
+        continue;
+      }
+      const long long g = (row0 + row) * nx + xx;
+      if (MODE == 0) {
+        vload<T, VEC>(in + g, v);
+        const int rs = rloc + row;
+        const int comp = rs / rows_per_comp;
+        const long long vox = (long long)(rs - comp * rows_per_comp) * nx + xx;
+#pragma unroll
+        for (int u = 0; u < VEC; ++u)
+          if (!a.act[a.phase[pbase + vox + u]]) v[u] = (T)0;
+      } else if (k == 0) {
+        vload<T, VEC>(r + g, v);
+        vstore<T, VEC>(p + g, v);
       } else {
-        const T po = p[g];
-        x[g] += alpha * po;
-        v = r[g] + beta * po;
-        p[g] = v;
+        T pv[VEC], xv[VEC];
+        vload<T, VEC>(p + g, pv);
+        vload<T, VEC>(x + g, xv);
+        vload<T, VEC>(r + g, v);
+#pragma unroll
+        for (int u = 0; u < VEC; ++u) {
+          xv[u] += alpha * pv[u];
+          v[u] += beta * pv[u];
+        }
+        vstore<T, VEC>(x + g, xv);
+        vstore<T, VEC>(p + g, v);
       }
     }
-    C2<T>* zc = Z + (row >> 1) * a.lsx + xx;
-    if (row & 1) zc->y = v;
-    else zc->x = v;
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) Z[lp * a.lsx + xx + u] = mkc<T>(v0[u], v1[u]);
   }
-  if (nr & 1)
-    for (int xx = threadIdx.x; xx < nx; xx += blockDim.x) Z[(nr >> 1) * a.lsx + xx].y = (T)0;
   __syncthreads();
   fft_lines<T, false>(Z, npair, a.lsx, a.px, tw);
   // split Z = X_a + i X_b into the two Hermitian half rows
   const T h = (T)0.5;
   for (int idx = threadIdx.x; idx < npair * a.nxh; idx += blockDim.x) {
-    const int lp = idx / a.nxh, kx = idx - lp * a.nxh;
+    const int lp = fdiv(idx, a.nxh), kx = idx - lp * a.nxh;
     const C2<T> z1 = Z[lp * a.lsx + pos[kx]];
     const C2<T> z2 = Z[lp * a.lsx + pos[kx == 0 ? 0 : nx - kx]];
     const long long hrow = row0 + 2 * lp;
@@ -101,33 +155,50 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(OpArgs<T> a, const T* __restr
 }
 
 // ------------------------------------------------------------------ y pass
+// blockIdx.y = plane (s, comp, z); TY consecutive kx columns per block.
 template <typename T, bool INV>
-__global__ void __launch_bounds__(kThreads) k_yfft(OpArgs<T> a, const SolverState* st) {
-  if (st != nullptr && st->done) return;
+__global__ void __launch_bounds__(kThreads) k_yfft(OpArgs<T> a, const SolverState* __restrict__ st) {
+  const long long plane = blockIdx.y;
+  const int s = (int)(plane / (a.c * a.nz));
+  if (st != nullptr && st[s].done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* buf = tw + a.ny;
   for (int i = threadIdx.x; i < a.ny; i += blockDim.x) tw[i] = a.twy[i];
-  const long long plane = blockIdx.y;
   const int kx0 = blockIdx.x * a.TY;
   const int nt = min(a.TY, a.nxh - kx0);
-  C2<T>* Hp = a.H + plane * a.ny * a.nxh + kx0;
-  for (int idx = threadIdx.x; idx < a.ny * a.TY; idx += blockDim.x) {
-    const int y = idx / a.TY, t = idx - y * a.TY;
-    if (t < nt) buf[t * a.lsy + y] = Hp[(long long)y * a.nxh + t];
+  const int TY = a.TY;
+  C2<T>* __restrict__ Hp = a.H + plane * a.ny * a.nxh + kx0;
+  const int tot = a.ny * TY;
+  for (int base = threadIdx.x; base < tot; base += 4 * blockDim.x) {
+    C2<T> v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int y = fdiv(idx, TY), t = idx - y * TY;
+      if (idx < tot && t < nt) v[u] = Hp[(long long)y * a.nxh + t];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int y = fdiv(idx, TY), t = idx - y * TY;
+      if (idx < tot && t < nt) buf[t * a.lsy + y] = v[u];
+    }
   }
   __syncthreads();
   fft_lines<T, INV>(buf, nt, a.lsy, a.py, tw);
-  for (int idx = threadIdx.x; idx < a.ny * a.TY; idx += blockDim.x) {
-    const int y = idx / a.TY, t = idx - y * a.TY;
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int y = fdiv(idx, TY), t = idx - y * TY;
     if (t < nt) Hp[(long long)y * a.nxh + t] = buf[t * a.lsy + y];
   }
 }
 
 // ------------------------------------------------------------------ z pass + Gamma
+// blockIdx.x = kx tile, blockIdx.y = y position, blockIdx.z = system.
 template <typename T, int NC>
-__global__ void __launch_bounds__(kThreads) k_zgamma(OpArgs<T> a, const SolverState* st) {
-  if (st != nullptr && st->done) return;
+__global__ void __launch_bounds__(kThreads) k_zgamma(OpArgs<T> a, const SolverState* __restrict__ st) {
+  const int s = blockIdx.z;
+  if (st != nullptr && st[s].done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* buf = tw + a.nz;
@@ -135,24 +206,35 @@ __global__ void __launch_bounds__(kThreads) k_zgamma(OpArgs<T> a, const SolverSt
   const int yp = blockIdx.y;
   const int kx0 = blockIdx.x * a.TZ;
   const int nt = min(a.TZ, a.nxh - kx0);
-  const int c = NC, nz = a.nz, TZ = a.TZ;
+  const int nz = a.nz, TZ = a.TZ;
   const long long zstride = (long long)a.ny * a.nxh;  // distance between z planes
   const long long cstride = zstride * nz;
-  C2<T>* Hp = a.H + (long long)yp * a.nxh + kx0;
-  for (int idx = threadIdx.x; idx < c * nz * TZ; idx += blockDim.x) {
-    const int t = idx % TZ, rest = idx / TZ;
-    const int z = rest % nz, comp = rest / nz;
-    C2<T> v = mkc<T>(0, 0);
-    if (t < nt) v = Hp[comp * cstride + z * zstride + t];
-    buf[(comp * TZ + t) * a.lsz + z] = v;
+  C2<T>* __restrict__ Hp = a.H + (long long)s * NC * cstride + (long long)yp * a.nxh + kx0;
+  const int tot = NC * nz * TZ;
+  for (int base = threadIdx.x; base < tot; base += 4 * blockDim.x) {
+    C2<T> v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int rest = fdiv(idx, TZ), t = idx - rest * TZ;
+      const int comp = fdiv(rest, nz), z = rest - comp * nz;
+      v[u] = mkc<T>(0, 0);
+      if (idx < tot && t < nt) v[u] = Hp[comp * cstride + z * zstride + t];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * blockDim.x;
+      const int rest = fdiv(idx, TZ), t = idx - rest * TZ;
+      const int comp = fdiv(rest, nz), z = rest - comp * nz;
+      if (idx < tot) buf[(comp * TZ + t) * a.lsz + z] = v[u];
+    }
   }
   __syncthreads();
-  if (nz > 1) fft_lines<T, false>(buf, c * TZ, a.lsz, a.pz, tw);
+  if (nz > 1) fft_lines<T, false>(buf, NC * TZ, a.lsz, a.pz, tw);
   // per-frequency product with the symmetric c x c table (packed upper triangle)
-  const T* G = a.gtab + (long long)yp * a.nxh + kx0;
-  const long long gstride = cstride;  // table has the same [nz][ny][nxh] layout per coefficient
+  const T* __restrict__ G = a.gtab + (long long)yp * a.nxh + kx0;
   for (int idx = threadIdx.x; idx < nz * TZ; idx += blockDim.x) {
-    const int t = idx % TZ, zp = idx / TZ;
+    const int zp = fdiv(idx, TZ), t = idx - zp * TZ;
     if (t >= nt) continue;
     C2<T> v[NC], y[NC];
 #pragma unroll
@@ -165,7 +247,7 @@ __global__ void __launch_bounds__(kThreads) k_zgamma(OpArgs<T> a, const SolverSt
     for (int i = 0; i < NC; ++i)
 #pragma unroll
       for (int j = i; j < NC; ++j, ++coef) {
-        const T g = G[coef * gstride + zp * zstride + t];
+        const T g = G[coef * cstride + zp * zstride + t];
         y[i].x += g * v[j].x;
         y[i].y += g * v[j].y;
         if (j != i) {
@@ -177,37 +259,40 @@ __global__ void __launch_bounds__(kThreads) k_zgamma(OpArgs<T> a, const SolverSt
     for (int i = 0; i < NC; ++i) buf[(i * TZ + t) * a.lsz + zp] = y[i];
   }
   __syncthreads();
-  if (nz > 1) fft_lines<T, true>(buf, c * TZ, a.lsz, a.pz, tw);
-  for (int idx = threadIdx.x; idx < c * nz * TZ; idx += blockDim.x) {
-    const int t = idx % TZ, rest = idx / TZ;
-    const int z = rest % nz, comp = rest / nz;
+  if (nz > 1) fft_lines<T, true>(buf, NC * TZ, a.lsz, a.pz, tw);
+  for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
+    const int rest = fdiv(idx, TZ), t = idx - rest * TZ;
+    const int comp = fdiv(rest, nz), z = rest - comp * nz;
     if (t < nt) Hp[comp * cstride + z * zstride + t] = buf[(comp * TZ + t) * a.lsz + z];
   }
 }
 
 // ------------------------------------------------------------------ x inverse + local term
 // MODE 0: out = P (M xin + g).  MODE 1 (CG): q = P (M p + g), (p, q) -> alpha.
-// MODE 2 (residual): out = P (load - M xin - g), (r, r) -> st->aux[0].
-template <typename T, int MODE>
+// MODE 2 (residual): out = P (load - M xin - g), (r, r) -> st[s].aux[0].
+template <typename T, int MODE, int VEC>
 __global__ void __launch_bounds__(kThreads) k_xinv(OpArgs<T> a, const T* __restrict__ xin, T* __restrict__ out,
-                                                   SolverState* st, double* partials) {
-  if (MODE == 1 && st->done) return;
+                                                   SolverState* __restrict__ st, double* __restrict__ partials) {
+  const int s = blockIdx.x / a.bps;
+  if (MODE == 1 && st[s].done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* Z = tw + a.nx;
-  int* pos = reinterpret_cast<int*>(Z + (a.RY >> 1) * a.lsx);
+  int* pos = reinterpret_cast<int*>(Z + ((a.RY + 1) >> 1) * a.lsx);
   const int nx = a.nx;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) {
     tw[i] = a.twx[i];
     pos[i] = a.posx[i];
   }
   __syncthreads();
-  const int row0 = blockIdx.x * a.RY;
-  const int nr = min(a.RY, a.nrows - row0);
+  const int blk = blockIdx.x - s * a.bps;
+  const int rloc = blk * a.RY;
+  const int nr = a.RY;
   const int npair = (nr + 1) >> 1;
+  const long long row0 = (long long)s * a.rps + rloc;
   // Z = X_a + i X_b over the full line, X(nx - k) = conj X(k) beyond the half
   for (int idx = threadIdx.x; idx < npair * a.nxh; idx += blockDim.x) {
-    const int lp = idx / a.nxh, kx = idx - lp * a.nxh;
+    const int lp = fdiv(idx, a.nxh), kx = idx - lp * a.nxh;
     const long long hrow = row0 + 2 * lp;
     const C2<T> xa = a.H[hrow * a.nxh + kx];
     const C2<T> xb = (2 * lp + 1 < nr) ? a.H[(hrow + 1) * a.nxh + kx] : mkc<T>(0, 0);
@@ -217,46 +302,61 @@ __global__ void __launch_bounds__(kThreads) k_xinv(OpArgs<T> a, const T* __restr
   __syncthreads();
   fft_lines<T, true>(Z, npair, a.lsx, a.px, tw);
   const int rows_per_comp = a.nz * a.ny;
-  const long long gbase = (long long)row0 * nx;
-  double acc = 0.0;
-  for (int idx = threadIdx.x; idx < nr * nx; idx += blockDim.x) {
-    const int row = idx / nx, xx = idx - row * nx;
-    const long long g = gbase + idx;
-    const C2<T> zc = Z[(row >> 1) * a.lsx + xx];
-    const T gv = (row & 1) ? zc.y : zc.x;
-    const int comp = (row0 + row) / rows_per_comp;
-    const long long vox = g - (long long)comp * a.V;
-    int active;
-    const T m = local_coef(a, vox, comp, &active);
-    const T xv = xin[g];
-    if (MODE == 0) {
-      out[g] = active ? m * xv + gv : (T)0;
-    } else if (MODE == 1) {
-      const T qv = active ? m * xv + gv : (T)0;
-      out[g] = qv;
-      acc += (double)xv * (double)qv;
-    } else {
-      const T rv = active ? a.load[comp] - (m * xv + gv) : (T)0;
-      out[g] = rv;
-      acc += (double)rv * (double)rv;
+  const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V;
+  const int nxv = nx / VEC;
+  Acc<T> acc;
+  for (int idx = threadIdx.x; idx < npair * nxv; idx += blockDim.x) {
+    const int lp = fdiv(idx, nxv);
+    const int xx = (idx - lp * nxv) * VEC;
+    C2<T> zc[VEC];
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) zc[u] = Z[lp * a.lsx + xx + u];
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int row = 2 * lp + h2;
+      if (row >= nr) continue;
+      const long long g = (row0 + row) * nx + xx;
+      const int rs = rloc + row;
+      const int comp = rs / rows_per_comp;
+      const long long vox = (long long)(rs - comp * rows_per_comp) * nx + xx;
+      T xv[VEC], ov[VEC];
+      vload<T, VEC>(xin + g, xv);
+#pragma unroll
+      for (int u = 0; u < VEC; ++u) {
+        int active;
+        const T m = local_coef(a, pbase + vox + u, comp, &active);
+        const T gv = h2 ? zc[u].y : zc[u].x;
+        if (MODE == 0) {
+          ov[u] = active ? m * xv[u] + gv : (T)0;
+        } else if (MODE == 1) {
+          ov[u] = active ? m * xv[u] + gv : (T)0;
+          acc.add(xv[u] * ov[u]);
+        } else {
+          ov[u] = active ? a.loads[s * 6 + comp] - (m * xv[u] + gv) : (T)0;
+          acc.add(ov[u] * ov[u]);
+        }
+      }
+      vstore<T, VEC>(out + g, ov);
     }
   }
   if (MODE != 0) {
-    acc = block_sum(acc);
-    if (publish_partial(partials, acc, &st->counter[0])) {
-      const double tot = gather_partials(partials, &st->counter[0]);
+    const double tot = block_sum(acc.get());
+    double* part = partials + (long long)s * a.bps;
+    SolverState* sst = st + s;
+    if (publish_partial_sys(part, blk, a.bps, tot, &sst->counter[0])) {
+      const double sum = gather_partials_sys(part, a.bps, &sst->counter[0]);
       if (threadIdx.x == 0) {
         if (MODE == 1) {
-          st->pq = tot;
-          if (!(fabs(tot) > 0.0) || !isfinite(tot) || !isfinite(st->rr)) {
-            st->status = 5;  // LSH_ERR_BREAKDOWN
-            st->alpha = 0.0;
-            st->done = 1;
+          sst->pq = sum;
+          if (!(fabs(sum) > 0.0) || !isfinite(sum) || !isfinite(sst->rr)) {
+            sst->status = 5;  // LSH_ERR_BREAKDOWN
+            sst->alpha = 0.0;
+            sst->done = 1;
           } else {
-            st->alpha = st->rr / tot;
+            sst->alpha = sst->rr / sum;
           }
         } else {
-          st->aux[0] = tot;
+          sst->aux[0] = sum;
         }
       }
     }
@@ -264,87 +364,124 @@ __global__ void __launch_bounds__(kThreads) k_xinv(OpArgs<T> a, const T* __restr
 }
 
 // ------------------------------------------------------------------ CG vector kernels
+// Grid (G, S): blockIdx.y is the system, n the elements per system.
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_cg_update(T* __restrict__ r, const T* __restrict__ q, long long n,
-                                                        SolverState* st, double* partials) {
-  if (st->done) return;
-  const T al = (T)st->alpha;
-  double acc = 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const T rv = r[i] - al * q[i];
-    r[i] = rv;
-    acc += (double)rv * (double)rv;
+                                                        SolverState* __restrict__ st, double* __restrict__ partials) {
+  const int s = blockIdx.y;
+  SolverState* sst = st + s;
+  if (sst->done) return;
+  const T al = (T)sst->alpha;
+  T* rs = r + s * n;
+  const T* qs = q + s * n;
+  Acc<T> acc;
+  constexpr int VEC = 16 / sizeof(T);
+  const long long nv = n / VEC;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
+    T rv[VEC], qv[VEC];
+    vload<T, VEC>(rs + i * VEC, rv);
+    vload<T, VEC>(qs + i * VEC, qv);
+#pragma unroll
+    for (int u = 0; u < VEC; ++u) {
+      rv[u] -= al * qv[u];
+      acc.add(rv[u] * rv[u]);
+    }
+    vstore<T, VEC>(rs + i * VEC, rv);
   }
-  acc = block_sum(acc);
-  if (publish_partial(partials, acc, &st->counter[1])) {
-    const double rrn = gather_partials(partials, &st->counter[1]);
+  for (long long i = nv * VEC + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const T rv = rs[i] - al * qs[i];
+    rs[i] = rv;
+    acc.add(rv * rv);
+  }
+  const double tot = block_sum(acc.get());
+  double* part = partials + (long long)s * gridDim.x;
+  if (publish_partial_sys(part, blockIdx.x, gridDim.x, tot, &sst->counter[1])) {
+    const double rrn = gather_partials_sys(part, gridDim.x, &sst->counter[1]);
     if (threadIdx.x == 0) {
-      st->beta = rrn / st->rr;
-      st->rr = rrn;
-      st->iter += 1;
+      sst->beta = rrn / sst->rr;
+      sst->rr = rrn;
+      sst->iter += 1;
       if (!isfinite(rrn)) {
-        st->status = 5;
-        st->done = 1;
-      } else if (rrn <= st->tol2) {
-        st->done = 1;
+        sst->status = 5;
+        sst->done = 1;
+      } else if (rrn <= sst->tol2) {
+        sst->done = 1;
       }
     }
   }
 }
 
 template <typename T>
-__global__ void k_cg_finalize(T* __restrict__ x, const T* __restrict__ p, long long n, const SolverState* st) {
-  const double al = st->alpha;
+__global__ void k_cg_finalize(T* __restrict__ x, const T* __restrict__ p, long long n,
+                              const SolverState* __restrict__ st) {
+  const int s = blockIdx.y;
+  const double al = st[s].alpha;
   if (al == 0.0) return;
   const T a = (T)al;
+  T* xs = x + s * n;
+  const T* ps = p + s * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    x[i] += a * p[i];
+    xs[i] += a * ps[i];
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_cg_begin(const T* __restrict__ r, long long n, SolverState* st,
-                                                       double* partials, double tol, double bb_given) {
-  double acc = 0.0;
+__global__ void __launch_bounds__(kThreads) k_cg_begin(const T* __restrict__ r, long long n,
+                                                       SolverState* __restrict__ st, double* __restrict__ partials,
+                                                       double tol, const double* __restrict__ bb_given) {
+  const int s = blockIdx.y;
+  const T* rs = r + s * n;
+  Acc<T> acc;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    acc += (double)r[i] * (double)r[i];
-  acc = block_sum(acc);
-  if (publish_partial(partials, acc, &st->counter[2])) {
-    const double rr = gather_partials(partials, &st->counter[2]);
+    acc.add(rs[i] * rs[i]);
+  const double tot = block_sum(acc.get());
+  double* part = partials + (long long)s * gridDim.x;
+  SolverState* sst = st + s;
+  if (publish_partial_sys(part, blockIdx.x, gridDim.x, tot, &sst->counter[2])) {
+    const double rr = gather_partials_sys(part, gridDim.x, &sst->counter[2]);
     if (threadIdx.x == 0) {
-      const double bb = bb_given >= 0.0 ? bb_given : rr;
-      st->rr = rr;
-      st->bb = bb;
-      st->tol2 = tol * tol * bb;
-      st->alpha = 0.0;
-      st->beta = 0.0;
-      st->pq = 0.0;
-      st->iter = 0;
-      st->status = 0;
-      st->done = (rr <= st->tol2) ? 1 : 0;
+      const double bb = bb_given != nullptr ? bb_given[s] : rr;
+      sst->rr = rr;
+      sst->bb = bb;
+      sst->tol2 = tol * tol * bb;
+      sst->alpha = 0.0;
+      sst->beta = 0.0;
+      sst->pq = 0.0;
+      sst->iter = 0;
+      sst->status = 0;
+      sst->done = (rr <= sst->tol2) ? 1 : 0;
     }
   }
 }
 
+// r = b (load on I0, 0 elsewhere), x = 0.  Grid (G, S).
 template <typename T>
 __global__ void k_fill_rhs(OpArgs<T> a, T* __restrict__ r, T* __restrict__ x) {
+  const int s = blockIdx.y;
   const long long n = (long long)a.c * a.V;
+  const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V;
+  T* rs = r + s * n;
+  T* xs = x + s * n;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int comp = (int)(i / a.V);
     const long long vox = i - comp * a.V;
-    r[i] = a.act[a.phase[vox]] ? a.load[comp] : (T)0;
-    x[i] = (T)0;
+    rs[i] = a.act[a.phase[pbase + vox]] ? a.loads[s * 6 + comp] : (T)0;
+    xs[i] = (T)0;
   }
 }
 
 // Internal basis <-> Mandel for the three normal components (shear unchanged):
 // h = (e11+e22+e33)/sqrt3, d1 = (e11-e22)/sqrt2, d2 = (e11+e22-2 e33)/sqrt6.
 template <typename T>
-__global__ void k_rotate(const T* in, T* out, long long V, int to_internal) {
+__global__ void k_rotate(const T* in, T* out, long long V, long long nvox, int to_internal) {
   const double s3 = 0.57735026918962576450914878050195745565;   // 1/sqrt3
   const double s2 = 0.70710678118654752440084436210484903928;   // 1/sqrt2
   const double s6 = 0.40824829046386301636621401245098189866;   // 1/sqrt6
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-    const double a0 = in[v], a1 = in[V + v], a2 = in[2 * V + v];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nvox; q += (long long)gridDim.x * blockDim.x) {
+    const long long sys = q / V, v = q - sys * V;
+    const T* i0 = in + sys * 6 * V;
+    T* o0 = out + sys * 6 * V;
+    const double a0 = i0[v], a1 = i0[V + v], a2 = i0[2 * V + v];
     double b0, b1, b2;
     if (to_internal) {
       b0 = (a0 + a1 + a2) * s3;
@@ -355,32 +492,34 @@ __global__ void k_rotate(const T* in, T* out, long long V, int to_internal) {
       b1 = a0 * s3 - a1 * s2 + a2 * s6;
       b2 = a0 * s3 - 2.0 * a2 * s6;
     }
-    out[v] = (T)b0;
-    out[V + v] = (T)b1;
-    out[2 * V + v] = (T)b2;
+    o0[v] = (T)b0;
+    o0[V + v] = (T)b1;
+    o0[2 * V + v] = (T)b2;
     if (in != out)
-      for (int k = 3; k < 6; ++k) out[k * V + v] = in[k * V + v];
+      for (int k = 3; k < 6; ++k) o0[k * V + v] = i0[k * V + v];
   }
 }
 
-// Per-component sums, deterministic: partials[comp][blk], then ordered sums.
+// Per-system, per-component sums, deterministic: partials[(s c + comp) nblk + blk].
 template <typename T>
-__global__ void __launch_bounds__(kThreads) k_comp_partials(const T* __restrict__ x, long long V, double* partials) {
-  const int comp = blockIdx.y;
-  const T* xc = x + comp * V;
+__global__ void __launch_bounds__(kThreads) k_comp_partials(const T* __restrict__ x, long long V, int c,
+                                                            double* __restrict__ partials) {
+  const int comp = blockIdx.y, s = blockIdx.z;
+  const T* xc = x + ((long long)s * c + comp) * V;
   double acc = 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x)
     acc += (double)xc[i];
   acc = block_sum(acc);
-  if (threadIdx.x == 0) partials[comp * gridDim.x + blockIdx.x] = acc;
+  if (threadIdx.x == 0) partials[((long long)s * c + comp) * gridDim.x + blockIdx.x] = acc;
 }
 
-__global__ void __launch_bounds__(kThreads) k_comp_final(const double* partials, int nblk, double* out) {
-  const int comp = blockIdx.x;
+__global__ void __launch_bounds__(kThreads) k_comp_final(const double* __restrict__ partials, int nblk,
+                                                         double* __restrict__ out) {
+  const int j = blockIdx.x;
   double s = 0.0;
-  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += partials[comp * nblk + i];
+  for (int i = threadIdx.x; i < nblk; i += blockDim.x) s += partials[(long long)j * nblk + i];
   s = block_sum(s);
-  if (threadIdx.x == 0) out[comp] = s;
+  if (threadIdx.x == 0) out[j] = s;
 }
 
 // ------------------------------------------------------------------ Gamma^h table
@@ -497,36 +636,44 @@ __global__ void k_gamma_table(OpArgs<T> a, GammaCtx g, const int* __restrict__ k
         }
     }
     const double invV = 1.0 / (double)a.V;
-    const long long cstride = nf;
     int coef = 0;
     T* out = const_cast<T*>(a.gtab);
     for (int i = 0; i < c; ++i)
-      for (int j = i; j < c; ++j, ++coef) out[coef * cstride + f] = (T)(0.5 * (Gi[i * c + j] + Gi[j * c + i]) * invV);
+      for (int j = i; j < c; ++j, ++coef) out[coef * nf + f] = (T)(0.5 * (Gi[i * c + j] + Gi[j * c + i]) * invV);
   }
 }
 
 // ------------------------------------------------------------------ mixed precision helpers
+// r32 = (float) r64, x32 = 0, inner CG state begun with tolerance tol relative
+// to the new right-hand side; systems with active[s] == 0 start done.
 __global__ void __launch_bounds__(kThreads) k_d2f_begin(const double* __restrict__ r64, float* __restrict__ r32,
-                                                        float* __restrict__ x32, long long n, SolverState* st,
-                                                        double* partials, double tol) {
-  double acc = 0.0;
+                                                        float* __restrict__ x32, long long n,
+                                                        SolverState* __restrict__ st, double* __restrict__ partials,
+                                                        double tol, const unsigned char* __restrict__ active) {
+  const int s = blockIdx.y;
+  const double* r64s = r64 + s * n;
+  float* r32s = r32 + s * n;
+  float* x32s = x32 + s * n;
+  Acc<float> acc;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float v = (float)r64[i];
-    r32[i] = v;
-    x32[i] = 0.0f;
-    acc += (double)v * (double)v;
+    const float v = (float)r64s[i];
+    r32s[i] = v;
+    x32s[i] = 0.0f;
+    acc.add(v * v);
   }
-  acc = block_sum(acc);
-  if (publish_partial(partials, acc, &st->counter[2])) {
-    const double rr = gather_partials(partials, &st->counter[2]);
+  const double tot = block_sum(acc.get());
+  double* part = partials + (long long)s * gridDim.x;
+  SolverState* sst = st + s;
+  if (publish_partial_sys(part, blockIdx.x, gridDim.x, tot, &sst->counter[2])) {
+    const double rr = gather_partials_sys(part, gridDim.x, &sst->counter[2]);
     if (threadIdx.x == 0) {
-      st->rr = rr;
-      st->bb = rr;
-      st->tol2 = tol * tol * rr;
-      st->alpha = st->beta = st->pq = 0.0;
-      st->iter = 0;
-      st->status = 0;
-      st->done = (rr <= st->tol2) ? 1 : 0;
+      sst->rr = rr;
+      sst->bb = rr;
+      sst->tol2 = tol * tol * rr;
+      sst->alpha = sst->beta = sst->pq = 0.0;
+      sst->iter = 0;
+      sst->status = 0;
+      sst->done = (!active[s] || rr <= sst->tol2) ? 1 : 0;
     }
   }
 }
@@ -536,37 +683,45 @@ __global__ void k_f2d_axpy(double* __restrict__ x64, const float* __restrict__ x
     x64[i] += (double)x32[i];
 }
 
-// Phase scan at setup: number of voxels in I0 (aux[1]) and largest phase id (aux[2]).
+// Phase scan at setup, grid (G, B): voxels in I0 per microstructure (st[b].aux[1])
+// and the largest phase id (st[0].pad via atomicMax).
 __global__ void __launch_bounds__(kThreads) k_scan_phase(const unsigned char* __restrict__ phase, long long V,
                                                          const unsigned char* __restrict__ act, int nphase,
-                                                         SolverState* st, double* partials) {
+                                                         SolverState* __restrict__ st, double* __restrict__ partials) {
+  const int b = blockIdx.y;
+  const unsigned char* ph = phase + (long long)b * V;
   double cnt = 0.0;
   int mx = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V; i += (long long)gridDim.x * blockDim.x) {
-    const int ph = phase[i];
-    mx = max(mx, ph);
-    if (ph < nphase && act[ph]) cnt += 1.0;
+    const int p = ph[i];
+    mx = max(mx, p);
+    if (p < nphase && act[p]) cnt += 1.0;
   }
   for (int o = 16; o > 0; o >>= 1) mx = max(mx, __shfl_down_sync(0xffffffffu, mx, o));
-  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(&st->pad, mx);
+  if ((threadIdx.x & 31) == 0 && mx > 0) atomicMax(&st[0].pad, mx);
   cnt = block_sum(cnt);
-  if (publish_partial(partials, cnt, &st->counter[3])) {
-    const double tot = gather_partials(partials, &st->counter[3]);
-    if (threadIdx.x == 0) st->aux[1] = tot;
+  double* part = partials + (long long)b * gridDim.x;
+  if (publish_partial_sys(part, blockIdx.x, gridDim.x, cnt, &st[b].counter[3])) {
+    const double tot = gather_partials_sys(part, gridDim.x, &st[b].counter[3]);
+    if (threadIdx.x == 0) st[b].aux[1] = tot;
   }
 }
 
-// Scale gradient: g = (1/V) sum_ij W_ij eps_i . A_phase eps_j, eps_j = M tau_j
-// (internal basis, where M and A_phase are diagonal).  tau_all is Mandel.
+// Scale gradient, grid (G, B): g = (1/V) sum_ij W_ij eps_i . A_phase eps_j with
+// eps_j = M tau_j (internal basis, where M and A_phase are diagonal); tau_all is
+// [B][c loads][c][V] in Mandel components.
 __global__ void k_scale_grad(const double* __restrict__ tau_all, const double* __restrict__ W,
                              const unsigned char* __restrict__ phase, const float* __restrict__ scale,
                              const double* __restrict__ modtab, const double* __restrict__ ref, int c, int elastic,
                              long long V, double* __restrict__ grad) {
   const double s3 = 0.57735026918962576450914878050195745565, s2 = 0.70710678118654752440084436210484903928,
                s6 = 0.40824829046386301636621401245098189866;
+  const int b = blockIdx.y;
+  const double* tau_b = tau_all + (long long)b * c * c * V;
   for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
-    const int ph = phase[v];
-    const double s = scale ? (double)scale[v] : 1.0;
+    const long long pv = (long long)b * V + v;
+    const int ph = phase[pv];
+    const double s = scale ? (double)scale[pv] : 1.0;
     double A[6], m[6];
     for (int k = 0; k < c; ++k) {
       A[k] = modtab[ph * c + k];
@@ -574,7 +729,7 @@ __global__ void k_scale_grad(const double* __restrict__ tau_all, const double* _
     }
     double eps[6][6];
     for (int j = 0; j < c; ++j) {
-      const double* tj = tau_all + (long long)j * c * V;
+      const double* tj = tau_b + (long long)j * c * V;
       double t[6];
       for (int k = 0; k < c; ++k) t[k] = tj[k * V + v];
       if (elastic) {
@@ -594,20 +749,26 @@ __global__ void k_scale_grad(const double* __restrict__ tau_all, const double* _
         for (int k = 0; k < c; ++k) e += eps[i][k] * A[k] * eps[j][k];
         gsum += w * e;
       }
-    grad[v] = gsum / (double)V;
+    grad[pv] = gsum / (double)V;
   }
 }
 
 // ------------------------------------------------------------------ launchers
 // The attribute is a per-function upper bound shared by every handle: always
 // allow the full 227 KB so that one handle never shrinks another's limit.
-template <typename T> void set_smem_attrs(const LaunchCfg&) {
+template <typename T> void set_smem_attrs() {
   const int mx = 227 * 1024;
-  cudaFuncSetAttribute(k_xfwd<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_xfwd<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_xinv<T, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_xinv<T, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-  cudaFuncSetAttribute(k_xinv<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  constexpr int VV = 16 / sizeof(T);
+  cudaFuncSetAttribute(k_xfwd<T, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xfwd<T, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xfwd<T, 0, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xfwd<T, 1, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv<T, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv<T, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv<T, 2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv<T, 0, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv<T, 1, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv<T, 2, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_yfft<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_yfft<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_zgamma<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -618,20 +779,27 @@ template <typename T> void set_smem_attrs(const LaunchCfg&) {
 template <typename T>
 void launch_xfwd(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* in, T* x, const T* r, T* p,
                  const SolverState* st, cudaStream_t s) {
-  if (mode == 0) k_xfwd<T, 0><<<L.grid_x, L.threads, L.smem_x, s>>>(a, in, x, r, p, st);
-  else k_xfwd<T, 1><<<L.grid_x, L.threads, L.smem_x, s>>>(a, in, x, r, p, st);
+  const int grid = a.S * a.bps;
+  constexpr int VV = 16 / sizeof(T);
+  if (L.VEC == VV) {
+    if (mode == 0) k_xfwd<T, 0, VV><<<grid, L.threads, L.smem_x, s>>>(a, in, x, r, p, st);
+    else k_xfwd<T, 1, VV><<<grid, L.threads, L.smem_x, s>>>(a, in, x, r, p, st);
+  } else {
+    if (mode == 0) k_xfwd<T, 0, 1><<<grid, L.threads, L.smem_x, s>>>(a, in, x, r, p, st);
+    else k_xfwd<T, 1, 1><<<grid, L.threads, L.smem_x, s>>>(a, in, x, r, p, st);
+  }
 }
 
 template <typename T>
 void launch_yfft(const OpArgs<T>& a, const LaunchCfg& L, bool inv, const SolverState* st, cudaStream_t s) {
-  dim3 g(L.grid_yx, L.grid_yy);
+  dim3 g(L.grid_yx, a.S * a.c * a.nz);
   if (inv) k_yfft<T, true><<<g, L.threads, L.smem_y, s>>>(a, st);
   else k_yfft<T, false><<<g, L.threads, L.smem_y, s>>>(a, st);
 }
 
 template <typename T>
 void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st, cudaStream_t s) {
-  dim3 g(L.grid_zx, L.grid_zy);
+  dim3 g(L.grid_zx, L.grid_zy, a.S);
   if (a.c == 6) k_zgamma<T, 6><<<g, L.threads, L.smem_z, s>>>(a, st);
   else if (a.c == 3) k_zgamma<T, 3><<<g, L.threads, L.smem_z, s>>>(a, st);
   else k_zgamma<T, 2><<<g, L.threads, L.smem_z, s>>>(a, st);
@@ -640,34 +808,44 @@ void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st
 template <typename T>
 void launch_xinv(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* xin, T* out, SolverState* st,
                  double* partials, cudaStream_t s) {
-  if (mode == 0) k_xinv<T, 0><<<L.grid_x, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
-  else if (mode == 1) k_xinv<T, 1><<<L.grid_x, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
-  else k_xinv<T, 2><<<L.grid_x, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
+  const int grid = a.S * a.bps;
+  constexpr int VV = 16 / sizeof(T);
+  if (L.VEC == VV) {
+    if (mode == 0) k_xinv<T, 0, VV><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
+    else if (mode == 1) k_xinv<T, 1, VV><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
+    else k_xinv<T, 2, VV><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
+  } else {
+    if (mode == 0) k_xinv<T, 0, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
+    else if (mode == 1) k_xinv<T, 1, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
+    else k_xinv<T, 2, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
+  }
 }
 
 template <typename T>
-void launch_cg_update(T* r, const T* q, long long n, SolverState* st, double* partials, int grid, cudaStream_t s) {
-  k_cg_update<T><<<grid, kThreads, 0, s>>>(r, q, n, st, partials);
+void launch_cg_update(T* r, const T* q, long long n, int S, SolverState* st, double* partials, int G, cudaStream_t s) {
+  k_cg_update<T><<<dim3(G, S), kThreads, 0, s>>>(r, q, n, st, partials);
 }
 template <typename T>
-void launch_cg_finalize(T* x, const T* p, long long n, const SolverState* st, int grid, cudaStream_t s) {
-  k_cg_finalize<T><<<grid, kThreads, 0, s>>>(x, p, n, st);
+void launch_cg_finalize(T* x, const T* p, long long n, int S, const SolverState* st, int G, cudaStream_t s) {
+  k_cg_finalize<T><<<dim3(G, S), kThreads, 0, s>>>(x, p, n, st);
 }
 template <typename T>
-void launch_cg_begin(const T* r, long long n, SolverState* st, double* partials, double tol, double bb_given,
-                     int grid, cudaStream_t s) {
-  k_cg_begin<T><<<grid, kThreads, 0, s>>>(r, n, st, partials, tol, bb_given);
+void launch_cg_begin(const T* r, long long n, int S, SolverState* st, double* partials, double tol,
+                     const double* bb_given, int G, cudaStream_t s) {
+  k_cg_begin<T><<<dim3(G, S), kThreads, 0, s>>>(r, n, st, partials, tol, bb_given);
 }
-template <typename T> void launch_fill_rhs(const OpArgs<T>& a, T* r, T* x, int grid, cudaStream_t s) {
-  k_fill_rhs<T><<<grid, kThreads, 0, s>>>(a, r, x);
+template <typename T> void launch_fill_rhs(const OpArgs<T>& a, T* r, T* x, int G, cudaStream_t s) {
+  k_fill_rhs<T><<<dim3(G, a.S), kThreads, 0, s>>>(a, r, x);
 }
-template <typename T> void launch_rotate(const T* in, T* out, long long V, int to_internal, int grid, cudaStream_t s) {
-  k_rotate<T><<<grid, kThreads, 0, s>>>(in, out, V, to_internal);
+template <typename T> void launch_rotate(const T* in, T* out, long long V, int nsys, int to_internal, cudaStream_t s) {
+  const long long nvox = V * nsys;
+  const int grid = (int)std::max(1LL, std::min((nvox + kThreads - 1) / kThreads, 152LL * 16));
+  k_rotate<T><<<grid, kThreads, 0, s>>>(in, out, V, nvox, to_internal);
 }
 template <typename T>
-void launch_comp_sums(const T* x, int c, long long V, double* partials, int nblk, double* out, cudaStream_t s) {
-  k_comp_partials<T><<<dim3(nblk, c), kThreads, 0, s>>>(x, V, partials);
-  k_comp_final<<<c, kThreads, 0, s>>>(partials, nblk, out);
+void launch_comp_sums(const T* x, int c, long long V, int S, double* partials, int nblk, double* out, cudaStream_t s) {
+  k_comp_partials<T><<<dim3(nblk, c, S), kThreads, 0, s>>>(x, V, c, partials);
+  k_comp_final<<<c * S, kThreads, 0, s>>>(partials, nblk, out);
 }
 template <typename T>
 void launch_gamma_table(const OpArgs<T>& a, int dim, int physics, int green, const double* ref_mandel,
@@ -685,38 +863,41 @@ void launch_gamma_table(const OpArgs<T>& a, int dim, int physics, int green, con
   const int grid = (int)std::min<long long>((nf + 127) / 128, 152LL * 16);
   k_gamma_table<T><<<grid, 128, 0, s>>>(a, g, kofy, kofz);
 }
-void launch_d2f_begin(const double* r64, float* r32, float* x32, long long n, SolverState* st, double* partials,
-                      double tol, int grid, cudaStream_t s) {
-  k_d2f_begin<<<grid, kThreads, 0, s>>>(r64, r32, x32, n, st, partials, tol);
+void launch_d2f_begin(const double* r64, float* r32, float* x32, long long n, int S, SolverState* st,
+                      double* partials, double tol, const unsigned char* active, int G, cudaStream_t s) {
+  k_d2f_begin<<<dim3(G, S), kThreads, 0, s>>>(r64, r32, x32, n, st, partials, tol, active);
 }
-void launch_f2d_axpy(double* x64, const float* x32, long long n, int grid, cudaStream_t s) {
+void launch_f2d_axpy(double* x64, const float* x32, long long n, cudaStream_t s) {
+  const int grid = (int)std::max(1LL, std::min((n + kThreads - 1) / kThreads, 152LL * 16));
   k_f2d_axpy<<<grid, kThreads, 0, s>>>(x64, x32, n);
 }
-void launch_scan_phase(const unsigned char* phase, long long V, const unsigned char* act, int nphase,
-                       SolverState* st, double* partials, int grid, cudaStream_t s) {
-  k_scan_phase<<<grid, kThreads, 0, s>>>(phase, V, act, nphase, st, partials);
+void launch_scan_phase(const unsigned char* phase, long long V, int B, const unsigned char* act, int nphase,
+                       SolverState* st, double* partials, int G, cudaStream_t s) {
+  k_scan_phase<<<dim3(G, B), kThreads, 0, s>>>(phase, V, act, nphase, st, partials);
 }
 void launch_scale_grad(const double* tau_all, const double* W, const unsigned char* phase, const float* scale,
-                       const double* modtab, const double* ref, int c, int elastic, long long V, double* grad,
-                       int grid, cudaStream_t s) {
-  k_scale_grad<<<grid, 128, 0, s>>>(tau_all, W, phase, scale, modtab, ref, c, elastic, V, grad);
+                       const double* modtab, const double* ref, int c, int elastic, long long V, int B,
+                       double* grad, cudaStream_t s) {
+  const int G = (int)std::max(1LL, std::min((V + 127) / 128, 152LL * 8));
+  k_scale_grad<<<dim3(G, B), 128, 0, s>>>(tau_all, W, phase, scale, modtab, ref, c, elastic, V, grad);
 }
 
-#define LSH_INSTANTIATE(T)                                                                                        \
-  template void set_smem_attrs<T>(const LaunchCfg&);                                                              \
-  template void launch_xfwd<T>(const OpArgs<T>&, const LaunchCfg&, int, const T*, T*, const T*, T*,               \
-                               const SolverState*, cudaStream_t);                                                 \
-  template void launch_yfft<T>(const OpArgs<T>&, const LaunchCfg&, bool, const SolverState*, cudaStream_t);       \
-  template void launch_zgamma<T>(const OpArgs<T>&, const LaunchCfg&, const SolverState*, cudaStream_t);           \
-  template void launch_xinv<T>(const OpArgs<T>&, const LaunchCfg&, int, const T*, T*, SolverState*, double*,      \
-                               cudaStream_t);                                                                     \
-  template void launch_cg_update<T>(T*, const T*, long long, SolverState*, double*, int, cudaStream_t);           \
-  template void launch_cg_finalize<T>(T*, const T*, long long, const SolverState*, int, cudaStream_t);            \
-  template void launch_cg_begin<T>(const T*, long long, SolverState*, double*, double, double, int, cudaStream_t); \
-  template void launch_fill_rhs<T>(const OpArgs<T>&, T*, T*, int, cudaStream_t);                                  \
-  template void launch_rotate<T>(const T*, T*, long long, int, int, cudaStream_t);                                \
-  template void launch_comp_sums<T>(const T*, int, long long, double*, int, double*, cudaStream_t);               \
-  template void launch_gamma_table<T>(const OpArgs<T>&, int, int, int, const double*, const int*, const int*,     \
+#define LSH_INSTANTIATE(T)                                                                                         \
+  template void set_smem_attrs<T>();                                                                               \
+  template void launch_xfwd<T>(const OpArgs<T>&, const LaunchCfg&, int, const T*, T*, const T*, T*,                \
+                               const SolverState*, cudaStream_t);                                                  \
+  template void launch_yfft<T>(const OpArgs<T>&, const LaunchCfg&, bool, const SolverState*, cudaStream_t);        \
+  template void launch_zgamma<T>(const OpArgs<T>&, const LaunchCfg&, const SolverState*, cudaStream_t);            \
+  template void launch_xinv<T>(const OpArgs<T>&, const LaunchCfg&, int, const T*, T*, SolverState*, double*,       \
+                               cudaStream_t);                                                                      \
+  template void launch_cg_update<T>(T*, const T*, long long, int, SolverState*, double*, int, cudaStream_t);       \
+  template void launch_cg_finalize<T>(T*, const T*, long long, int, const SolverState*, int, cudaStream_t);        \
+  template void launch_cg_begin<T>(const T*, long long, int, SolverState*, double*, double, const double*, int,    \
+                                   cudaStream_t);                                                                  \
+  template void launch_fill_rhs<T>(const OpArgs<T>&, T*, T*, int, cudaStream_t);                                   \
+  template void launch_rotate<T>(const T*, T*, long long, int, int, cudaStream_t);                                 \
+  template void launch_comp_sums<T>(const T*, int, long long, int, double*, int, double*, cudaStream_t);           \
+  template void launch_gamma_table<T>(const OpArgs<T>&, int, int, int, const double*, const int*, const int*,      \
                                       cudaStream_t);
 
 LSH_INSTANTIATE(double)

@@ -3,9 +3,10 @@
 // Setup validates the problem, derives the diagonal local operator per phase,
 // builds the FFT plans, twiddles and the Gamma^h table, and carves every
 // device buffer out of the caller's workspace.  Solves drive the operator
-// passes of kernels.cu from the host: each CG iteration is six launches whose
-// scalars (alpha, beta, (r,r)) stay on the device; the host reads the device
-// state only every `check_every` iterations.
+// passes of kernels.cu from the host: each CG iteration is six launches that
+// advance all systems of a wave (microstructure x load) together; the CG
+// scalars stay on the device and the host reads the per-system states only
+// every `check_every` iterations.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -77,6 +78,8 @@ template <typename T> void twiddles(int n, std::vector<T>& out) {
 // ---------------------------------------------------------------- derived problem data
 struct Derived {
   int dim, c, nx, ny, nz, nxh, ncoef, physics, green, precision, nphase;
+  int B;       // microstructures
+  int Smax;    // systems per wave
   long long V;
   bool has_scale;
   Plan1D px, py, pz;
@@ -110,6 +113,10 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
   d->nxh = d->nx / 2 + 1;
   d->c = pr->physics == LSH_ELASTIC_ISO ? 6 : pr->dim;
   d->ncoef = d->c * (d->c + 1) / 2;
+  d->B = pr->nbatch > 1 ? pr->nbatch : 1;
+  d->Smax = d->B * d->c;
+  if (pr->max_systems > 0) d->Smax = std::min(d->Smax, pr->max_systems);
+  if ((long long)d->Smax * d->c * d->nz > 65535LL || (long long)d->B * d->V > (1LL << 40)) return LSH_ERR_UNSUPPORTED_SIZE;
   d->has_scale = pr->scale != nullptr;
   if (!make_plan(d->nx, &d->px) || !make_plan(d->ny, &d->py) || !make_plan(d->nz, &d->pz))
     return LSH_ERR_UNSUPPORTED_SIZE;
@@ -169,8 +176,8 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
       for (int i = 0; i < dim; ++i) md[i] = pr->phase_moduli[ph * dim * dim + i * dim + i];
     }
     if (d->has_scale) {
-      // the scale field makes every voxel of an active phase active; the sign
-      // structure is the caller's responsibility (A0 softer than s A_phase)
+      // with a scale field every voxel is in I0; the sign structure of
+      // s A_phase - A0 is the caller's responsibility (A0 softer than all)
       d->act[ph] = 1;
       pos = true;
       continue;
@@ -195,62 +202,62 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
   return LSH_OK;
 }
 
-// ---------------------------------------------------------------- workspace layout
-template <typename T> struct PrecBufs {
-  T *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
-  C2<T>* H = nullptr;
-  T* gtab = nullptr;
-  C2<T>*twx = nullptr, *twy = nullptr, *twz = nullptr;
-  T *mtab = nullptr, *modtab = nullptr;
-  SolverState* st = nullptr;
-  LaunchCfg L{};
-  OpArgs<T> a{};
-};
-
-struct Layout {
-  size_t off_state, off_partials, off_phase, off_scale, off_act, off_posx, off_kofy, off_kofz, off_sums, off_W;
-  size_t off_tabd, off_tabf;  // per-phase tables (mtab, modtab) for each precision
-  size_t off_tw_d, off_tw_f;
-  size_t off_fd[4], off_Hd, off_gd;
-  size_t off_ff[4], off_Hf, off_gf;
-  size_t total;
-  int nparts;
-};
+// ---------------------------------------------------------------- launch configuration
+int choose_ry(int rps, int lsx, size_t cs, int S) {
+  int target = std::max(2, 2 * (int)(32768 / (lsx * cs)));
+  // keep at least ~4 blocks per SM in flight for small problems
+  target = std::min(target, std::max(2, (int)((long long)rps * S / 608)));
+  if (target >= rps) return rps;
+  int best = 1;
+  for (int d = target; d >= 1; --d)
+    if (rps % d == 0) {
+      if (d % 2 == 0) return d;
+      if (best == 1) best = d;
+    }
+  return best;
+}
 
 template <typename T> LaunchCfg make_cfg(const Derived& d) {
   LaunchCfg L{};
   L.threads = kThreads;
   const size_t cs = sizeof(C2<T>);
   const int lsx = d.nx | 1, lsy = d.ny | 1, lsz = d.nz | 1;
-  const int nrows = d.c * d.nz * d.ny;
-  int npair = std::max(1, (int)(32768 / (lsx * cs)));
-  int RY = 2 * npair;
-  RY = std::min(RY, nrows + (nrows & 1));
-  L.smem_x = d.nx * cs + (size_t)(RY / 2) * lsx * cs + d.nx * sizeof(int);
-  int TY = sizeof(T) == 8 ? 8 : 16;
-  TY = std::min(TY, d.nxh);
-  L.smem_y = d.ny * cs + (size_t)TY * lsy * cs;
-  int TZ = sizeof(T) == 8 ? 8 : 16;
-  TZ = std::min(TZ, d.nxh);
+  const int rps = d.c * d.nz * d.ny;
+  L.RY = choose_ry(rps, lsx, cs, d.Smax);
+  L.VEC = (d.nx % (16 / (int)sizeof(T)) == 0) ? 16 / (int)sizeof(T) : 1;
+  L.smem_x = d.nx * cs + (size_t)((L.RY + 1) / 2) * lsx * cs + d.nx * sizeof(int);
+  L.TY = std::min(sizeof(T) == 8 ? 8 : 16, d.nxh);
+  L.smem_y = d.ny * cs + (size_t)L.TY * lsy * cs;
+  int TZ = std::min(8, d.nxh);
   while (TZ > 1 && (size_t)d.c * TZ * lsz * cs > 100 * 1024) TZ /= 2;
+  L.TZ = TZ;
   L.smem_z = d.nz * cs + (size_t)d.c * TZ * lsz * cs;
-  L.grid_x = (nrows + RY - 1) / RY;
-  L.grid_yx = (d.nxh + TY - 1) / TY;
-  L.grid_yy = d.c * d.nz;
+  L.grid_x = rps / L.RY;  // per system
+  L.grid_yx = (d.nxh + L.TY - 1) / L.TY;
+  L.grid_yy = d.c * d.nz;  // per system
   L.grid_zx = (d.nxh + TZ - 1) / TZ;
   L.grid_zy = d.ny;
   const long long n = (long long)d.c * d.V;
-  L.grid_ew = (int)std::max(1LL, std::min((n + kThreads - 1) / kThreads, 152LL * 8));
-  L.RY = RY;
-  L.TY = TY;
-  L.TZ = TZ;
+  const long long want = (n + kThreads * 8 - 1) / (kThreads * 8);
+  L.ew_per_sys = (int)std::max(1LL, std::min(want, std::max(1LL, 2432LL / d.Smax)));
   return L;
 }
 
-template <typename T> bool cfg_fits(const LaunchCfg& L) {
+bool cfg_fits(const LaunchCfg& L) {
   return L.smem_x <= (size_t)kMaxSmem && L.smem_y <= (size_t)kMaxSmem && L.smem_z <= (size_t)kMaxSmem &&
-         L.grid_yy <= 65535 && L.grid_zy <= 65535;
+         L.grid_zy <= 65535;
 }
+
+// ---------------------------------------------------------------- workspace layout
+struct Layout {
+  size_t off_state, off_partials, off_phase, off_scale, off_act, off_posx, off_kofy, off_kofz, off_sums, off_W;
+  size_t off_tabd, off_tabf, off_loads_d, off_loads_f, off_bb, off_flags;
+  size_t off_tw_d, off_tw_f;
+  size_t off_fd[4], off_Hd, off_gd;
+  size_t off_ff[4], off_Hf, off_gf;
+  size_t total;
+  long long nparts;
+};
 
 Layout make_layout(const Derived& d) {
   Layout l{};
@@ -260,36 +267,60 @@ Layout make_layout(const Derived& d) {
     o = align_up(o + bytes);
     return at;
   };
-  const long long n = (long long)d.c * d.V;
+  const int S = d.Smax;
+  const long long n = (long long)d.c * d.V;  // elements per system
   const long long nf = (long long)d.nz * d.ny * d.nxh;
   LaunchCfg Ld = make_cfg<double>(d), Lf = make_cfg<float>(d);
-  int np = std::max({Ld.grid_x, Ld.grid_ew, Lf.grid_x, Lf.grid_ew, 152 * 8 * 6});
+  long long np = std::max<long long>({(long long)S * Ld.grid_x, (long long)S * Lf.grid_x, (long long)S * Ld.ew_per_sys,
+                                      (long long)S * Lf.ew_per_sys, (long long)S * d.c * 152,
+                                      (long long)d.B * 1216});
   l.nparts = np;
-  l.off_state = take(sizeof(SolverState) * 4);
-  l.off_partials = take(sizeof(double) * 2 * (size_t)np);
-  l.off_phase = take((size_t)d.V);
-  l.off_scale = take(d.has_scale ? sizeof(float) * (size_t)d.V : 0);
+  l.off_state = take(sizeof(SolverState) * (size_t)(3 * S + d.B));
+  l.off_partials = take(sizeof(double) * (size_t)np);
+  l.off_phase = take((size_t)(d.B * d.V));
+  l.off_scale = take(d.has_scale ? sizeof(float) * (size_t)(d.B * d.V) : 0);
   l.off_act = take(256);
   l.off_posx = take(sizeof(int) * d.nx);
   l.off_kofy = take(sizeof(int) * d.ny);
   l.off_kofz = take(sizeof(int) * d.nz);
-  l.off_sums = take(sizeof(double) * 64);
+  l.off_sums = take(sizeof(double) * (size_t)S * d.c);
   l.off_W = take(sizeof(double) * 64);
   l.off_tabd = take(sizeof(double) * 2 * 256 * 6);
   l.off_tabf = take(sizeof(float) * 2 * 256 * 6);
+  l.off_loads_d = take(sizeof(double) * 6 * (size_t)S);
+  l.off_loads_f = take(sizeof(float) * 6 * (size_t)S);
+  l.off_bb = take(sizeof(double) * (size_t)S);
+  l.off_flags = take((size_t)S);
   l.off_tw_d = take(sizeof(double2) * (size_t)(d.nx + d.ny + d.nz));
   l.off_tw_f = take(sizeof(float2) * (size_t)(d.nx + d.ny + d.nz));
-  for (int i = 0; i < 4; ++i) l.off_fd[i] = take(sizeof(double) * (size_t)n);
-  l.off_Hd = take(sizeof(double2) * (size_t)(d.c * nf));
+  // FP64 fields: x, r always; p, q for the FP64 CG (one system's worth of p, q
+  // suffices for the Mandel rotations of lsh_apply on a mixed handle)
+  const bool mixed = d.precision == LSH_MIXED;
+  for (int i = 0; i < 4; ++i) {
+    const long long ns = (i < 2 || !mixed) ? S : 1;
+    l.off_fd[i] = take(sizeof(double) * (size_t)(ns * n));
+  }
+  l.off_Hd = take(sizeof(double2) * (size_t)(S * d.c * nf));
   l.off_gd = take(sizeof(double) * (size_t)(d.ncoef * nf));
-  if (d.precision == LSH_MIXED) {
-    for (int i = 0; i < 4; ++i) l.off_ff[i] = take(sizeof(float) * (size_t)n);
-    l.off_Hf = take(sizeof(float2) * (size_t)(d.c * nf));
+  if (mixed) {
+    for (int i = 0; i < 4; ++i) l.off_ff[i] = take(sizeof(float) * (size_t)(S * n));
+    l.off_Hf = take(sizeof(float2) * (size_t)(S * d.c * nf));
     l.off_gf = take(sizeof(float) * (size_t)(d.ncoef * nf));
   }
   l.total = o;
   return l;
 }
+
+template <typename T> struct PrecBufs {
+  T *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr;
+  C2<T>* H = nullptr;
+  T* gtab = nullptr;
+  C2<T>*twx = nullptr, *twy = nullptr, *twz = nullptr;
+  T *mtab = nullptr, *modtab = nullptr, *loads = nullptr;
+  SolverState* st = nullptr;  // Smax CG states
+  LaunchCfg L{};
+  OpArgs<T> a{};
+};
 
 }  // namespace
 
@@ -299,17 +330,15 @@ struct lsh_handle {
   Layout lay;
   cudaStream_t stream;
   unsigned char* base;
-  SolverState* st;  // [0] FP64 CG, [1] FP32 CG, [2] residual / scratch, [3] setup scan
+  SolverState* st;      // [0,S) FP64 CG, [S,2S) FP32 CG, [2S,3S) residual, [3S,3S+B) setup scan
   double* partials;
-  unsigned char *phase, *act;
+  unsigned char *phase, *act, *flags;
   float* scale;
   int *posx, *kofy, *kofz;
-  double* sums;
-  double* Wdev;
-  double* tabd;  // mtab (256*6) then modtab (256*6)
+  double *sums, *Wdev, *tabd, *bbdev;
   PrecBufs<double> pd;
   PrecBufs<float> pf;
-  long long n_active;
+  std::vector<long long> n_active;  // voxels in I0 per microstructure
   // diagnostics
   long long launches = 0;
   bool prof = false;
@@ -344,7 +373,7 @@ template <> PrecBufs<float>& bufs<float>(lsh_handle* h) { return h->pf; }
 
 template <typename T>
 void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H, size_t off_g, size_t off_tw,
-               size_t off_tab, SolverState* st) {
+               size_t off_tab, size_t off_loads, SolverState* st) {
   const Derived& d = h->d;
   unsigned char* b = h->base;
   P.x = (T*)(b + off_f[0]);
@@ -358,6 +387,7 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   P.twz = P.twy + d.ny;
   P.mtab = (T*)(b + off_tab);
   P.modtab = P.mtab + 256 * 6;
+  P.loads = (T*)(b + off_loads);
   P.st = st;
   P.L = make_cfg<T>(d);
   OpArgs<T>& a = P.a;
@@ -367,13 +397,17 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.nxh = d.nxh;
   a.c = d.c;
   a.V = d.V;
-  a.nrows = d.c * d.nz * d.ny;
+  a.S = d.Smax;
+  a.sys0 = 0;
+  a.sys_per_ms = d.c;
+  a.rps = d.c * d.nz * d.ny;
+  a.RY = P.L.RY;
+  a.bps = a.rps / a.RY;
+  a.TY = P.L.TY;
+  a.TZ = P.L.TZ;
   a.lsx = d.nx | 1;
   a.lsy = d.ny | 1;
   a.lsz = d.nz | 1;
-  a.RY = P.L.RY;
-  a.TY = P.L.TY;
-  a.TZ = P.L.TZ;
   a.px = d.px;
   a.py = d.py;
   a.pz = d.pz;
@@ -389,10 +423,8 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.act = h->act;
   a.mtab = P.mtab;
   a.modtab = P.modtab;
-  for (int i = 0; i < 6; ++i) {
-    a.ref[i] = (T)(i < d.c ? d.ref_in[i] : 0.0);
-    a.load[i] = (T)0;
-  }
+  for (int i = 0; i < 6; ++i) a.ref[i] = (T)(i < d.c ? d.ref_in[i] : 0.0);
+  a.loads = P.loads;
 }
 
 // internal basis <-> Mandel for elasticity (see k_rotate)
@@ -429,57 +461,84 @@ void ref_matrix(const Derived& d, double* A0) {
   }
 }
 
-lsh_status read_state(lsh_handle* h, int idx, SolverState* out) {
-  LSH_CK(cudaMemcpyAsync(out, h->st + idx, sizeof(SolverState), cudaMemcpyDeviceToHost, h->stream));
+lsh_status read_states(lsh_handle* h, const SolverState* dev, int n, SolverState* out) {
+  LSH_CK(cudaMemcpyAsync(out, dev, sizeof(SolverState) * n, cudaMemcpyDeviceToHost, h->stream));
   LSH_CK(cudaStreamSynchronize(h->stream));
   return LSH_OK;
 }
 
+// A wave: S systems starting at global system sys0, sys_per_ms systems per
+// microstructure; loads (internal basis) per system.
+struct Wave {
+  int S, sys0, sys_per_ms;
+  const double* loads;  // host [S][6]
+};
+
+template <typename T> OpArgs<T> wave_args(lsh_handle* h, const Wave& w) {
+  OpArgs<T> a = bufs<T>(h).a;
+  a.S = w.S;
+  a.sys0 = w.sys0;
+  a.sys_per_ms = w.sys_per_ms;
+  return a;
+}
+
+lsh_status upload_loads(lsh_handle* h, const Wave& w) {
+  std::vector<double> ld(6 * (size_t)w.S);
+  std::vector<float> lf(6 * (size_t)w.S);
+  for (size_t i = 0; i < ld.size(); ++i) {
+    ld[i] = w.loads[i];
+    lf[i] = (float)w.loads[i];
+  }
+  LSH_CK(cudaMemcpyAsync(h->pd.loads, ld.data(), sizeof(double) * ld.size(), cudaMemcpyHostToDevice, h->stream));
+  if (h->d.precision == LSH_MIXED)
+    LSH_CK(cudaMemcpyAsync(h->pf.loads, lf.data(), sizeof(float) * lf.size(), cudaMemcpyHostToDevice, h->stream));
+  return LSH_OK;
+}
+
 // ---------------------------------------------------------------- operator sequences
-// out = K in (both in the internal basis), precision T.
-template <typename T> lsh_status apply_internal(lsh_handle* h, const T* in, T* out) {
+// out = K in (internal basis), precision T, for the systems of `a`.
+template <typename T> lsh_status apply_internal(lsh_handle* h, const OpArgs<T>& a, const T* in, T* out) {
   PrecBufs<T>& P = bufs<T>(h);
   cudaStream_t s = h->stream;
-  launch_xfwd<T>(P.a, P.L, 0, in, nullptr, nullptr, nullptr, nullptr, s);
-  launch_yfft<T>(P.a, P.L, false, nullptr, s);
-  launch_zgamma<T>(P.a, P.L, nullptr, s);
-  launch_yfft<T>(P.a, P.L, true, nullptr, s);
-  launch_xinv<T>(P.a, P.L, 0, in, out, nullptr, nullptr, s);
+  launch_xfwd<T>(a, P.L, 0, in, nullptr, nullptr, nullptr, nullptr, s);
+  launch_yfft<T>(a, P.L, false, nullptr, s);
+  launch_zgamma<T>(a, P.L, nullptr, s);
+  launch_yfft<T>(a, P.L, true, nullptr, s);
+  launch_xinv<T>(a, P.L, 0, in, out, nullptr, nullptr, s);
   h->launches += 5;
   return last_launch();
 }
 
-// r = b - K x in FP64, (r, r) -> st[2].aux[0]
-lsh_status residual64(lsh_handle* h, const double* load_in, const double* x, double* r) {
+// r = b - K x in FP64 for the wave, (r, r) -> residual states' aux[0]
+lsh_status residual64(lsh_handle* h, const OpArgs<double>& a, const double* x, double* r) {
   PrecBufs<double>& P = h->pd;
   cudaStream_t s = h->stream;
-  OpArgs<double> a = P.a;
-  for (int i = 0; i < 6; ++i) a.load[i] = i < h->d.c ? load_in[i] : 0.0;
+  SolverState* sres = h->st + 2 * h->d.Smax;
   launch_xfwd<double>(a, P.L, 0, x, nullptr, nullptr, nullptr, nullptr, s);
   launch_yfft<double>(a, P.L, false, nullptr, s);
   launch_zgamma<double>(a, P.L, nullptr, s);
   launch_yfft<double>(a, P.L, true, nullptr, s);
-  launch_xinv<double>(a, P.L, 2, x, r, h->st + 2, h->partials, s);
+  launch_xinv<double>(a, P.L, 2, x, r, sres, h->partials, s);
   h->launches += 5;
   return last_launch();
 }
 
-template <typename T> void enqueue_cg_iteration(lsh_handle* h, PrecBufs<T>& P) {
+template <typename T> void enqueue_cg_iteration(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a) {
   cudaStream_t s = h->stream;
   const bool timed = h->prof && h->ev_used + 7 <= (int)h->ev.size();
   cudaEvent_t* e = timed ? &h->ev[h->ev_used] : nullptr;
   if (timed) cudaEventRecord(e[0], s);
-  launch_xfwd<T>(P.a, P.L, 1, nullptr, P.x, P.r, P.p, P.st, s);
+  launch_xfwd<T>(a, P.L, 1, nullptr, P.x, P.r, P.p, P.st, s);
   if (timed) cudaEventRecord(e[1], s);
-  launch_yfft<T>(P.a, P.L, false, P.st, s);
+  launch_yfft<T>(a, P.L, false, P.st, s);
   if (timed) cudaEventRecord(e[2], s);
-  launch_zgamma<T>(P.a, P.L, P.st, s);
+  launch_zgamma<T>(a, P.L, P.st, s);
   if (timed) cudaEventRecord(e[3], s);
-  launch_yfft<T>(P.a, P.L, true, P.st, s);
+  launch_yfft<T>(a, P.L, true, P.st, s);
   if (timed) cudaEventRecord(e[4], s);
-  launch_xinv<T>(P.a, P.L, 1, P.p, P.q, P.st, h->partials, s);
+  launch_xinv<T>(a, P.L, 1, P.p, P.q, P.st, h->partials, s);
   if (timed) cudaEventRecord(e[5], s);
-  launch_cg_update<T>(P.r, P.q, (long long)h->d.c * h->d.V, P.st, h->partials, P.L.grid_ew, s);
+  launch_cg_update<T>(P.r, P.q, (long long)a.c * a.V, a.S, P.st, h->partials, P.L.ew_per_sys, s);
   if (timed) {
     cudaEventRecord(e[6], s);
     h->ev_used += 7;
@@ -488,7 +547,8 @@ template <typename T> void enqueue_cg_iteration(lsh_handle* h, PrecBufs<T>& P) {
 }
 
 // After a host synchronisation: add the pass times of the first `real`
-// recorded iterations (later ones returned at once because the solve was done).
+// recorded iterations (later ones returned at once because every system of
+// the wave was done).
 void harvest_profile(lsh_handle* h, int real) {
   const int groups = h->ev_used / 7;
   for (int g = 0; g < groups && g < real; ++g) {
@@ -505,132 +565,192 @@ void harvest_profile(lsh_handle* h, int real) {
   h->ev_used = 0;
 }
 
-// CG on the state already begun in P.st; finalises x.  Returns the state.
+// CG on the states already begun for the wave; finalises x.  `out` receives
+// the S states.
 template <typename T>
-lsh_status cg_run(lsh_handle* h, PrecBufs<T>& P, int maxit, int check_every, SolverState* out) {
-  int idx = (P.st == h->st) ? 0 : 1;
-  lsh_status stt = read_state(h, idx, out);
+lsh_status cg_run(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int maxit, int check_every,
+                  std::vector<SolverState>& out) {
+  const int S = a.S;
+  out.resize(S);
+  lsh_status stt = read_states(h, P.st, S, out.data());
   if (stt) return stt;
+  auto all_done = [&]() {
+    for (int s = 0; s < S; ++s)
+      if (!out[s].done) return false;
+    return true;
+  };
+  auto max_iter = [&]() {
+    int m = 0;
+    for (int s = 0; s < S; ++s) m = std::max(m, out[s].iter);
+    return m;
+  };
   int it = 0;
-  while (!out->done && it < maxit) {
+  while (!all_done() && it < maxit) {
     const int chunk = std::min(check_every, maxit - it);
-    const int before = out->iter;
-    for (int j = 0; j < chunk; ++j) enqueue_cg_iteration<T>(h, P);
+    const int before = max_iter();
+    for (int j = 0; j < chunk; ++j) enqueue_cg_iteration<T>(h, P, a);
     if ((stt = last_launch())) return stt;
     it += chunk;
-    if ((stt = read_state(h, idx, out))) return stt;
-    if (h->prof) harvest_profile(h, out->iter - before);
+    if ((stt = read_states(h, P.st, S, out.data()))) return stt;
+    if (h->prof) harvest_profile(h, max_iter() - before);
   }
-  launch_cg_finalize<T>(P.x, P.p, (long long)h->d.c * h->d.V, P.st, P.L.grid_ew, h->stream);
+  launch_cg_finalize<T>(P.x, P.p, (long long)a.c * a.V, S, P.st, P.L.ew_per_sys, h->stream);
   h->launches += 1;
   if ((stt = last_launch())) return stt;
-  return read_state(h, idx, out);
+  return read_states(h, P.st, S, out.data());
 }
 
-lsh_status solve_internal(lsh_handle* h, const double* load_in, bool warm, const lsh_solve_opts* o,
-                          lsh_solve_info* info) {
+// Solve the systems of a wave; the solutions end in pd.x (internal basis).
+// warm: pd.x holds initial guesses.  infos: S entries.
+lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_opts* o, lsh_solve_info* infos) {
   const Derived& d = h->d;
+  const int S = w.S;
   const long long n = (long long)d.c * d.V;
-  double tol = o && o->tol > 0 ? o->tol : 1e-10;
-  int maxit = o && o->maxit > 0 ? o->maxit : 10000;
-  int check = o && o->check_every > 0 ? o->check_every : 8;
-  double lb = 0.0;
-  for (int i = 0; i < d.c; ++i) lb += load_in[i] * load_in[i];
-  const double bb = (double)h->n_active * lb;
-  lsh_solve_info inf{};
-  PrecBufs<double>& Pd = h->pd;
+  const double tol = o && o->tol > 0 ? o->tol : 1e-10;
+  const int maxit = o && o->maxit > 0 ? o->maxit : 10000;
+  const int check = o && o->check_every > 0 ? o->check_every : 8;
   lsh_status stt;
+  if ((stt = upload_loads(h, w))) return stt;
+  // (b, b) per system = |load|^2 x (voxels in I0 of its microstructure)
+  std::vector<double> bb(S);
+  for (int s = 0; s < S; ++s) {
+    double lb = 0.0;
+    for (int i = 0; i < d.c; ++i) lb += w.loads[6 * s + i] * w.loads[6 * s + i];
+    bb[s] = lb * (double)h->n_active[(w.sys0 + s) / w.sys_per_ms];
+  }
+  LSH_CK(cudaMemcpyAsync(h->bbdev, bb.data(), sizeof(double) * S, cudaMemcpyHostToDevice, h->stream));
+  for (int s = 0; s < S; ++s) infos[s] = lsh_solve_info{};
+  PrecBufs<double>& Pd = h->pd;
+  const OpArgs<double> ad = wave_args<double>(h, w);
+  const int G = Pd.L.ew_per_sys;
+  std::vector<SolverState> st;
   if (d.precision == LSH_FP64) {
     if (!warm) {
-      OpArgs<double> a = Pd.a;
-      for (int i = 0; i < 6; ++i) a.load[i] = i < d.c ? load_in[i] : 0.0;
-      launch_fill_rhs<double>(a, Pd.r, Pd.x, Pd.L.grid_ew, h->stream);
-      launch_cg_begin<double>(Pd.r, n, Pd.st, h->partials, tol, -1.0, Pd.L.grid_ew, h->stream);
+      launch_fill_rhs<double>(ad, Pd.r, Pd.x, G, h->stream);
+      launch_cg_begin<double>(Pd.r, n, S, Pd.st, h->partials, tol, h->bbdev, G, h->stream);
       h->launches += 2;
     } else {
-      if ((stt = residual64(h, load_in, Pd.x, Pd.r))) return stt;
-      inf.applies64 += 1;
-      launch_cg_begin<double>(Pd.r, n, Pd.st, h->partials, tol, bb, Pd.L.grid_ew, h->stream);
+      if ((stt = residual64(h, ad, Pd.x, Pd.r))) return stt;
+      for (int s = 0; s < S; ++s) infos[s].applies64 += 1;
+      launch_cg_begin<double>(Pd.r, n, S, Pd.st, h->partials, tol, h->bbdev, G, h->stream);
       h->launches += 1;
     }
     if ((stt = last_launch())) return stt;
-    SolverState s;
-    if ((stt = cg_run<double>(h, Pd, maxit, check, &s))) return stt;
-    inf.iters = s.iter;
-    inf.applies64 += s.iter;
-    inf.relres = s.bb > 0 ? std::sqrt(std::max(s.rr, 0.0) / s.bb) : 0.0;
-    inf.status = s.status ? s.status : (s.done ? LSH_OK : LSH_ERR_NOT_CONVERGED);
+    if ((stt = cg_run<double>(h, Pd, ad, maxit, check, st))) return stt;
+    for (int s = 0; s < S; ++s) {
+      infos[s].iters = st[s].iter;
+      infos[s].applies64 += st[s].iter;
+      infos[s].relres = st[s].bb > 0 ? std::sqrt(std::max(st[s].rr, 0.0) / st[s].bb) : 0.0;
+      infos[s].status = st[s].status ? st[s].status : (st[s].done ? LSH_OK : LSH_ERR_NOT_CONVERGED);
+    }
   } else {
     // mixed precision: iterative refinement, FP64 residual, FP32 inner CG
     PrecBufs<float>& Pf = h->pf;
+    const OpArgs<float> af = wave_args<float>(h, w);
     const double itol = o && o->inner_tol > 0 ? o->inner_tol : 1e-4;
     const int max_outer = o && o->max_outer > 0 ? o->max_outer : 30;
-    double rr;
+    std::vector<double> rr(S);
+    SolverState* sres = h->st + 2 * d.Smax;
     if (!warm) {
-      OpArgs<double> a = Pd.a;
-      for (int i = 0; i < 6; ++i) a.load[i] = i < d.c ? load_in[i] : 0.0;
-      launch_fill_rhs<double>(a, Pd.r, Pd.x, Pd.L.grid_ew, h->stream);
+      launch_fill_rhs<double>(ad, Pd.r, Pd.x, G, h->stream);
       h->launches += 1;
       rr = bb;
     } else {
-      if ((stt = residual64(h, load_in, Pd.x, Pd.r))) return stt;
-      inf.applies64 += 1;
-      SolverState s2;
-      if ((stt = read_state(h, 2, &s2))) return stt;
-      rr = s2.aux[0];
+      if ((stt = residual64(h, ad, Pd.x, Pd.r))) return stt;
+      for (int s = 0; s < S; ++s) infos[s].applies64 += 1;
+      std::vector<SolverState> s2(S);
+      if ((stt = read_states(h, sres, S, s2.data()))) return stt;
+      for (int s = 0; s < S; ++s) rr[s] = s2[s].aux[0];
     }
     if ((stt = last_launch())) return stt;
-    int total = 0, outer = 0, status = LSH_OK;
-    double prev = rr;
-    while (rr > tol * tol * bb) {
-      if (outer >= max_outer || total >= maxit) { status = LSH_ERR_NOT_CONVERGED; break; }
-      launch_d2f_begin(Pd.r, Pf.r, Pf.x, n, Pf.st, h->partials, itol, Pf.L.grid_ew, h->stream);
+    std::vector<unsigned char> active(S);
+    std::vector<double> prev = rr;
+    std::vector<int> total(S, 0), stall(S, 0);
+    int outer = 0, total_max = 0;
+    for (;;) {
+      int nact = 0;
+      for (int s = 0; s < S; ++s) {
+        const bool conv = rr[s] <= tol * tol * bb[s];
+        const bool failed = infos[s].status != LSH_OK;
+        active[s] = (!conv && !failed) ? 1 : 0;
+        nact += active[s];
+      }
+      if (nact == 0) break;
+      if (outer >= max_outer || total_max >= maxit) {
+        for (int s = 0; s < S; ++s)
+          if (active[s]) infos[s].status = LSH_ERR_NOT_CONVERGED;
+        break;
+      }
+      LSH_CK(cudaMemcpyAsync(h->flags, active.data(), S, cudaMemcpyHostToDevice, h->stream));
+      launch_d2f_begin(Pd.r, Pf.r, Pf.x, n, S, Pf.st, h->partials, itol, h->flags, Pf.L.ew_per_sys, h->stream);
       h->launches += 1;
-      SolverState s;
-      if ((stt = cg_run<float>(h, Pf, maxit - total, check, &s))) return stt;
-      total += s.iter;
-      launch_f2d_axpy(Pd.x, Pf.x, n, Pd.L.grid_ew, h->stream);
+      if ((stt = cg_run<float>(h, Pf, af, maxit - total_max, check, st))) return stt;
+      launch_f2d_axpy(Pd.x, Pf.x, n * S, h->stream);
       h->launches += 1;
-      if ((stt = residual64(h, load_in, Pd.x, Pd.r))) return stt;
-      inf.applies64 += 1;
-      SolverState s2;
-      if ((stt = read_state(h, 2, &s2))) return stt;
-      rr = s2.aux[0];
+      if ((stt = residual64(h, ad, Pd.x, Pd.r))) return stt;
+      std::vector<SolverState> s2(S);
+      if ((stt = read_states(h, sres, S, s2.data()))) return stt;
       ++outer;
-      if (s.status == LSH_ERR_BREAKDOWN && rr >= prev) { status = LSH_ERR_BREAKDOWN; break; }
-      if (!(rr < prev) && s.iter == 0) { status = LSH_ERR_NOT_CONVERGED; break; }
-      prev = rr;
+      for (int s = 0; s < S; ++s) {
+        if (!active[s]) continue;
+        infos[s].applies64 += 1;
+        infos[s].outer += 1;
+        total[s] += st[s].iter;
+        total_max = std::max(total_max, total[s]);
+        rr[s] = s2[s].aux[0];
+        if (st[s].status == LSH_ERR_BREAKDOWN && rr[s] >= prev[s]) infos[s].status = LSH_ERR_BREAKDOWN;
+        // refinement that stops reducing the true residual has reached the
+        // attainable accuracy of the inner solver: give up after 3 such steps
+        if (!(rr[s] < 0.5 * prev[s])) {
+          if (++stall[s] >= 3) infos[s].status = LSH_ERR_NOT_CONVERGED;
+        }
+        prev[s] = rr[s];
+      }
     }
-    inf.iters = total;
-    inf.outer = outer;
-    inf.relres = bb > 0 ? std::sqrt(std::max(rr, 0.0) / bb) : 0.0;
-    inf.status = status;
+    for (int s = 0; s < S; ++s) {
+      infos[s].iters = total[s];
+      infos[s].relres = bb[s] > 0 ? std::sqrt(std::max(rr[s], 0.0) / bb[s]) : 0.0;
+    }
   }
-  if (info) *info = inf;
-  return (lsh_status)inf.status;
+  return LSH_OK;
 }
 
 lsh_status scan_microstructure(lsh_handle* h) {
-  SolverState zero{};
-  LSH_CK(cudaMemcpyAsync(h->st + 3, &zero, sizeof(zero), cudaMemcpyHostToDevice, h->stream));
-  launch_scan_phase(h->phase, h->d.V, h->act, h->d.nphase, h->st + 3, h->partials,
-                    (int)std::min<long long>((h->d.V + kThreads - 1) / kThreads, 152 * 8), h->stream);
+  const Derived& d = h->d;
+  SolverState* sscan = h->st + 3 * d.Smax;
+  std::vector<SolverState> zero(d.B);
+  LSH_CK(cudaMemcpyAsync(sscan, zero.data(), sizeof(SolverState) * d.B, cudaMemcpyHostToDevice, h->stream));
+  const int G = (int)std::max(1LL, std::min((d.V + kThreads - 1) / kThreads, 1216LL));
+  launch_scan_phase(h->phase, d.V, d.B, h->act, d.nphase, sscan, h->partials, G, h->stream);
   lsh_status stt = last_launch();
   if (stt) return stt;
-  SolverState s;
-  if ((stt = read_state(h, 3, &s))) return stt;
-  if (s.pad >= h->d.nphase) return LSH_ERR_INVALID_ARG;
-  h->n_active = (long long)s.aux[1];
+  std::vector<SolverState> s(d.B);
+  if ((stt = read_states(h, sscan, d.B, s.data()))) return stt;
+  if (s[0].pad >= d.nphase) return LSH_ERR_INVALID_ARG;
+  h->n_active.resize(d.B);
+  for (int b = 0; b < d.B; ++b) h->n_active[b] = (long long)s[b].aux[1];
   return LSH_OK;
 }
 
 lsh_status copy_microstructure(lsh_handle* h, const unsigned char* phase, const float* scale, int on_host) {
   const cudaMemcpyKind k = on_host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
-  LSH_CK(cudaMemcpyAsync(h->phase, phase, (size_t)h->d.V, k, h->stream));
+  const size_t nv = (size_t)(h->d.B * h->d.V);
+  LSH_CK(cudaMemcpyAsync(h->phase, phase, nv, k, h->stream));
   if (h->d.has_scale) {
     if (!scale) return LSH_ERR_INVALID_ARG;
-    LSH_CK(cudaMemcpyAsync(h->scale, scale, sizeof(float) * (size_t)h->d.V, k, h->stream));
+    LSH_CK(cudaMemcpyAsync(h->scale, scale, sizeof(float) * nv, k, h->stream));
   }
+  return LSH_OK;
+}
+
+lsh_status rotate_or_copy(lsh_handle* h, const double* in, double* out, int nsys, int to_internal) {
+  const Derived& d = h->d;
+  if (d.physics == LSH_ELASTIC_ISO) {
+    launch_rotate<double>(in, out, d.V, nsys, to_internal, h->stream);
+    h->launches += 1;
+    return last_launch();
+  }
+  if (in != out) LSH_CK(cudaMemcpyAsync(out, in, sizeof(double) * d.c * d.V * nsys, cudaMemcpyDeviceToDevice, h->stream));
   return LSH_OK;
 }
 
@@ -660,8 +780,7 @@ lsh_status lsh_workspace_size(const lsh_problem* prob, size_t* bytes) {
   Derived d;
   lsh_status s = derive(prob, &d);
   if (s) return s;
-  if (!cfg_fits<double>(make_cfg<double>(d)) || !cfg_fits<float>(make_cfg<float>(d)))
-    return LSH_ERR_UNSUPPORTED_SIZE;
+  if (!cfg_fits(make_cfg<double>(d)) || !cfg_fits(make_cfg<float>(d))) return LSH_ERR_UNSUPPORTED_SIZE;
   *bytes = make_layout(d).total;
   return LSH_OK;
 }
@@ -674,7 +793,7 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   lsh_status s = derive(prob, &h->d);
   if (s) { delete h; return s; }
   Derived& d = h->d;
-  if (!cfg_fits<double>(make_cfg<double>(d)) || !cfg_fits<float>(make_cfg<float>(d))) {
+  if (!cfg_fits(make_cfg<double>(d)) || !cfg_fits(make_cfg<float>(d))) {
     delete h;
     return LSH_ERR_UNSUPPORTED_SIZE;
   }
@@ -694,8 +813,11 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   h->sums = (double*)(h->base + l.off_sums);
   h->Wdev = (double*)(h->base + l.off_W);
   h->tabd = (double*)(h->base + l.off_tabd);
-  init_prec<double>(h, h->pd, l.off_fd, l.off_Hd, l.off_gd, l.off_tw_d, l.off_tabd, h->st + 0);
-  if (d.precision == LSH_MIXED) init_prec<float>(h, h->pf, l.off_ff, l.off_Hf, l.off_gf, l.off_tw_f, l.off_tabf, h->st + 1);
+  h->bbdev = (double*)(h->base + l.off_bb);
+  h->flags = h->base + l.off_flags;
+  init_prec<double>(h, h->pd, l.off_fd, l.off_Hd, l.off_gd, l.off_tw_d, l.off_tabd, l.off_loads_d, h->st);
+  if (d.precision == LSH_MIXED)
+    init_prec<float>(h, h->pf, l.off_ff, l.off_Hf, l.off_gf, l.off_tw_f, l.off_tabf, l.off_loads_f, h->st + d.Smax);
 
   // host tables
   std::vector<int> posx(d.nx), kofy(d.ny), kofz(d.nz);
@@ -718,9 +840,9 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   for (size_t i = 0; i < tabd.size(); ++i) tabf[i] = (float)tabd[i];
 
   cudaStream_t st = h->stream;
-  SolverState zero[4] = {};
+  std::vector<SolverState> zero(3 * d.Smax + d.B);
 #define SETUP_CK(call) do { if ((call) != cudaSuccess) { cudaGetLastError(); delete h; return LSH_ERR_CUDA; } } while (0)
-  SETUP_CK(cudaMemcpyAsync(h->st, zero, sizeof(zero), cudaMemcpyHostToDevice, st));
+  SETUP_CK(cudaMemcpyAsync(h->st, zero.data(), sizeof(SolverState) * zero.size(), cudaMemcpyHostToDevice, st));
   SETUP_CK(cudaMemcpyAsync(h->act, d.act.data(), 256, cudaMemcpyHostToDevice, st));
   SETUP_CK(cudaMemcpyAsync(h->posx, posx.data(), sizeof(int) * d.nx, cudaMemcpyHostToDevice, st));
   SETUP_CK(cudaMemcpyAsync(h->kofy, kofy.data(), sizeof(int) * d.ny, cudaMemcpyHostToDevice, st));
@@ -730,8 +852,8 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   SETUP_CK(cudaMemcpyAsync(h->base + l.off_tabd, tabd.data(), sizeof(double) * tabd.size(), cudaMemcpyHostToDevice, st));
   SETUP_CK(cudaMemcpyAsync(h->base + l.off_tabf, tabf.data(), sizeof(float) * tabf.size(), cudaMemcpyHostToDevice, st));
   if (copy_microstructure(h, prob->phase, prob->scale, prob->phase_on_host) != LSH_OK) { delete h; return LSH_ERR_CUDA; }
-  set_smem_attrs<double>(h->pd.L);
-  set_smem_attrs<float>(h->pf.L.threads ? h->pf.L : h->pd.L);
+  set_smem_attrs<double>();
+  set_smem_attrs<float>();
   launch_gamma_table<double>(h->pd.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st);
   if (d.precision == LSH_MIXED)
     launch_gamma_table<float>(h->pf.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st);
@@ -754,30 +876,39 @@ lsh_status lsh_apply(lsh_handle* h, int dtype, const void* x, void* y) {
   if (!h || !x || !y) return LSH_ERR_INVALID_ARG;
   const Derived& d = h->d;
   const bool el = d.physics == LSH_ELASTIC_ISO;
-  const int grid = h->pd.L.grid_ew;
-  if (dtype == LSH_F64) {
-    PrecBufs<double>& P = h->pd;
-    const double* in = (const double*)x;
-    if (el) {
-      launch_rotate<double>(in, P.p, d.V, 1, grid, h->stream);
-      in = P.p;
+  const long long n = (long long)d.c * d.V;
+  if (dtype != LSH_F64 && dtype != LSH_F32) return LSH_ERR_INVALID_ARG;
+  if (dtype == LSH_F32 && d.precision != LSH_MIXED) return LSH_ERR_UNSUPPORTED;
+  // one system per microstructure; in waves when the handle holds fewer systems
+  // (FP64 on a mixed handle: one system at a time through the p, q scratch)
+  const int per_wave = (dtype == LSH_F64 && d.precision == LSH_MIXED) ? 1 : std::min(d.Smax, d.B);
+  for (int b0 = 0; b0 < d.B; b0 += per_wave) {
+    const int S = std::min(per_wave, d.B - b0);
+    std::vector<double> zl(6 * (size_t)S, 0.0);
+    Wave w{S, b0, 1, zl.data()};
+    if (dtype == LSH_F64) {
+      PrecBufs<double>& P = h->pd;
+      const double* in = (const double*)x + b0 * n;
+      double* o = (double*)y + b0 * n;
+      if (el) {
+        launch_rotate<double>(in, P.p, d.V, S, 1, h->stream);
+        in = P.p;
+      }
+      lsh_status s = apply_internal<double>(h, wave_args<double>(h, w), in, el ? P.q : o);
+      if (s) return s;
+      if (el) launch_rotate<double>(P.q, o, d.V, S, 0, h->stream);
+    } else {
+      PrecBufs<float>& P = h->pf;
+      const float* in = (const float*)x + b0 * n;
+      float* o = (float*)y + b0 * n;
+      if (el) {
+        launch_rotate<float>(in, P.p, d.V, S, 1, h->stream);
+        in = P.p;
+      }
+      lsh_status s = apply_internal<float>(h, wave_args<float>(h, w), in, el ? P.q : o);
+      if (s) return s;
+      if (el) launch_rotate<float>(P.q, o, d.V, S, 0, h->stream);
     }
-    lsh_status s = apply_internal<double>(h, in, el ? P.q : (double*)y);
-    if (s) return s;
-    if (el) launch_rotate<double>(P.q, (double*)y, d.V, 0, grid, h->stream);
-  } else if (dtype == LSH_F32) {
-    if (d.precision != LSH_MIXED) return LSH_ERR_UNSUPPORTED;
-    PrecBufs<float>& P = h->pf;
-    const float* in = (const float*)x;
-    if (el) {
-      launch_rotate<float>(in, P.p, d.V, 1, grid, h->stream);
-      in = P.p;
-    }
-    lsh_status s = apply_internal<float>(h, in, el ? P.q : (float*)y);
-    if (s) return s;
-    if (el) launch_rotate<float>(P.q, (float*)y, d.V, 0, grid, h->stream);
-  } else {
-    return LSH_ERR_INVALID_ARG;
   }
   return last_launch();
 }
@@ -786,22 +917,33 @@ lsh_status lsh_solve(lsh_handle* h, const double* load, double* tau, const lsh_s
                      lsh_solve_info* info) {
   if (!h || !load || !tau) return LSH_ERR_INVALID_ARG;
   const Derived& d = h->d;
-  double lin[6];
+  const long long n = (long long)d.c * d.V;
+  double lin[6] = {0, 0, 0, 0, 0, 0};
   to_internal(d, load, lin);
   const bool warm = opts && opts->warm_start;
-  const int grid = h->pd.L.grid_ew;
-  if (warm) {
-    if (d.physics == LSH_ELASTIC_ISO) launch_rotate<double>(tau, h->pd.x, d.V, 1, grid, h->stream);
-    else if (cudaMemcpyAsync(h->pd.x, tau, sizeof(double) * d.c * d.V, cudaMemcpyDeviceToDevice, h->stream))
-      return LSH_ERR_CUDA;
+  lsh_status worst = LSH_OK;
+  const int per_wave = std::min(d.Smax, d.B);
+  for (int b0 = 0; b0 < d.B; b0 += per_wave) {
+    const int S = std::min(per_wave, d.B - b0);
+    std::vector<double> loads(6 * (size_t)S);
+    for (int s = 0; s < S; ++s)
+      for (int i = 0; i < 6; ++i) loads[6 * s + i] = lin[i];
+    Wave w{S, b0, 1, loads.data()};
+    if (warm) {
+      lsh_status r = rotate_or_copy(h, tau + b0 * n, h->pd.x, S, 1);
+      if (r) return r;
+    }
+    std::vector<lsh_solve_info> inf(S);
+    lsh_status r = solve_wave(h, w, warm, opts, inf.data());
+    if (r) return r;
+    if ((r = rotate_or_copy(h, h->pd.x, tau + b0 * n, S, 0))) return r;
+    for (int s = 0; s < S; ++s) {
+      if (info) info[b0 + s] = inf[s];
+      if (inf[s].status != LSH_OK && worst == LSH_OK) worst = (lsh_status)inf[s].status;
+    }
   }
-  lsh_status s = solve_internal(h, lin, warm, opts, info);
-  if (s != LSH_OK && s != LSH_ERR_NOT_CONVERGED && s != LSH_ERR_BREAKDOWN) return s;
-  if (d.physics == LSH_ELASTIC_ISO) launch_rotate<double>(h->pd.x, tau, d.V, 0, grid, h->stream);
-  else if (cudaMemcpyAsync(tau, h->pd.x, sizeof(double) * d.c * d.V, cudaMemcpyDeviceToDevice, h->stream))
-    return LSH_ERR_CUDA;
-  if (cudaStreamSynchronize(h->stream) != cudaSuccess) return LSH_ERR_CUDA;
-  return s;
+  LSH_CK(cudaStreamSynchronize(h->stream));
+  return worst;
 }
 
 lsh_status lsh_effective(lsh_handle* h, const lsh_solve_opts* opts, double* Astar, double* tau_all,
@@ -809,36 +951,43 @@ lsh_status lsh_effective(lsh_handle* h, const lsh_solve_opts* opts, double* Asta
   if (!h || !Astar) return LSH_ERR_INVALID_ARG;
   const Derived& d = h->d;
   const int c = d.c;
+  const long long n = (long long)c * d.V;
   double A0[36];
   ref_matrix(d, A0);
   const int nblk = 152;
+  const int total = d.B * c;
   lsh_status worst = LSH_OK;
-  for (int j = 0; j < c; ++j) {
-    double e[6] = {0, 0, 0, 0, 0, 0}, lin[6];
-    e[j] = 1.0;
-    to_internal(d, e, lin);
-    lsh_solve_info inf{};
-    lsh_solve_opts o = opts ? *opts : lsh_solve_opts{};
-    o.warm_start = 0;
-    lsh_status s = solve_internal(h, lin, false, &o, &inf);
-    if (infos) infos[j] = inf;
-    if (s != LSH_OK && s != LSH_ERR_NOT_CONVERGED && s != LSH_ERR_BREAKDOWN) return s;
-    if (s != LSH_OK && worst == LSH_OK) worst = s;
-    // A*_h e_j = A0 e_j + h^d sum_beta tau_beta (Eq. (tau_Astar), Theorem 13)
-    launch_comp_sums<double>(h->pd.x, c, d.V, h->partials, nblk, h->sums, h->stream);
-    h->launches += 2;
-    if (tau_all) {
-      double* dst = tau_all + (long long)j * c * d.V;
-      if (d.physics == LSH_ELASTIC_ISO) launch_rotate<double>(h->pd.x, dst, d.V, 0, h->pd.L.grid_ew, h->stream);
-      else if (cudaMemcpyAsync(dst, h->pd.x, sizeof(double) * c * d.V, cudaMemcpyDeviceToDevice, h->stream))
-        return LSH_ERR_CUDA;
+  lsh_solve_opts o = opts ? *opts : lsh_solve_opts{};
+  o.warm_start = 0;
+  for (int s0 = 0; s0 < total; s0 += d.Smax) {
+    const int S = std::min(d.Smax, total - s0);
+    // system g = b * c + j: microstructure b, unit load e_j (Mandel)
+    std::vector<double> loads(6 * (size_t)S, 0.0);
+    for (int s = 0; s < S; ++s) {
+      double e[6] = {0, 0, 0, 0, 0, 0};
+      e[(s0 + s) % c] = 1.0;
+      to_internal(d, e, &loads[6 * s]);
     }
-    double sums[6], mean[6], meanM[6];
-    LSH_CK(cudaMemcpyAsync(sums, h->sums, sizeof(double) * c, cudaMemcpyDeviceToHost, h->stream));
+    Wave w{S, s0, c, loads.data()};
+    std::vector<lsh_solve_info> inf(S);
+    lsh_status r = solve_wave(h, w, false, &o, inf.data());
+    if (r) return r;
+    // A*_h e_j = A0 e_j + h^d sum_beta tau_beta (Eq. (tau_Astar), Theorem 13)
+    launch_comp_sums<double>(h->pd.x, c, d.V, S, h->partials, nblk, h->sums, h->stream);
+    h->launches += 2;
+    if (tau_all && (r = rotate_or_copy(h, h->pd.x, tau_all + (long long)s0 * n, S, 0))) return r;
+    std::vector<double> sums((size_t)S * c);
+    LSH_CK(cudaMemcpyAsync(sums.data(), h->sums, sizeof(double) * S * c, cudaMemcpyDeviceToHost, h->stream));
     LSH_CK(cudaStreamSynchronize(h->stream));
-    for (int i = 0; i < c; ++i) mean[i] = sums[i] / (double)d.V;
-    to_mandel(d, mean, meanM);
-    for (int i = 0; i < c; ++i) Astar[i * c + j] = A0[i * c + j] + meanM[i];
+    for (int s = 0; s < S; ++s) {
+      const int g = s0 + s, b = g / c, j = g % c;
+      double mean[6], meanM[6];
+      for (int i = 0; i < c; ++i) mean[i] = sums[(size_t)s * c + i] / (double)d.V;
+      to_mandel(d, mean, meanM);
+      for (int i = 0; i < c; ++i) Astar[((size_t)b * c + i) * c + j] = A0[i * c + j] + meanM[i];
+      if (infos) infos[g] = inf[s];
+      if (inf[s].status != LSH_OK && worst == LSH_OK) worst = (lsh_status)inf[s].status;
+    }
   }
   return worst;
 }
@@ -846,16 +995,15 @@ lsh_status lsh_effective(lsh_handle* h, const lsh_solve_opts* opts, double* Asta
 lsh_status lsh_effective_grad(lsh_handle* h, const double* tau_all, const double* W, double* grad) {
   if (!h || !tau_all || !W || !grad) return LSH_ERR_INVALID_ARG;
   const Derived& d = h->d;
-  LSH_CK(cudaMemcpyAsync(h->Wdev, W, sizeof(double) * d.c * d.c, cudaMemcpyHostToDevice, h->stream));
-  double refd[6];
-  for (int i = 0; i < 6; ++i) refd[i] = i < d.c ? d.ref_in[i] : 0.0;
-  LSH_CK(cudaMemcpyAsync(h->Wdev + 40, refd, sizeof(refd), cudaMemcpyHostToDevice, h->stream));
+  double wbuf[64] = {0};
+  for (int i = 0; i < d.c * d.c; ++i) wbuf[i] = W[i];
+  for (int i = 0; i < 6; ++i) wbuf[40 + i] = i < d.c ? d.ref_in[i] : 0.0;
+  LSH_CK(cudaMemcpyAsync(h->Wdev, wbuf, sizeof(wbuf), cudaMemcpyHostToDevice, h->stream));
   launch_scale_grad(tau_all, h->Wdev, h->phase, h->scale, h->tabd + 256 * 6, h->Wdev + 40, d.c,
-                    d.physics == LSH_ELASTIC_ISO, d.V, grad,
-                    (int)std::min<long long>((d.V + 127) / 128, 152 * 16), h->stream);
+                    d.physics == LSH_ELASTIC_ISO, d.V, d.B, grad, h->stream);
+  h->launches += 1;
   lsh_status s = last_launch();
   if (s) return s;
-  // the host arrays above are stack memory: finish the copies before returning
   LSH_CK(cudaStreamSynchronize(h->stream));
   return LSH_OK;
 }

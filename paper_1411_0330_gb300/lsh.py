@@ -45,7 +45,7 @@ class _Problem(ctypes.Structure):
                 ("phase_moduli", ctypes.POINTER(ctypes.c_double)),
                 ("ref_moduli", ctypes.POINTER(ctypes.c_double)),
                 ("phase", ctypes.c_void_p), ("phase_on_host", ctypes.c_int),
-                ("scale", ctypes.c_void_p)]
+                ("scale", ctypes.c_void_p), ("nbatch", ctypes.c_int), ("max_systems", ctypes.c_int)]
 
 
 class _Opts(ctypes.Structure):
@@ -116,7 +116,8 @@ def _check(status: int, what: str, allow=()):
     return status
 
 
-def _problem_struct(phase_ptr, on_host, shape, physics, green, precision, moduli, ref, scale_ptr):
+def _problem_struct(phase_ptr, on_host, shape, physics, green, precision, moduli, ref, scale_ptr, nbatch=1,
+                    max_systems=0):
     s = _Problem()
     dim = len(shape)
     s.dim = dim
@@ -130,6 +131,8 @@ def _problem_struct(phase_ptr, on_host, shape, physics, green, precision, moduli
     s.phase = phase_ptr
     s.phase_on_host = 1 if on_host else 0
     s.scale = scale_ptr
+    s.nbatch = nbatch
+    s.max_systems = max_systems
     return s
 
 
@@ -138,14 +141,14 @@ def _opts(tol, maxit, solver, inner_tol, max_outer, check_every, warm_start=Fals
 
 
 def workspace_size(shape, phase_moduli, physics=SCALAR, green=TRUNCATED, precision=FP64, ref=None,
-                   has_scale=False) -> int:
+                   has_scale=False, nbatch=1, max_systems=0) -> int:
     """Workspace bytes for a problem (host-only computation; no GPU needed)."""
     lib = load_library()
     mods = np.ascontiguousarray(phase_moduli, dtype=np.float64)
     refa = None if ref is None else np.ascontiguousarray(ref, dtype=np.float64)
     dummy = ctypes.c_void_p(1)
     s = _problem_struct(dummy, True, tuple(shape), physics, green, precision, mods, refa,
-                        ctypes.c_void_p(1) if has_scale else None)
+                        ctypes.c_void_p(1) if has_scale else None, nbatch, max_systems)
     out = ctypes.c_size_t(0)
     _check(lib.lsh_workspace_size(ctypes.byref(s), ctypes.byref(out)), "lsh_workspace_size")
     return out.value
@@ -154,14 +157,16 @@ def workspace_size(shape, phase_moduli, physics=SCALAR, green=TRUNCATED, precisi
 class Handle:
     """One corrector problem on one GPU (Sec. 2.2 / Sec. 3 of the paper).
 
-    phase: uint8 torch tensor (device or CPU) or numpy array, shape (n2, n1, n0) or (n1, n0).
+    phase: uint8 torch tensor (device or CPU) or numpy array, shape (n2, n1, n0) or (n1, n0);
+        with batch=True a leading axis stacks microstructures of the same grid.
     phase_moduli: scalar -> (nphase, d, d) diagonal conductivities; elastic -> (nphase, 2) (K, mu).
     ref: reference medium in the same format as one phase, or None (half the softest phase).
-    scale: optional per-voxel float32 factor s (A_beta = s_beta A_phase).
+    scale: optional per-voxel float32 factor s (A_beta = s_beta A_phase), shaped like phase.
+    max_systems: systems (microstructure x load) solved at once; bounds the workspace.
     """
 
     def __init__(self, phase, phase_moduli, physics=SCALAR, green=TRUNCATED, precision=FP64, ref=None,
-                 scale=None, device=None, stream=None):
+                 scale=None, device=None, stream=None, batch=False, max_systems=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("liblsh needs a CUDA device; no CPU fallback exists")
@@ -177,7 +182,9 @@ class Handle:
             phase_t = phase.contiguous()
             if phase_t.dtype != torch.uint8:
                 raise TypeError("phase must be uint8")
-        self.shape = tuple(phase_t.shape)
+        self.batch = bool(batch)
+        self.nbatch = int(phase_t.shape[0]) if batch else 1
+        self.shape = tuple(phase_t.shape[1:]) if batch else tuple(phase_t.shape)
         self.dim = len(self.shape)
         self.physics = physics
         self.precision = precision
@@ -195,7 +202,8 @@ class Handle:
         self.has_scale = scale_t is not None
         self.phase_source = phase_t  # kept so the scale field can be replaced alone
         s = _problem_struct(ctypes.c_void_p(phase_t.data_ptr()), on_host, self.shape, physics, green, precision,
-                            self.moduli, self.ref, ctypes.c_void_p(scale_t.data_ptr()) if scale_t is not None else None)
+                            self.moduli, self.ref, ctypes.c_void_p(scale_t.data_ptr()) if scale_t is not None else None,
+                            self.nbatch, max_systems)
         nbytes = ctypes.c_size_t(0)
         _check(self.lib.lsh_workspace_size(ctypes.byref(s), ctypes.byref(nbytes)), "lsh_workspace_size")
         self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
@@ -208,7 +216,11 @@ class Handle:
     # ------------------------------------------------------------------ helpers
     @property
     def field_shape(self):
-        return (self.c,) + self.shape
+        return ((self.nbatch,) if self.batch else ()) + (self.c,) + self.shape
+
+    @property
+    def grid_shape(self):
+        return ((self.nbatch,) if self.batch else ()) + self.shape
 
     def _field(self, x, dtype):
         t = self._torch
@@ -262,27 +274,31 @@ class Handle:
         ld = np.ascontiguousarray(load, dtype=np.float64)
         if tau is None:
             tau = t.zeros(self.field_shape, dtype=t.float64, device=self.device)
-        info = _Info()
+        infos = (_Info * self.nbatch)()
         o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every, warm_start)
         st = self.lib.lsh_solve(self._h, ld.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
-                                ctypes.c_void_p(tau.data_ptr()), ctypes.byref(o), ctypes.byref(info))
+                                ctypes.c_void_p(tau.data_ptr()), ctypes.byref(o), infos)
         _check(st, "lsh_solve", allow=() if raise_on_fail else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
-        return tau, info.as_dict()
+        out = [i.as_dict() for i in infos]
+        return tau, (out if self.batch else out[0])
 
     def effective(self, tol=1e-10, maxit=10000, solver=SOLVER_AUTO, inner_tol=0.0, max_outer=0, check_every=0,
                   return_tau=False, tau_out=None, raise_on_fail=True):
-        """A*_h (c x c numpy, A[i, j] = e_i . A*_h e_j) and per-load info dicts."""
+        """A*_h (c x c numpy, A[i, j] = e_i . A*_h e_j; (nbatch, c, c) for a batch) and
+        per-system info dicts (load-major within each microstructure)."""
         t = self._torch
-        A = np.zeros(self.c * self.c)
-        infos = (_Info * self.c)()
+        A = np.zeros(self.nbatch * self.c * self.c)
+        infos = (_Info * (self.nbatch * self.c))()
         tau_all = tau_out
         if return_tau and tau_all is None:
-            tau_all = t.empty((self.c,) + self.field_shape, dtype=t.float64, device=self.device)
+            lead = (self.nbatch,) if self.batch else ()
+            tau_all = t.empty(lead + (self.c, self.c) + self.shape, dtype=t.float64, device=self.device)
         o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every)
         st = self.lib.lsh_effective(self._h, ctypes.byref(o), A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                     ctypes.c_void_p(tau_all.data_ptr()) if tau_all is not None else None, infos)
         _check(st, "lsh_effective", allow=() if raise_on_fail else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
-        out = (A.reshape(self.c, self.c), [i.as_dict() for i in infos])
+        A = A.reshape(self.nbatch, self.c, self.c) if self.batch else A.reshape(self.c, self.c)
+        out = (A, [i.as_dict() for i in infos])
         return out + (tau_all,) if tau_all is not None else out
 
     def profile_enable(self, enable=True):
@@ -299,7 +315,7 @@ class Handle:
         """d(sum_ij W_ij e_i.A*_h e_j)/d s_beta for the per-voxel scale field."""
         t = self._torch
         w = np.ascontiguousarray(W, dtype=np.float64)
-        g = out if out is not None else t.empty(self.shape, dtype=t.float64, device=self.device)
+        g = out if out is not None else t.empty(self.grid_shape, dtype=t.float64, device=self.device)
         _check(self.lib.lsh_effective_grad(self._h, ctypes.c_void_p(tau_all.data_ptr()),
                                            w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                            ctypes.c_void_p(g.data_ptr())), "lsh_effective_grad")

@@ -48,10 +48,14 @@ def test_workspace_size_scales(lib):
     s64 = lsh.workspace_size((64, 64, 64), EL, physics=lsh.ELASTIC, green=lsh.FILTERED)
     s128 = lsh.workspace_size((128, 128, 128), EL, physics=lsh.ELASTIC, green=lsh.FILTERED)
     assert 7.5 < s128 / s64 < 8.5
-    # four FP64 fields + spectrum + table at 128^3: between 0.5 and 1 GB
-    assert 0.5e9 < s128 < 1.0e9
+    # all 6 load systems at once: 6 x (4 FP64 fields + spectrum) + shared table
+    assert 2.5e9 < s128 < 4.0e9
+    one = lsh.workspace_size((128, 128, 128), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, max_systems=1)
+    assert 0.5e9 < one < 1.0e9
     mixed = lsh.workspace_size((128, 128, 128), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
     assert mixed > s128
+    batch = lsh.workspace_size((32, 32, 32), EL, physics=lsh.ELASTIC, nbatch=10, max_systems=12)
+    assert batch < lsh.workspace_size((32, 32, 32), EL, physics=lsh.ELASTIC, nbatch=10)
 
 
 @pytest.mark.parametrize("shape", [(32, 32), (7, 5), (12, 10, 6), (1, 3, 4), (48, 96, 32), (256, 256, 256)])
