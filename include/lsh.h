@@ -162,6 +162,26 @@ lsh_status lsh_effective(lsh_handle *h, const lsh_solve_opts *opts, double *Asta
  * Synchronous. */
 lsh_status lsh_effective_grad(lsh_handle *h, const double *tau_all, const double *W, double *grad);
 
+/* Allocation-free variant of lsh_apply (no counterpart in the paper; an
+ * interface for callers that cannot allocate device memory where they need
+ * K x: plugins inside host programs that own the device memory and offer no
+ * allocator, processes whose memory is already claimed by another
+ * framework's pool, or code that must not risk the device synchronisation
+ * cudaMalloc / cudaFree may cause).  Computes y = K x exactly as lsh_apply on
+ * a handle built from `prob` (one microstructure, FP64), without a handle or
+ * workspace: the scratch (spectrum, Gamma^h table, FFT and phase tables) is a
+ * 64 MiB array inside the library that every device loading the library
+ * keeps until process exit; problems needing more return
+ * LSH_ERR_UNSUPPORTED_SIZE (64^3 elasticity fits, 128^3 does not).  prob->phase
+ * (and prob->scale) must be device memory (phase_on_host = 0, nbatch <= 1);
+ * x, y: device, c*V doubles.  It calls no allocator, host or device.
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress and caches it; make that first call before any stream
+ * capture.  All calls share the array: calls whose device work overlaps race
+ * on it and must be serialised by the caller.  Synchronises `stream`
+ * (a cudaStream_t) before returning. */
+lsh_status lsh_apply_noalloc(const lsh_problem *prob, const double *x, double *y, void *stream);
+
 /* Diagnostics (no counterpart in the paper): kernel launches issued by the
  * handle, and, when enabled, the device time of each pass of the CG
  * iteration measured with CUDA events recorded on the handle's stream

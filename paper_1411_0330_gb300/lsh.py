@@ -72,7 +72,7 @@ PASS_NAMES = ["x_forward", "y_forward", "z_gamma", "y_inverse", "x_inverse_local
 
 EXPORTS = ["lsh_workspace_size", "lsh_setup", "lsh_set_microstructure", "lsh_apply", "lsh_solve",
            "lsh_effective", "lsh_effective_grad", "lsh_profile_enable", "lsh_profile_read", "lsh_destroy",
-           "lsh_status_string"]
+           "lsh_status_string", "lsh_apply_noalloc"]
 
 
 def library_path() -> str:
@@ -106,6 +106,7 @@ def load_library(build_if_missing: bool = True):
             lib.lsh_profile_read.argtypes = [vp, ctypes.POINTER(_Profile), ctypes.c_int]
             lib.lsh_destroy.argtypes = [vp]
             lib.lsh_destroy.restype = None
+            lib.lsh_apply_noalloc.argtypes = [P, vp, vp, vp]
             _lib = lib
     return _lib
 
@@ -152,6 +153,27 @@ def workspace_size(shape, phase_moduli, physics=SCALAR, green=TRUNCATED, precisi
     out = ctypes.c_size_t(0)
     _check(lib.lsh_workspace_size(ctypes.byref(s), ctypes.byref(out)), "lsh_workspace_size")
     return out.value
+
+
+def apply_noalloc(phase, x, phase_moduli, physics=SCALAR, green=TRUNCATED, ref=None, scale=None, out=None,
+                  stream=None):
+    """y = K x through lsh_apply_noalloc: no handle, no workspace, nothing allocated by
+    the library (its scratch is a fixed 64 MiB device array).  phase, scale, x are CUDA
+    tensors of one microstructure; returns y (float64, like x)."""
+    import torch
+    lib = load_library()
+    phase = phase.contiguous()
+    x = x.to(torch.float64).contiguous()
+    y = out if out is not None else torch.empty_like(x)
+    mods = np.ascontiguousarray(phase_moduli, dtype=np.float64)
+    refa = None if ref is None else np.ascontiguousarray(ref, dtype=np.float64)
+    sc = None if scale is None else scale.to(torch.float32).contiguous()
+    s = _problem_struct(ctypes.c_void_p(phase.data_ptr()), False, tuple(phase.shape), physics, green, FP64, mods,
+                        refa, ctypes.c_void_p(sc.data_ptr()) if sc is not None else None)
+    st = stream if stream is not None else torch.cuda.current_stream(x.device)
+    _check(lib.lsh_apply_noalloc(ctypes.byref(s), ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(y.data_ptr()),
+                                 ctypes.c_void_p(st.cuda_stream)), "lsh_apply_noalloc")
+    return y
 
 
 class Handle:
