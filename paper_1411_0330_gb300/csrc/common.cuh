@@ -73,6 +73,46 @@ template <> struct Acc<float> {
   __device__ __forceinline__ double get() const { return (double)s - (double)c; }
 };
 
+// Block sum of per-thread accumulators; result valid in thread 0.  FP32
+// compensated pairs are first merged across the warp in FP32 (TwoSum keeps
+// the rounding error of each merge), so only one value per warp touches the
+// FP64 pipe.
+__device__ __forceinline__ double block_sum(double v);
+__device__ __forceinline__ double block_reduce(const Acc<double>& a) { return block_sum(a.get()); }
+__device__ __forceinline__ void warp_merge_pair(float& s, float& c) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float s2 = __shfl_down_sync(0xffffffffu, s, o);
+    const float c2 = __shfl_down_sync(0xffffffffu, c, o);
+    const float t = s + s2;
+    const float bp = t - s;
+    const float e = (s - (t - bp)) + (s2 - bp);  // s + s2 = t + e exactly
+    s = t;
+    c = c + c2 - e;
+  }
+}
+__device__ __forceinline__ double block_reduce(const Acc<float>& a) {
+  __shared__ float pair_sh[2][32];
+  float s = a.s, c = a.c;  // value = s - c
+  warp_merge_pair(s, c);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) {
+    pair_sh[0][w] = s;
+    pair_sh[1][w] = c;
+  }
+  __syncthreads();
+  double out = 0.0;
+  if (w == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    s = l < nw ? pair_sh[0][l] : 0.0f;
+    c = l < nw ? pair_sh[1][l] : 0.0f;
+    warp_merge_pair(s, c);
+    if (l == 0) out = (double)s - (double)c;
+  }
+  return out;
+}
+
 // a / d with a shift when d is a power of two (d is uniform across the block).
 __device__ __forceinline__ int fdiv(int a, int d) { return (d & (d - 1)) == 0 ? (a >> (__ffs(d) - 1)) : a / d; }
 

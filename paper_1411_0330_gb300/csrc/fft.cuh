@@ -175,9 +175,91 @@ __device__ __forceinline__ void fft_stage(C2<T>* __restrict__ buf, int nlines, i
   }
 }
 
+// ---------------------------------------------------------------- compile-time schedules
+// For the common lengths the radix sequence is a template argument: every
+// index split becomes a shift or a mask and the stage loop unrolls.
+template <typename T, bool INV, int N, int R, int L>
+__device__ __forceinline__ void stage_ct(C2<T>* __restrict__ buf, int nlines, int ls, const C2<T>* __restrict__ tw) {
+  constexpr int m = L / R, nb = N / R, tws = N / L;
+  constexpr bool jmajor = m >= 16;
+  const int total = nb * nlines;
+  for (int w = threadIdx.x; w < total; w += blockDim.x) {
+    int line, b;
+    if (jmajor) {
+      line = w / nb;
+      b = w - line * nb;
+    } else {
+      b = fdiv(w, nlines);
+      line = w - b * nlines;
+    }
+    const int sp = b / m, j = b - sp * m;
+    butterfly<T, R, INV>(buf + line * ls + sp * L + j, m, j * tws, tw, N);
+  }
+}
+
+template <typename T, int N, int L, int... Rs> struct DifStages {
+  static __device__ __forceinline__ void run(C2<T>*, int, int, const C2<T>*) {}
+};
+template <typename T, int N, int L, int R, int... Rs> struct DifStages<T, N, L, R, Rs...> {
+  static __device__ __forceinline__ void run(C2<T>* buf, int nlines, int ls, const C2<T>* tw) {
+    stage_ct<T, false, N, R, L>(buf, nlines, ls, tw);
+    __syncthreads();
+    DifStages<T, N, L / R, Rs...>::run(buf, nlines, ls, tw);
+  }
+};
+// DIT stages run the DIF radices in reverse; the span of a stage is its radix
+// times the product of the radices after it.
+template <typename T, int N, int... Rs> struct DitStages {
+  static constexpr int P = 1;
+  static __device__ __forceinline__ void run(C2<T>*, int, int, const C2<T>*) {}
+};
+template <typename T, int N, int R, int... Rs> struct DitStages<T, N, R, Rs...> {
+  static constexpr int P = R * DitStages<T, N, Rs...>::P;
+  static __device__ __forceinline__ void run(C2<T>* buf, int nlines, int ls, const C2<T>* tw) {
+    DitStages<T, N, Rs...>::run(buf, nlines, ls, tw);
+    stage_ct<T, true, N, R, P>(buf, nlines, ls, tw);
+    __syncthreads();
+  }
+};
+
+template <int... Rs> __device__ __forceinline__ bool plan_is(const Plan1D& pl) {
+  constexpr int r[] = {Rs...};
+  constexpr int k = sizeof...(Rs);
+  if (pl.nst != k) return false;
+#pragma unroll
+  for (int i = 0; i < k; ++i)
+    if (pl.radix[i] != r[i]) return false;
+  return true;
+}
+
+template <typename T, bool INV, int N, int... Rs>
+__device__ __forceinline__ bool try_fixed(C2<T>* buf, int nlines, int ls, const Plan1D& pl, const C2<T>* tw) {
+  if (pl.n != N || !plan_is<Rs...>(pl)) return false;
+  if (INV) DitStages<T, N, Rs...>::run(buf, nlines, ls, tw);
+  else DifStages<T, N, N, Rs...>::run(buf, nlines, ls, tw);
+  return true;
+}
+
+template <typename T, bool INV>
+__device__ void fft_lines_generic(C2<T>* buf, int nlines, int ls, const Plan1D& pl, const C2<T>* tw);
+
 // Forward (DIF) or inverse (DIT) transform of nlines lines; ends synchronised.
+// The fixed schedules mirror the host's radix choice (8s first, an 8*2 pair
+// becomes 4*4, then 3, 5, 7); any other plan runs the generic stage loop.
 template <typename T, bool INV>
 __device__ void fft_lines(C2<T>* buf, int nlines, int ls, const Plan1D& pl, const C2<T>* tw) {
+  if (try_fixed<T, INV, 128, 4, 8, 4>(buf, nlines, ls, pl, tw)) return;
+  if (try_fixed<T, INV, 64, 8, 8>(buf, nlines, ls, pl, tw)) return;
+  if (try_fixed<T, INV, 256, 8, 8, 4>(buf, nlines, ls, pl, tw)) return;
+  if (try_fixed<T, INV, 32, 8, 4>(buf, nlines, ls, pl, tw)) return;
+  if (try_fixed<T, INV, 96, 8, 4, 3>(buf, nlines, ls, pl, tw)) return;
+  if (try_fixed<T, INV, 48, 4, 4, 3>(buf, nlines, ls, pl, tw)) return;
+  if (try_fixed<T, INV, 16, 4, 4>(buf, nlines, ls, pl, tw)) return;
+  fft_lines_generic<T, INV>(buf, nlines, ls, pl, tw);
+}
+
+template <typename T, bool INV>
+__device__ void fft_lines_generic(C2<T>* buf, int nlines, int ls, const Plan1D& pl, const C2<T>* tw) {
   const int n = pl.n;
   if (!INV) {
     int L = n;

@@ -38,10 +38,19 @@ template <typename T> struct OpArgs {
   const unsigned char* phase;  // [nbatch][V]
   const float* scale;          // [nbatch][V] or null
   const unsigned char* act;    // per phase: 1 if A_phase != A0 (voxel in I0)
+  int nphase;
   const T* mtab;               // per phase * c: diagonal of M (no scale field)
   const T* modtab;             // per phase * c: diagonal of A_phase (scale field)
   T ref[6];                    // diagonal of A0 (internal basis)
   const T* loads;              // [S][6] macroscopic load per system (internal basis)
+  // Green operator computed in the z pass instead of read from gtab (truncated
+  // operator, FP32): physics, grid lengths, signed-frequency tables, constants
+  int onfly;                   // 1: compute Gamma^h_k on the fly
+  int physics;
+  const int* kofy;             // y position -> frequency
+  const int* kofz;             // z position -> frequency
+  T g0[6];                     // elastic: 1/(2 mu0 V), cb/V, 1/(3 K0 V), 1/(2 mu0 V); scalar: A0 diagonal
+  T invV;
 };
 
 // Thread-block sizes and tile shapes, chosen at setup for one system count.

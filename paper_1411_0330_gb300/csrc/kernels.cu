@@ -25,6 +25,10 @@
 namespace lsh {
 
 static constexpr int kThreads = 256;
+// resident blocks per SM the register allocation must allow: FP64 passes
+// are FP64-pipe bound and need 2 blocks to hide latency, FP32 passes are
+// memory bound and need 3
+template <typename T> struct MinBlocks { static constexpr int value = sizeof(T) == 8 ? 2 : 3; };
 
 template <typename T, int VEC> struct VecOf;
 template <> struct VecOf<float, 4> { typedef float4 type; };
@@ -70,7 +74,7 @@ __device__ __forceinline__ T local_coef(const OpArgs<T>& a, long long pv, int co
 // Each thread handles VEC consecutive x of a row pair and writes complete
 // complex values of the packed line Z = row_even + i row_odd.
 template <typename T, int MODE, int VEC>
-__global__ void __launch_bounds__(kThreads) k_xfwd(OpArgs<T> a, const T* __restrict__ in, T* __restrict__ x,
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xfwd(OpArgs<T> a, const T* __restrict__ in, T* __restrict__ x,
                                                    const T* __restrict__ r, T* __restrict__ p,
                                                    const SolverState* __restrict__ st) {
   const int s = blockIdx.x / a.bps;
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(kThreads) k_xfwd(OpArgs<T> a, const T* __restr
 // ------------------------------------------------------------------ y pass
 // blockIdx.y = plane (s, comp, z); TY consecutive kx columns per block.
 template <typename T, bool INV>
-__global__ void __launch_bounds__(kThreads) k_yfft(OpArgs<T> a, const SolverState* __restrict__ st) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_yfft(OpArgs<T> a, const SolverState* __restrict__ st) {
   const long long plane = blockIdx.y;
   const int s = (int)(plane / (a.c * a.nz));
   if (st != nullptr && st[s].done) return;
@@ -194,17 +198,106 @@ __global__ void __launch_bounds__(kThreads) k_yfft(OpArgs<T> a, const SolverStat
 }
 
 // ------------------------------------------------------------------ z pass + Gamma
-// blockIdx.x = kx tile, blockIdx.y = y position, blockIdx.z = system.
+// Truncated Green operator at one frequency, computed in place on the c
+// components of the internal basis (Eqs. (14)-(15) and the Nyquist rule of
+// Sec. 3.2.1), scaled by 1/V.  Used for FP32, where it is cheaper than
+// reading the tabulated coefficients.
 template <typename T, int NC>
-__global__ void __launch_bounds__(kThreads) k_zgamma(OpArgs<T> a, const SolverState* __restrict__ st) {
-  const int s = blockIdx.z;
+__device__ __forceinline__ void gamma_trunc_onfly(const OpArgs<T>& a, int kx, int ky, int kz, C2<T>* v) {
+  const int kk[3] = {kx, ky, kz};
+  const int nn[3] = {a.nx, a.ny, a.nz};
+  T xi[3];
+  bool zero = true, nyq = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int ki = kk[i] <= nn[i] / 2 ? kk[i] : kk[i] - nn[i];
+    if ((nn[i] & 1) == 0 && kk[i] == nn[i] / 2 && nn[i] > 1) nyq = true;
+    xi[i] = (T)ki;
+    if (ki != 0) zero = false;
+  }
+  if (zero) {
+#pragma unroll
+    for (int i = 0; i < NC; ++i) v[i] = mkc<T>(0, 0);
+    return;
+  }
+  if (NC != 6) {
+    // scalar: xi (xi . v) / (xi^T A0 xi), or A0^{-1} v at the Nyquist frequencies
+    if (nyq) {
+#pragma unroll
+      for (int i = 0; i < NC; ++i) v[i] = cscale<T>(v[i], a.invV / a.g0[i]);
+      return;
+    }
+    T q = 0;
+    C2<T> d = mkc<T>(0, 0);
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      q += a.g0[i] * xi[i] * xi[i];
+      d.x += xi[i] * v[i].x;
+      d.y += xi[i] * v[i].y;
+    }
+    const T f = a.invV / q;
+#pragma unroll
+    for (int i = 0; i < NC; ++i) v[i] = mkc<T>(f * xi[i] * d.x, f * xi[i] * d.y);
+    return;
+  }
+  if (nyq) {
+    // C0^{-1}: diagonal in the internal basis
+    v[0] = cscale<T>(v[0], a.g0[2]);
+#pragma unroll
+    for (int i = 1; i < 6; ++i) v[i] = cscale<T>(v[i], a.g0[3]);
+    return;
+  }
+  const T s3 = (T)0.57735026918962576450914878050195745565, s2 = (T)0.70710678118654752440084436210484903928,
+          s6 = (T)0.40824829046386301636621401245098189866;
+  const T rn = (T)1 / sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
+  const T n0 = xi[0] * rn, n1 = xi[1] * rn, n2 = xi[2] * rn;
+  // internal -> tensor components (t11, t22, t33, t23, t13, t12)
+  C2<T> t11, t22, t33, t23, t13, t12;
+  t11 = mkc<T>(v[0].x * s3 + v[1].x * s2 + v[2].x * s6, v[0].y * s3 + v[1].y * s2 + v[2].y * s6);
+  t22 = mkc<T>(v[0].x * s3 - v[1].x * s2 + v[2].x * s6, v[0].y * s3 - v[1].y * s2 + v[2].y * s6);
+  t33 = mkc<T>(v[0].x * s3 - (T)2 * v[2].x * s6, v[0].y * s3 - (T)2 * v[2].y * s6);
+  t23 = cscale<T>(v[3], s2);
+  t13 = cscale<T>(v[4], s2);
+  t12 = cscale<T>(v[5], s2);
+  // Tn and n.Tn
+  const C2<T> u0 = mkc<T>(t11.x * n0 + t12.x * n1 + t13.x * n2, t11.y * n0 + t12.y * n1 + t13.y * n2);
+  const C2<T> u1 = mkc<T>(t12.x * n0 + t22.x * n1 + t23.x * n2, t12.y * n0 + t22.y * n1 + t23.y * n2);
+  const C2<T> u2 = mkc<T>(t13.x * n0 + t23.x * n1 + t33.x * n2, t13.y * n0 + t23.y * n1 + t33.y * n2);
+  const C2<T> w = mkc<T>(n0 * u0.x + n1 * u1.x + n2 * u2.x, n0 * u0.y + n1 * u1.y + n2 * u2.y);
+  const T a1 = a.g0[0], a2 = a.g0[1];
+  // S_ij = a1 (u_i n_j + n_i u_j) - a2 w n_i n_j
+#define LSH_SIJ(ui, nj, ni, uj, nij) \
+  mkc<T>(a1 * (ui.x * nj + ni * uj.x) - a2 * w.x * nij, a1 * (ui.y * nj + ni * uj.y) - a2 * w.y * nij)
+  const C2<T> S11 = LSH_SIJ(u0, n0, n0, u0, n0 * n0);
+  const C2<T> S22 = LSH_SIJ(u1, n1, n1, u1, n1 * n1);
+  const C2<T> S33 = LSH_SIJ(u2, n2, n2, u2, n2 * n2);
+  const C2<T> S23 = LSH_SIJ(u1, n2, n1, u2, n1 * n2);
+  const C2<T> S13 = LSH_SIJ(u0, n2, n0, u2, n0 * n2);
+  const C2<T> S12 = LSH_SIJ(u0, n1, n0, u1, n0 * n1);
+#undef LSH_SIJ
+  // tensor -> internal basis (Mandel shear components carry sqrt 2)
+  const T r2 = (T)1.41421356237309504880168872420969807857;
+  v[0] = mkc<T>((S11.x + S22.x + S33.x) * s3, (S11.y + S22.y + S33.y) * s3);
+  v[1] = mkc<T>((S11.x - S22.x) * s2, (S11.y - S22.y) * s2);
+  v[2] = mkc<T>((S11.x + S22.x - (T)2 * S33.x) * s6, (S11.y + S22.y - (T)2 * S33.y) * s6);
+  v[3] = cscale<T>(S23, r2);
+  v[4] = cscale<T>(S13, r2);
+  v[5] = cscale<T>(S12, r2);
+}
+
+// blockIdx.x = system, blockIdx.y = kx tile, blockIdx.z = y position: the
+// blocks of all systems for one tile run together and share its Gamma
+// coefficients through L2.
+template <typename T, int NC>
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs<T> a, const SolverState* __restrict__ st) {
+  const int s = blockIdx.x;
   if (st != nullptr && st[s].done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* buf = tw + a.nz;
   for (int i = threadIdx.x; i < a.nz; i += blockDim.x) tw[i] = a.twz[i];
-  const int yp = blockIdx.y;
-  const int kx0 = blockIdx.x * a.TZ;
+  const int yp = blockIdx.z;
+  const int kx0 = blockIdx.y * a.TZ;
   const int nt = min(a.TZ, a.nxh - kx0);
   const int nz = a.nz, TZ = a.TZ;
   const long long zstride = (long long)a.ny * a.nxh;  // distance between z planes
@@ -231,32 +324,40 @@ __global__ void __launch_bounds__(kThreads) k_zgamma(OpArgs<T> a, const SolverSt
   }
   __syncthreads();
   if (nz > 1) fft_lines<T, false>(buf, NC * TZ, a.lsz, a.pz, tw);
-  // per-frequency product with the symmetric c x c table (packed upper triangle)
+  // per-frequency product with Gamma^h_k
   const T* __restrict__ G = a.gtab + (long long)yp * a.nxh + kx0;
+  const int ky = a.onfly ? a.kofy[yp] : 0;
   for (int idx = threadIdx.x; idx < nz * TZ; idx += blockDim.x) {
     const int zp = fdiv(idx, TZ), t = idx - zp * TZ;
     if (t >= nt) continue;
-    C2<T> v[NC], y[NC];
+    C2<T> v[NC];
 #pragma unroll
-    for (int i = 0; i < NC; ++i) {
-      v[i] = buf[(i * TZ + t) * a.lsz + zp];
-      y[i] = mkc<T>(0, 0);
-    }
-    int coef = 0;
+    for (int i = 0; i < NC; ++i) v[i] = buf[(i * TZ + t) * a.lsz + zp];
+    if (a.onfly) {
+      gamma_trunc_onfly<T, NC>(a, kx0 + t, ky, a.kofz[zp], v);
+    } else {
+      // symmetric c x c table, packed upper triangle
+      C2<T> y[NC];
 #pragma unroll
-    for (int i = 0; i < NC; ++i)
+      for (int i = 0; i < NC; ++i) y[i] = mkc<T>(0, 0);
+      int coef = 0;
 #pragma unroll
-      for (int j = i; j < NC; ++j, ++coef) {
-        const T g = G[coef * cstride + zp * zstride + t];
-        y[i].x += g * v[j].x;
-        y[i].y += g * v[j].y;
-        if (j != i) {
-          y[j].x += g * v[i].x;
-          y[j].y += g * v[i].y;
+      for (int i = 0; i < NC; ++i)
+#pragma unroll
+        for (int j = i; j < NC; ++j, ++coef) {
+          const T g = G[coef * cstride + zp * zstride + t];
+          y[i].x += g * v[j].x;
+          y[i].y += g * v[j].y;
+          if (j != i) {
+            y[j].x += g * v[i].x;
+            y[j].y += g * v[i].y;
+          }
         }
-      }
 #pragma unroll
-    for (int i = 0; i < NC; ++i) buf[(i * TZ + t) * a.lsz + zp] = y[i];
+      for (int i = 0; i < NC; ++i) v[i] = y[i];
+    }
+#pragma unroll
+    for (int i = 0; i < NC; ++i) buf[(i * TZ + t) * a.lsz + zp] = v[i];
   }
   __syncthreads();
   if (nz > 1) fft_lines<T, true>(buf, NC * TZ, a.lsz, a.pz, tw);
@@ -271,11 +372,15 @@ __global__ void __launch_bounds__(kThreads) k_zgamma(OpArgs<T> a, const SolverSt
 // MODE 0: out = P (M xin + g).  MODE 1 (CG): q = P (M p + g), (p, q) -> alpha.
 // MODE 2 (residual): out = P (load - M xin - g), (r, r) -> st[s].aux[0].
 template <typename T, int MODE, int VEC>
-__global__ void __launch_bounds__(kThreads) k_xinv(OpArgs<T> a, const T* __restrict__ xin, T* __restrict__ out,
-                                                   SolverState* __restrict__ st, double* __restrict__ partials) {
+__global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xinv(OpArgs<T> a, const T* __restrict__ xin,
+                                                                        T* __restrict__ out,
+                                                                        SolverState* __restrict__ st,
+                                                                        double* __restrict__ partials) {
   const int s = blockIdx.x / a.bps;
   if (MODE == 1 && st[s].done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ T mloc[256 * 6];  // local coefficients (no scale field) or A_phase diagonal
+  __shared__ unsigned char aloc[256];
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* Z = tw + a.nx;
   int* pos = reinterpret_cast<int*>(Z + ((a.RY + 1) >> 1) * a.lsx);
@@ -284,20 +389,39 @@ __global__ void __launch_bounds__(kThreads) k_xinv(OpArgs<T> a, const T* __restr
     tw[i] = a.twx[i];
     pos[i] = a.posx[i];
   }
+  const int ntab = a.nphase * a.c;
+  for (int i = threadIdx.x; i < ntab; i += blockDim.x) mloc[i] = a.scale ? a.modtab[i] : a.mtab[i];
+  for (int i = threadIdx.x; i < a.nphase; i += blockDim.x) aloc[i] = a.act[i];
   __syncthreads();
   const int blk = blockIdx.x - s * a.bps;
   const int rloc = blk * a.RY;
   const int nr = a.RY;
   const int npair = (nr + 1) >> 1;
   const long long row0 = (long long)s * a.rps + rloc;
+  const C2<T>* __restrict__ Hb = a.H + row0 * a.nxh;
   // Z = X_a + i X_b over the full line, X(nx - k) = conj X(k) beyond the half
-  for (int idx = threadIdx.x; idx < npair * a.nxh; idx += blockDim.x) {
-    const int lp = fdiv(idx, a.nxh), kx = idx - lp * a.nxh;
-    const long long hrow = row0 + 2 * lp;
-    const C2<T> xa = a.H[hrow * a.nxh + kx];
-    const C2<T> xb = (2 * lp + 1 < nr) ? a.H[(hrow + 1) * a.nxh + kx] : mkc<T>(0, 0);
-    Z[lp * a.lsx + pos[kx]] = mkc<T>(xa.x - xb.y, xa.y + xb.x);
-    if (kx >= 1 && kx <= nx - a.nxh) Z[lp * a.lsx + pos[nx - kx]] = mkc<T>(xa.x + xb.y, xb.x - xa.y);
+  const int nz_items = npair * a.nxh;
+  for (int base = threadIdx.x; base < nz_items; base += 4 * blockDim.x) {
+    C2<T> xa[4], xb[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * blockDim.x;
+      xa[u] = xb[u] = mkc<T>(0, 0);
+      if (idx < nz_items) {
+        const int lp = fdiv(idx, a.nxh), kx = idx - lp * a.nxh;
+        xa[u] = Hb[(2 * lp) * a.nxh + kx];
+        if (2 * lp + 1 < nr) xb[u] = Hb[(2 * lp + 1) * a.nxh + kx];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < nz_items) {
+        const int lp = fdiv(idx, a.nxh), kx = idx - lp * a.nxh;
+        Z[lp * a.lsx + pos[kx]] = mkc<T>(xa[u].x - xb[u].y, xa[u].y + xb[u].x);
+        if (kx >= 1 && kx <= nx - a.nxh) Z[lp * a.lsx + pos[nx - kx]] = mkc<T>(xa[u].x + xb[u].y, xb[u].x - xa[u].y);
+      }
+    }
   }
   __syncthreads();
   fft_lines<T, true>(Z, npair, a.lsx, a.px, tw);
@@ -308,6 +432,31 @@ __global__ void __launch_bounds__(kThreads) k_xinv(OpArgs<T> a, const T* __restr
   for (int idx = threadIdx.x; idx < npair * nxv; idx += blockDim.x) {
     const int lp = fdiv(idx, nxv);
     const int xx = (idx - lp * nxv) * VEC;
+    // issue every global load of the row pair first
+    T xv[2][VEC];
+    unsigned char ph[2][VEC];
+    int comp[2];
+    long long voxs[2];
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const int row = 2 * lp + h2;
+      const int rs = rloc + min(row, nr - 1);
+      comp[h2] = rs / rows_per_comp;
+      const long long vox = (long long)(rs - comp[h2] * rows_per_comp) * nx + xx;
+      voxs[h2] = pbase + vox;
+      if (row < nr) {
+        vload<T, VEC>(xin + (row0 + row) * nx + xx, xv[h2]);
+        if constexpr (VEC == 4) {
+          const uchar4 q = *reinterpret_cast<const uchar4*>(a.phase + pbase + vox);
+          ph[h2][0] = q.x; ph[h2][1] = q.y; ph[h2][2] = q.z; ph[h2][3] = q.w;
+        } else if constexpr (VEC == 2) {
+          const uchar2 q = *reinterpret_cast<const uchar2*>(a.phase + pbase + vox);
+          ph[h2][0] = q.x; ph[h2][1] = q.y;
+        } else {
+          ph[h2][0] = a.phase[pbase + vox];
+        }
+      }
+    }
     C2<T> zc[VEC];
 #pragma unroll
     for (int u = 0; u < VEC; ++u) zc[u] = Z[lp * a.lsx + xx + u];
@@ -316,23 +465,22 @@ __global__ void __launch_bounds__(kThreads) k_xinv(OpArgs<T> a, const T* __restr
       const int row = 2 * lp + h2;
       if (row >= nr) continue;
       const long long g = (row0 + row) * nx + xx;
-      const int rs = rloc + row;
-      const int comp = rs / rows_per_comp;
-      const long long vox = (long long)(rs - comp * rows_per_comp) * nx + xx;
-      T xv[VEC], ov[VEC];
-      vload<T, VEC>(xin + g, xv);
+      T ov[VEC];
 #pragma unroll
       for (int u = 0; u < VEC; ++u) {
-        int active;
-        const T m = local_coef(a, pbase + vox + u, comp, &active);
+        const int p = ph[h2][u];
+        const bool active = aloc[p] != 0;
+        T m = mloc[p * a.c + comp[h2]];
+        if (a.scale) m = (T)1 / ((T)a.scale[voxs[h2] + u] * m - a.ref[comp[h2]]);
         const T gv = h2 ? zc[u].y : zc[u].x;
+        const T xq = xv[h2][u];
         if (MODE == 0) {
-          ov[u] = active ? m * xv[u] + gv : (T)0;
+          ov[u] = active ? m * xq + gv : (T)0;
         } else if (MODE == 1) {
-          ov[u] = active ? m * xv[u] + gv : (T)0;
-          acc.add(xv[u] * ov[u]);
+          ov[u] = active ? m * xq + gv : (T)0;
+          acc.add(xq * ov[u]);
         } else {
-          ov[u] = active ? a.loads[s * 6 + comp] - (m * xv[u] + gv) : (T)0;
+          ov[u] = active ? a.loads[s * 6 + comp[h2]] - (m * xq + gv) : (T)0;
           acc.add(ov[u] * ov[u]);
         }
       }
@@ -340,7 +488,7 @@ __global__ void __launch_bounds__(kThreads) k_xinv(OpArgs<T> a, const T* __restr
     }
   }
   if (MODE != 0) {
-    const double tot = block_sum(acc.get());
+    const double tot = block_reduce(acc);
     double* part = partials + (long long)s * a.bps;
     SolverState* sst = st + s;
     if (publish_partial_sys(part, blk, a.bps, tot, &sst->counter[0])) {
@@ -394,7 +542,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(T* __restrict__ r, const
     rs[i] = rv;
     acc.add(rv * rv);
   }
-  const double tot = block_sum(acc.get());
+  const double tot = block_reduce(acc);
   double* part = partials + (long long)s * gridDim.x;
   if (publish_partial_sys(part, blockIdx.x, gridDim.x, tot, &sst->counter[1])) {
     const double rrn = gather_partials_sys(part, gridDim.x, &sst->counter[1]);
@@ -434,7 +582,7 @@ __global__ void __launch_bounds__(kThreads) k_cg_begin(const T* __restrict__ r, 
   Acc<T> acc;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     acc.add(rs[i] * rs[i]);
-  const double tot = block_sum(acc.get());
+  const double tot = block_reduce(acc);
   double* part = partials + (long long)s * gridDim.x;
   SolverState* sst = st + s;
   if (publish_partial_sys(part, blockIdx.x, gridDim.x, tot, &sst->counter[2])) {
@@ -661,7 +809,7 @@ __global__ void __launch_bounds__(kThreads) k_d2f_begin(const double* __restrict
     x32s[i] = 0.0f;
     acc.add(v * v);
   }
-  const double tot = block_sum(acc.get());
+  const double tot = block_reduce(acc);
   double* part = partials + (long long)s * gridDim.x;
   SolverState* sst = st + s;
   if (publish_partial_sys(part, blockIdx.x, gridDim.x, tot, &sst->counter[2])) {
@@ -799,7 +947,7 @@ void launch_yfft(const OpArgs<T>& a, const LaunchCfg& L, bool inv, const SolverS
 
 template <typename T>
 void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st, cudaStream_t s) {
-  dim3 g(L.grid_zx, L.grid_zy, a.S);
+  dim3 g(a.S, L.grid_zx, L.grid_zy);
   if (a.c == 6) k_zgamma<T, 6><<<g, L.threads, L.smem_z, s>>>(a, st);
   else if (a.c == 3) k_zgamma<T, 3><<<g, L.threads, L.smem_z, s>>>(a, st);
   else k_zgamma<T, 2><<<g, L.threads, L.smem_z, s>>>(a, st);

@@ -421,10 +421,28 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.phase = h->phase;
   a.scale = h->scale;
   a.act = h->act;
+  a.nphase = d.nphase;
   a.mtab = P.mtab;
   a.modtab = P.modtab;
   for (int i = 0; i < 6; ++i) a.ref[i] = (T)(i < d.c ? d.ref_in[i] : 0.0);
   a.loads = P.loads;
+  // FP32 truncated operator: computed on the fly in the z pass (no table read)
+  a.onfly = (sizeof(T) == 4 && d.green == LSH_GREEN_TRUNCATED) ? 1 : 0;
+  a.physics = d.physics;
+  a.kofy = h->kofy;
+  a.kofz = h->kofz;
+  const double invV = 1.0 / (double)d.V;
+  a.invV = (T)invV;
+  for (int i = 0; i < 6; ++i) a.g0[i] = (T)0;
+  if (d.physics == LSH_ELASTIC_ISO) {
+    const double K0 = d.ref_user[0], mu0 = d.ref_user[1], lam0 = K0 - 2.0 * mu0 / 3.0;
+    a.g0[0] = (T)(invV / (2.0 * mu0));
+    a.g0[1] = (T)(invV * (lam0 + mu0) / (mu0 * (lam0 + 2.0 * mu0)));
+    a.g0[2] = (T)(invV / (3.0 * K0));
+    a.g0[3] = (T)(invV / (2.0 * mu0));
+  } else {
+    for (int i = 0; i < d.c; ++i) a.g0[i] = (T)d.ref_user[i];
+  }
 }
 
 // internal basis <-> Mandel for elasticity (see k_rotate)

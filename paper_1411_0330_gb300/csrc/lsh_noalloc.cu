@@ -287,6 +287,7 @@ extern "C" lsh_status lsh_apply_noalloc(const lsh_problem* pr, const double* x, 
   a.phase = pr->phase;
   a.scale = pr->scale;
   a.act = base + o_act;
+  a.nphase = pr->nphase;
   a.mtab = (const double*)(base + o_mtab);
   a.modtab = (const double*)(base + o_modtab);
   for (int i = 0; i < 6; ++i) a.ref[i] = i < c ? ref_in[i] : 0.0;

@@ -322,3 +322,16 @@ def test_batched_apply_and_solve():
         to, _, _ = oracle.solve(P, load, tol=1e-13)
         assert rel(tau[b].cpu().numpy(), to) < 1e-9
         assert infos[b]["status"] == 0
+
+
+@pytest.mark.parametrize("shape,green", [((32, 32), 0), ((12, 10), 1), ((10, 12, 16), 0), ((9, 8, 6), 1)])
+def test_apply_fp32_scalar(shape, green):
+    rng = np.random.default_rng(sum(shape) + green)
+    d = len(shape)
+    ph = rng.integers(0, 3, shape).astype(np.uint8)
+    mods = _scalar_mods(d, 3)
+    P = oracle.Problem(ph, mods, physics=0, green=green)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=0, green=green, precision=lsh.MIXED)
+    x = rng.standard_normal(P.field_shape)
+    y32 = h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy()
+    assert rel(y32, oracle.apply(P, x)) < 2e-5
