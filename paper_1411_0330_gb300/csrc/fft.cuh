@@ -104,6 +104,43 @@ template <typename T, bool INV> struct Dft<T, 5, INV> {
   }
 };
 
+// 16 = 4 x 4: x[n2 + 4 n1] -> X[k1 + 4 k2] = sum_n2 w4^(n2 k2) w16^(n2 k1) sum_n1 x[n2 + 4 n1] w4^(n1 k1)
+template <typename T, bool INV> struct Dft<T, 16, INV> {
+  static __device__ __forceinline__ void run(C2<T>* a, const C2<T>* tw, int n) {
+    const T c1 = (T)0.92387953251128675612818318939678828682;  // cos(pi/8)
+    const T s1 = (T)0.38268343236508977172845998403039886676;  // sin(pi/8)
+    const T h = (T)0.70710678118654752440084436210484903928;   // cos(pi/4)
+    C2<T> b[4][4];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+      C2<T> c[4] = {a[n2], a[n2 + 4], a[n2 + 8], a[n2 + 12]};
+      Dft<T, 4, INV>::run(c, tw, n);
+#pragma unroll
+      for (int k1 = 0; k1 < 4; ++k1) b[n2][k1] = c[k1];
+    }
+    // twiddles w16^m, m = n2 k1: (cos, -+sin) of 2 pi m / 16
+    const T sg = INV ? (T)1 : (T)-1;
+    const C2<T> w1 = mkc<T>(c1, sg * s1), w2 = mkc<T>(h, sg * h), w3 = mkc<T>(s1, sg * c1);
+    const C2<T> w6 = mkc<T>(-h, sg * h), w9 = mkc<T>(-c1, -sg * s1);
+    b[1][1] = cmul<T>(b[1][1], w1);
+    b[1][2] = cmul<T>(b[1][2], w2);
+    b[1][3] = cmul<T>(b[1][3], w3);
+    b[2][1] = cmul<T>(b[2][1], w2);
+    b[2][2] = INV ? cmul_pi<T>(b[2][2]) : cmul_mi<T>(b[2][2]);  // w16^4 = -+i
+    b[2][3] = cmul<T>(b[2][3], w6);
+    b[3][1] = cmul<T>(b[3][1], w3);
+    b[3][2] = cmul<T>(b[3][2], w6);
+    b[3][3] = cmul<T>(b[3][3], w9);
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+      C2<T> d[4] = {b[0][k1], b[1][k1], b[2][k1], b[3][k1]};
+      Dft<T, 4, INV>::run(d, tw, n);
+#pragma unroll
+      for (int k2 = 0; k2 < 4; ++k2) a[k1 + 4 * k2] = d[k2];
+    }
+  }
+};
+
 // Direct DFT for the remaining small prime (7), from the twiddle table.
 template <typename T, bool INV> struct Dft<T, 7, INV> {
   static __device__ __forceinline__ void run(C2<T>* a, const C2<T>* tw, int n) {

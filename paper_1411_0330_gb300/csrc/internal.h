@@ -51,6 +51,8 @@ template <typename T> struct OpArgs {
   const int* kofz;             // z position -> frequency
   T g0[6];                     // elastic: 1/(2 mu0 V), cb/V, 1/(3 K0 V), 1/(2 mu0 V); scalar: A0 diagonal
   T invV;
+  // register-FFT passes (natural-order y / z frequencies) for lengths 16..256
+  int yreg, zreg;
 };
 
 // Thread-block sizes and tile shapes, chosen at setup for one system count.
@@ -98,5 +100,9 @@ void launch_scale_grad(const double* tau_all, const double* W, const unsigned ch
                        double* grad, cudaStream_t s);
 
 template <typename T> void set_smem_attrs();
+template <typename T> void set_smem_attrs_reg();
+template <typename T> void launch_yfft_reg(const OpArgs<T>& a, bool inv, const SolverState* st, cudaStream_t s);
+template <typename T> void launch_zgamma_reg(const OpArgs<T>& a, const SolverState* st, cudaStream_t s);
+bool reg_length(int n);
 
 }  // namespace lsh

@@ -21,6 +21,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "internal.h"
+#include "gamma_onfly.cuh"
 
 namespace lsh {
 
@@ -198,93 +199,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_yfft(OpArgs<T
 }
 
 // ------------------------------------------------------------------ z pass + Gamma
-// Truncated Green operator at one frequency, computed in place on the c
-// components of the internal basis (Eqs. (14)-(15) and the Nyquist rule of
-// Sec. 3.2.1), scaled by 1/V.  Used for FP32, where it is cheaper than
-// reading the tabulated coefficients.
-template <typename T, int NC>
-__device__ __forceinline__ void gamma_trunc_onfly(const OpArgs<T>& a, int kx, int ky, int kz, C2<T>* v) {
-  const int kk[3] = {kx, ky, kz};
-  const int nn[3] = {a.nx, a.ny, a.nz};
-  T xi[3];
-  bool zero = true, nyq = false;
-#pragma unroll
-  for (int i = 0; i < 3; ++i) {
-    const int ki = kk[i] <= nn[i] / 2 ? kk[i] : kk[i] - nn[i];
-    if ((nn[i] & 1) == 0 && kk[i] == nn[i] / 2 && nn[i] > 1) nyq = true;
-    xi[i] = (T)ki;
-    if (ki != 0) zero = false;
-  }
-  if (zero) {
-#pragma unroll
-    for (int i = 0; i < NC; ++i) v[i] = mkc<T>(0, 0);
-    return;
-  }
-  if (NC != 6) {
-    // scalar: xi (xi . v) / (xi^T A0 xi), or A0^{-1} v at the Nyquist frequencies
-    if (nyq) {
-#pragma unroll
-      for (int i = 0; i < NC; ++i) v[i] = cscale<T>(v[i], a.invV / a.g0[i]);
-      return;
-    }
-    T q = 0;
-    C2<T> d = mkc<T>(0, 0);
-#pragma unroll
-    for (int i = 0; i < NC; ++i) {
-      q += a.g0[i] * xi[i] * xi[i];
-      d.x += xi[i] * v[i].x;
-      d.y += xi[i] * v[i].y;
-    }
-    const T f = a.invV / q;
-#pragma unroll
-    for (int i = 0; i < NC; ++i) v[i] = mkc<T>(f * xi[i] * d.x, f * xi[i] * d.y);
-    return;
-  }
-  if (nyq) {
-    // C0^{-1}: diagonal in the internal basis
-    v[0] = cscale<T>(v[0], a.g0[2]);
-#pragma unroll
-    for (int i = 1; i < 6; ++i) v[i] = cscale<T>(v[i], a.g0[3]);
-    return;
-  }
-  const T s3 = (T)0.57735026918962576450914878050195745565, s2 = (T)0.70710678118654752440084436210484903928,
-          s6 = (T)0.40824829046386301636621401245098189866;
-  const T rn = (T)1 / sqrt(xi[0] * xi[0] + xi[1] * xi[1] + xi[2] * xi[2]);
-  const T n0 = xi[0] * rn, n1 = xi[1] * rn, n2 = xi[2] * rn;
-  // internal -> tensor components (t11, t22, t33, t23, t13, t12)
-  C2<T> t11, t22, t33, t23, t13, t12;
-  t11 = mkc<T>(v[0].x * s3 + v[1].x * s2 + v[2].x * s6, v[0].y * s3 + v[1].y * s2 + v[2].y * s6);
-  t22 = mkc<T>(v[0].x * s3 - v[1].x * s2 + v[2].x * s6, v[0].y * s3 - v[1].y * s2 + v[2].y * s6);
-  t33 = mkc<T>(v[0].x * s3 - (T)2 * v[2].x * s6, v[0].y * s3 - (T)2 * v[2].y * s6);
-  t23 = cscale<T>(v[3], s2);
-  t13 = cscale<T>(v[4], s2);
-  t12 = cscale<T>(v[5], s2);
-  // Tn and n.Tn
-  const C2<T> u0 = mkc<T>(t11.x * n0 + t12.x * n1 + t13.x * n2, t11.y * n0 + t12.y * n1 + t13.y * n2);
-  const C2<T> u1 = mkc<T>(t12.x * n0 + t22.x * n1 + t23.x * n2, t12.y * n0 + t22.y * n1 + t23.y * n2);
-  const C2<T> u2 = mkc<T>(t13.x * n0 + t23.x * n1 + t33.x * n2, t13.y * n0 + t23.y * n1 + t33.y * n2);
-  const C2<T> w = mkc<T>(n0 * u0.x + n1 * u1.x + n2 * u2.x, n0 * u0.y + n1 * u1.y + n2 * u2.y);
-  const T a1 = a.g0[0], a2 = a.g0[1];
-  // S_ij = a1 (u_i n_j + n_i u_j) - a2 w n_i n_j
-#define LSH_SIJ(ui, nj, ni, uj, nij) \
-  mkc<T>(a1 * (ui.x * nj + ni * uj.x) - a2 * w.x * nij, a1 * (ui.y * nj + ni * uj.y) - a2 * w.y * nij)
-  const C2<T> S11 = LSH_SIJ(u0, n0, n0, u0, n0 * n0);
-  const C2<T> S22 = LSH_SIJ(u1, n1, n1, u1, n1 * n1);
-  const C2<T> S33 = LSH_SIJ(u2, n2, n2, u2, n2 * n2);
-  const C2<T> S23 = LSH_SIJ(u1, n2, n1, u2, n1 * n2);
-  const C2<T> S13 = LSH_SIJ(u0, n2, n0, u2, n0 * n2);
-  const C2<T> S12 = LSH_SIJ(u0, n1, n0, u1, n0 * n1);
-#undef LSH_SIJ
-  // tensor -> internal basis (Mandel shear components carry sqrt 2)
-  const T r2 = (T)1.41421356237309504880168872420969807857;
-  v[0] = mkc<T>((S11.x + S22.x + S33.x) * s3, (S11.y + S22.y + S33.y) * s3);
-  v[1] = mkc<T>((S11.x - S22.x) * s2, (S11.y - S22.y) * s2);
-  v[2] = mkc<T>((S11.x + S22.x - (T)2 * S33.x) * s6, (S11.y + S22.y - (T)2 * S33.y) * s6);
-  v[3] = cscale<T>(S23, r2);
-  v[4] = cscale<T>(S13, r2);
-  v[5] = cscale<T>(S12, r2);
-}
-
 // blockIdx.x = system, blockIdx.y = kx tile, blockIdx.z = y position: the
 // blocks of all systems for one tile run together and share its Gamma
 // coefficients through L2.
@@ -922,6 +836,7 @@ template <typename T> void set_smem_attrs() {
   cudaFuncSetAttribute(k_zgamma<T, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_zgamma<T, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_zgamma<T, 6>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  set_smem_attrs_reg<T>();
 }
 
 template <typename T>
@@ -940,6 +855,10 @@ void launch_xfwd(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* in, 
 
 template <typename T>
 void launch_yfft(const OpArgs<T>& a, const LaunchCfg& L, bool inv, const SolverState* st, cudaStream_t s) {
+  if (a.yreg) {
+    launch_yfft_reg<T>(a, inv, st, s);
+    return;
+  }
   dim3 g(L.grid_yx, a.S * a.c * a.nz);
   if (inv) k_yfft<T, true><<<g, L.threads, L.smem_y, s>>>(a, st);
   else k_yfft<T, false><<<g, L.threads, L.smem_y, s>>>(a, st);
@@ -947,6 +866,10 @@ void launch_yfft(const OpArgs<T>& a, const LaunchCfg& L, bool inv, const SolverS
 
 template <typename T>
 void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st, cudaStream_t s) {
+  if (a.zreg) {
+    launch_zgamma_reg<T>(a, st, s);
+    return;
+  }
   dim3 g(a.S, L.grid_zx, L.grid_zy);
   if (a.c == 6) k_zgamma<T, 6><<<g, L.threads, L.smem_z, s>>>(a, st);
   else if (a.c == 3) k_zgamma<T, 3><<<g, L.threads, L.smem_z, s>>>(a, st);

@@ -433,6 +433,8 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.kofz = h->kofz;
   const double invV = 1.0 / (double)d.V;
   a.invV = (T)invV;
+  a.yreg = reg_length(d.ny) ? 1 : 0;
+  a.zreg = (reg_length(d.nz)) ? 1 : 0;
   for (int i = 0; i < 6; ++i) a.g0[i] = (T)0;
   if (d.physics == LSH_ELASTIC_ISO) {
     const double K0 = d.ref_user[0], mu0 = d.ref_user[1], lam0 = K0 - 2.0 * mu0 / 3.0;
@@ -838,10 +840,11 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
     init_prec<float>(h, h->pf, l.off_ff, l.off_Hf, l.off_gf, l.off_tw_f, l.off_tabf, l.off_loads_f, h->st + d.Smax);
 
   // host tables
+  // register-FFT axes keep natural frequency order; the others are digit-reversed
   std::vector<int> posx(d.nx), kofy(d.ny), kofz(d.nz);
   for (int k = 0; k < d.nx; ++k) posx[k] = dif_position(d.px, k);
-  for (int k = 0; k < d.ny; ++k) kofy[dif_position(d.py, k)] = k;
-  for (int k = 0; k < d.nz; ++k) kofz[dif_position(d.pz, k)] = k;
+  for (int k = 0; k < d.ny; ++k) kofy[h->pd.a.yreg ? k : dif_position(d.py, k)] = k;
+  for (int k = 0; k < d.nz; ++k) kofz[h->pd.a.zreg ? k : dif_position(d.pz, k)] = k;
   std::vector<double> twd, tmpd;
   twiddles<double>(d.nx, tmpd); twd.insert(twd.end(), tmpd.begin(), tmpd.end());
   twiddles<double>(d.ny, tmpd); twd.insert(twd.end(), tmpd.begin(), tmpd.end());
