@@ -97,6 +97,9 @@ typedef struct lsh_solve_opts {
   int max_outer;     /* LSH_MIXED: refinement steps (<= 0 selects 30)                    */
   int check_every;   /* iterations between host convergence checks (<= 0 selects 8)     */
   int warm_start;    /* lsh_solve: tau holds the initial guess on entry                  */
+  int no_graphs;     /* 0: each block of check_every CG iterations is captured once in a
+                        CUDA graph (per handle, wave and precision) and replayed;
+                        1: the kernels are launched one by one.  Results are identical. */
 } lsh_solve_opts;
 
 typedef struct lsh_solve_info {

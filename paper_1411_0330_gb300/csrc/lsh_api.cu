@@ -347,7 +347,24 @@ struct lsh_handle {
   double pass_ms[6] = {0, 0, 0, 0, 0, 0};
   long long pass_n[6] = {0, 0, 0, 0, 0, 0};
   long long timed_iters = 0;
+  // CUDA graphs of check_every CG iterations, one per (precision, wave, chunk,
+  // profiling), captured on a private stream and replayed on `stream`
+  struct Graph {
+    int prec, sys0, S, sys_per_ms, chunk;
+    bool prof;
+    cudaGraphExec_t exec;
+    long long launches;
+  };
+  std::vector<Graph> graphs;
+  cudaStream_t cap = nullptr;
+  bool capturing = false;
+  void drop_graphs() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.exec);
+    graphs.clear();
+  }
   ~lsh_handle() {
+    drop_graphs();
+    if (cap) cudaStreamDestroy(cap);
     for (auto e : ev) cudaEventDestroy(e);
   }
 };
@@ -547,23 +564,66 @@ template <typename T> void enqueue_cg_iteration(lsh_handle* h, PrecBufs<T>& P, c
   cudaStream_t s = h->stream;
   const bool timed = h->prof && h->ev_used + 7 <= (int)h->ev.size();
   cudaEvent_t* e = timed ? &h->ev[h->ev_used] : nullptr;
-  if (timed) cudaEventRecord(e[0], s);
+  // inside a capture the records become graph nodes that record at replay
+  const unsigned rf = h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+  if (timed) cudaEventRecordWithFlags(e[0], s, rf);
   launch_xfwd<T>(a, P.L, 1, nullptr, P.x, P.r, P.p, P.st, s);
-  if (timed) cudaEventRecord(e[1], s);
+  if (timed) cudaEventRecordWithFlags(e[1], s, rf);
   launch_yfft<T>(a, P.L, false, P.st, s);
-  if (timed) cudaEventRecord(e[2], s);
+  if (timed) cudaEventRecordWithFlags(e[2], s, rf);
   launch_zgamma<T>(a, P.L, P.st, s);
-  if (timed) cudaEventRecord(e[3], s);
+  if (timed) cudaEventRecordWithFlags(e[3], s, rf);
   launch_yfft<T>(a, P.L, true, P.st, s);
-  if (timed) cudaEventRecord(e[4], s);
+  if (timed) cudaEventRecordWithFlags(e[4], s, rf);
   launch_xinv<T>(a, P.L, 1, P.p, P.q, P.st, h->partials, s);
-  if (timed) cudaEventRecord(e[5], s);
+  if (timed) cudaEventRecordWithFlags(e[5], s, rf);
   launch_cg_update<T>(P.r, P.q, (long long)a.c * a.V, a.S, P.st, h->partials, P.L.ew_per_sys, s);
   if (timed) {
-    cudaEventRecord(e[6], s);
+    cudaEventRecordWithFlags(e[6], s, rf);
     h->ev_used += 7;
   }
   h->launches += 6;
+}
+
+// The graph replaying `chunk` CG iterations of this wave, captured on first use.
+// Everything the kernels read is fixed per handle and wave (device pointers,
+// OpArgs); the CG scalars and the done flags stay on the device.
+template <typename T>
+lsh_status chunk_graph(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int chunk, lsh_handle::Graph** out) {
+  const int prec = (int)sizeof(T);
+  for (auto& g : h->graphs)
+    if (g.prec == prec && g.sys0 == a.sys0 && g.S == a.S && g.sys_per_ms == a.sys_per_ms && g.chunk == chunk &&
+        g.prof == h->prof) {
+      *out = &g;
+      return LSH_OK;
+    }
+  if (!h->cap) LSH_CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  cudaStream_t user = h->stream;
+  const long long l0 = h->launches;
+  const int ev0 = h->ev_used;
+  h->ev_used = 0;
+  h->stream = h->cap;
+  h->capturing = true;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    for (int j = 0; j < chunk; ++j) enqueue_cg_iteration<T>(h, P, a);
+    e = cudaStreamEndCapture(h->cap, &graph);
+  }
+  h->capturing = false;
+  h->stream = user;
+  lsh_handle::Graph g{prec, a.sys0, a.S, a.sys_per_ms, chunk, h->prof, nullptr, h->launches - l0};
+  h->launches = l0;
+  h->ev_used = ev0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
+  if (graph) cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return LSH_ERR_CUDA;
+  }
+  h->graphs.push_back(g);
+  *out = &h->graphs.back();
+  return LSH_OK;
 }
 
 // After a host synchronisation: add the pass times of the first `real`
@@ -588,7 +648,7 @@ void harvest_profile(lsh_handle* h, int real) {
 // CG on the states already begun for the wave; finalises x.  `out` receives
 // the S states.
 template <typename T>
-lsh_status cg_run(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int maxit, int check_every,
+lsh_status cg_run(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int maxit, int check_every, bool graphs,
                   std::vector<SolverState>& out) {
   const int S = a.S;
   out.resize(S);
@@ -608,7 +668,16 @@ lsh_status cg_run(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int maxit, 
   while (!all_done() && it < maxit) {
     const int chunk = std::min(check_every, maxit - it);
     const int before = max_iter();
-    for (int j = 0; j < chunk; ++j) enqueue_cg_iteration<T>(h, P, a);
+    if (graphs && chunk == check_every) {
+      lsh_handle::Graph* g = nullptr;
+      if ((stt = chunk_graph<T>(h, P, a, chunk, &g))) return stt;
+      if (h->prof) h->ev_used = 0;
+      LSH_CK(cudaGraphLaunch(g->exec, h->stream));
+      h->launches += g->launches;
+      if (h->prof) h->ev_used = (int)std::min<size_t>(7 * (size_t)chunk, h->ev.size() / 7 * 7);
+    } else {
+      for (int j = 0; j < chunk; ++j) enqueue_cg_iteration<T>(h, P, a);
+    }
     if ((stt = last_launch())) return stt;
     it += chunk;
     if ((stt = read_states(h, P.st, S, out.data()))) return stt;
@@ -629,6 +698,7 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
   const double tol = o && o->tol > 0 ? o->tol : 1e-10;
   const int maxit = o && o->maxit > 0 ? o->maxit : 10000;
   const int check = o && o->check_every > 0 ? o->check_every : 8;
+  const bool graphs = !(o && o->no_graphs);
   lsh_status stt;
   if ((stt = upload_loads(h, w))) return stt;
   // (b, b) per system = |load|^2 x (voxels in I0 of its microstructure)
@@ -656,7 +726,7 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
       h->launches += 1;
     }
     if ((stt = last_launch())) return stt;
-    if ((stt = cg_run<double>(h, Pd, ad, maxit, check, st))) return stt;
+    if ((stt = cg_run<double>(h, Pd, ad, maxit, check, graphs, st))) return stt;
     for (int s = 0; s < S; ++s) {
       infos[s].iters = st[s].iter;
       infos[s].applies64 += st[s].iter;
@@ -704,7 +774,7 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
       LSH_CK(cudaMemcpyAsync(h->flags, active.data(), S, cudaMemcpyHostToDevice, h->stream));
       launch_d2f_begin(Pd.r, Pf.r, Pf.x, n, S, Pf.st, h->partials, itol, h->flags, Pf.L.ew_per_sys, h->stream);
       h->launches += 1;
-      if ((stt = cg_run<float>(h, Pf, af, maxit - total_max, check, st))) return stt;
+      if ((stt = cg_run<float>(h, Pf, af, maxit - total_max, check, graphs, st))) return stt;
       launch_f2d_axpy(Pd.x, Pf.x, n * S, h->stream);
       h->launches += 1;
       if ((stt = residual64(h, ad, Pd.x, Pd.r))) return stt;
@@ -888,6 +958,7 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
 
 lsh_status lsh_set_microstructure(lsh_handle* h, const unsigned char* phase, const float* scale, int on_host) {
   if (!h || !phase) return LSH_ERR_INVALID_ARG;
+  h->drop_graphs();  // the scale pointer in the captured arguments may change
   lsh_status s = copy_microstructure(h, phase, scale, on_host);
   if (s) return s;
   return scan_microstructure(h);

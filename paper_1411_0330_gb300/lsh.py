@@ -51,7 +51,7 @@ class _Problem(ctypes.Structure):
 class _Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("maxit", ctypes.c_int), ("solver", ctypes.c_int),
                 ("inner_tol", ctypes.c_double), ("max_outer", ctypes.c_int), ("check_every", ctypes.c_int),
-                ("warm_start", ctypes.c_int)]
+                ("warm_start", ctypes.c_int), ("no_graphs", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -137,8 +137,9 @@ def _problem_struct(phase_ptr, on_host, shape, physics, green, precision, moduli
     return s
 
 
-def _opts(tol, maxit, solver, inner_tol, max_outer, check_every, warm_start=False):
-    return _Opts(tol, maxit, solver, inner_tol, max_outer, check_every, 1 if warm_start else 0)
+def _opts(tol, maxit, solver, inner_tol, max_outer, check_every, warm_start=False, graphs=True):
+    return _Opts(tol, maxit, solver, inner_tol, max_outer, check_every, 1 if warm_start else 0,
+                 0 if graphs else 1)
 
 
 def workspace_size(shape, phase_moduli, physics=SCALAR, green=TRUNCATED, precision=FP64, ref=None,
@@ -290,14 +291,15 @@ class Handle:
         return y
 
     def solve(self, load, tau=None, tol=1e-10, maxit=10000, solver=SOLVER_AUTO, inner_tol=0.0, max_outer=0,
-              check_every=0, warm_start=False, raise_on_fail=True):
-        """Solve Eq. (13) for the macroscopic load p (c values).  Returns (tau, info dict)."""
+              check_every=0, warm_start=False, raise_on_fail=True, graphs=True):
+        """Solve Eq. (13) for the macroscopic load p (c values).  Returns (tau, info dict).
+        graphs=False launches the CG kernels one by one instead of replaying a CUDA graph."""
         t = self._torch
         ld = np.ascontiguousarray(load, dtype=np.float64)
         if tau is None:
             tau = t.zeros(self.field_shape, dtype=t.float64, device=self.device)
         infos = (_Info * self.nbatch)()
-        o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every, warm_start)
+        o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every, warm_start, graphs)
         st = self.lib.lsh_solve(self._h, ld.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                 ctypes.c_void_p(tau.data_ptr()), ctypes.byref(o), infos)
         _check(st, "lsh_solve", allow=() if raise_on_fail else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
@@ -305,7 +307,7 @@ class Handle:
         return tau, (out if self.batch else out[0])
 
     def effective(self, tol=1e-10, maxit=10000, solver=SOLVER_AUTO, inner_tol=0.0, max_outer=0, check_every=0,
-                  return_tau=False, tau_out=None, raise_on_fail=True):
+                  return_tau=False, tau_out=None, raise_on_fail=True, graphs=True):
         """A*_h (c x c numpy, A[i, j] = e_i . A*_h e_j; (nbatch, c, c) for a batch) and
         per-system info dicts (load-major within each microstructure)."""
         t = self._torch
@@ -315,7 +317,7 @@ class Handle:
         if return_tau and tau_all is None:
             lead = (self.nbatch,) if self.batch else ()
             tau_all = t.empty(lead + (self.c, self.c) + self.shape, dtype=t.float64, device=self.device)
-        o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every)
+        o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every, graphs=graphs)
         st = self.lib.lsh_effective(self._h, ctypes.byref(o), A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                     ctypes.c_void_p(tau_all.data_ptr()) if tau_all is not None else None, infos)
         _check(st, "lsh_effective", allow=() if raise_on_fail else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
