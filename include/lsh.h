@@ -156,6 +156,19 @@ lsh_status lsh_solve(lsh_handle *h, const double *load, double *tau, const lsh_s
 lsh_status lsh_effective(lsh_handle *h, const lsh_solve_opts *opts, double *Astar, double *tau_all,
                          lsh_solve_info *infos);
 
+/* lsh_effective for several handles at once (microstructures of different
+ * grids or phase sets; Sec. 5 computes one effective tensor per
+ * microstructure).  Each handle runs on its own host thread and its own
+ * stream, so the handles' kernels overlap on the device; give every handle a
+ * distinct stream (handles that share one stream still give the same results,
+ * one after the other).  Astar: host, the handles' nbatch*c*c blocks one after
+ * the other in the order of hs; infos: optional host array of the handles'
+ * nbatch*c entries in the same order.  A handle may appear once only
+ * (LSH_ERR_INVALID_ARG otherwise).  Returns the first status other than
+ * LSH_OK in handle order.  Synchronous. */
+lsh_status lsh_effective_batch(int nh, lsh_handle *const *hs, const lsh_solve_opts *opts, double *Astar,
+                               lsh_solve_info *infos);
+
 /* Gradient of sum_ij W_ij e_i.A*_h e_j with respect to the per-voxel scale
  * s_beta (A_beta = s_beta A_phase; s = 1 without a scale field), for every
  * microstructure: g_beta = h^d sum_ij W_ij eps_i,beta . A_phase(beta)

@@ -14,6 +14,7 @@
 #include <cstdint>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -327,6 +328,7 @@ template <typename T> struct PrecBufs {
 // ---------------------------------------------------------------- the handle
 struct lsh_handle {
   Derived d;
+  int device = 0;
   Layout lay;
   cudaStream_t stream;
   unsigned char* base;
@@ -890,6 +892,7 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   h->lay = make_layout(d);
   if (bytes < h->lay.total || ((uintptr_t)workspace % kAlign) != 0) { delete h; return LSH_ERR_WORKSPACE; }
   h->stream = (cudaStream_t)stream;
+  cudaGetDevice(&h->device);
   h->base = (unsigned char*)workspace;
   const Layout& l = h->lay;
   h->st = (SolverState*)(h->base + l.off_state);
@@ -1082,6 +1085,41 @@ lsh_status lsh_effective(lsh_handle* h, const lsh_solve_opts* opts, double* Asta
     }
   }
   return worst;
+}
+
+lsh_status lsh_effective_batch(int nh, lsh_handle* const* hs, const lsh_solve_opts* opts, double* Astar,
+                               lsh_solve_info* infos) {
+  if (nh < 0 || (nh > 0 && (!hs || !Astar))) return LSH_ERR_INVALID_ARG;
+  std::vector<size_t> aoff(nh + 1, 0), ioff(nh + 1, 0);
+  for (int k = 0; k < nh; ++k) {
+    if (!hs[k]) return LSH_ERR_INVALID_ARG;
+    for (int j = 0; j < k; ++j)
+      if (hs[j] == hs[k]) return LSH_ERR_INVALID_ARG;
+    const size_t nb = (size_t)hs[k]->d.B, c = (size_t)hs[k]->d.c;
+    aoff[k + 1] = aoff[k] + nb * c * c;
+    ioff[k + 1] = ioff[k] + nb * c;
+  }
+  std::vector<lsh_status> st(nh, LSH_OK);
+  auto run = [&](int k) {
+    if (cudaSetDevice(hs[k]->device) != cudaSuccess) {
+      cudaGetLastError();
+      st[k] = LSH_ERR_CUDA;
+      return;
+    }
+    st[k] = lsh_effective(hs[k], opts, Astar + aoff[k], nullptr, infos ? infos + ioff[k] : nullptr);
+  };
+  std::vector<std::thread> pool;
+  int k0 = 0;
+  try {
+    for (; k0 < nh; ++k0) pool.emplace_back(run, k0);
+  } catch (...) {
+    // no more host threads: the remaining handles run on this one
+  }
+  for (int k = k0; k < nh; ++k) run(k);
+  for (auto& t : pool) t.join();
+  for (int k = 0; k < nh; ++k)
+    if (st[k] != LSH_OK) return st[k];
+  return LSH_OK;
 }
 
 lsh_status lsh_effective_grad(lsh_handle* h, const double* tau_all, const double* W, double* grad) {

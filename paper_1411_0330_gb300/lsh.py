@@ -72,7 +72,7 @@ PASS_NAMES = ["x_forward", "y_forward", "z_gamma", "y_inverse", "x_inverse_local
 
 EXPORTS = ["lsh_workspace_size", "lsh_setup", "lsh_set_microstructure", "lsh_apply", "lsh_solve",
            "lsh_effective", "lsh_effective_grad", "lsh_profile_enable", "lsh_profile_read", "lsh_destroy",
-           "lsh_status_string", "lsh_apply_noalloc"]
+           "lsh_status_string", "lsh_apply_noalloc", "lsh_effective_batch"]
 
 
 def library_path() -> str:
@@ -107,6 +107,8 @@ def load_library(build_if_missing: bool = True):
             lib.lsh_destroy.argtypes = [vp]
             lib.lsh_destroy.restype = None
             lib.lsh_apply_noalloc.argtypes = [P, vp, vp, vp]
+            lib.lsh_effective_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(_Opts), dp,
+                                                ctypes.POINTER(_Info)]
             _lib = lib
     return _lib
 
@@ -199,6 +201,7 @@ class Handle:
         if self.device.index is None:
             self.device = torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self._own_stream = self.stream != torch.cuda.current_stream(self.device)
         if isinstance(phase, np.ndarray):
             phase_t = torch.from_numpy(np.ascontiguousarray(phase, dtype=np.uint8))
         else:
@@ -230,6 +233,7 @@ class Handle:
         nbytes = ctypes.c_size_t(0)
         _check(self.lib.lsh_workspace_size(ctypes.byref(s), ctypes.byref(nbytes)), "lsh_workspace_size")
         self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        self._wait_inputs()
         h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             _check(self.lib.lsh_setup(ctypes.byref(s), ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
@@ -254,6 +258,16 @@ class Handle:
             x = x.reshape(self.field_shape)
         return x
 
+    def _wait_inputs(self):
+        """With a stream of its own, the handle waits for work queued on the
+        caller's current stream (its inputs) before using them."""
+        if self._own_stream:
+            self.stream.wait_stream(self._torch.cuda.current_stream(self.device))
+
+    def _release_outputs(self):
+        if self._own_stream:
+            self._torch.cuda.current_stream(self.device).wait_stream(self.stream)
+
     def close(self):
         if getattr(self, "_h", None):
             self.lib.lsh_destroy(self._h)
@@ -277,6 +291,7 @@ class Handle:
             scale = t.as_tensor(scale, dtype=t.float32)
             scale = scale.cpu().contiguous() if on_host else scale.to(self.device).contiguous()
             sp = ctypes.c_void_p(scale.data_ptr())
+        self._wait_inputs()
         _check(self.lib.lsh_set_microstructure(self._h, ctypes.c_void_p(phase.data_ptr()), sp, 1 if on_host else 0),
                "lsh_set_microstructure")
 
@@ -286,8 +301,10 @@ class Handle:
         dtype = dtype or (x.dtype if isinstance(x, t.Tensor) and x.dtype in (t.float32, t.float64) else t.float64)
         x = self._field(x, dtype)
         y = out if out is not None else t.empty_like(x)
+        self._wait_inputs()
         _check(self.lib.lsh_apply(self._h, F64 if dtype == t.float64 else F32, ctypes.c_void_p(x.data_ptr()),
                                   ctypes.c_void_p(y.data_ptr())), "lsh_apply")
+        self._release_outputs()
         return y
 
     def solve(self, load, tau=None, tol=1e-10, maxit=10000, solver=SOLVER_AUTO, inner_tol=0.0, max_outer=0,
@@ -300,6 +317,7 @@ class Handle:
             tau = t.zeros(self.field_shape, dtype=t.float64, device=self.device)
         infos = (_Info * self.nbatch)()
         o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every, warm_start, graphs)
+        self._wait_inputs()
         st = self.lib.lsh_solve(self._h, ld.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                 ctypes.c_void_p(tau.data_ptr()), ctypes.byref(o), infos)
         _check(st, "lsh_solve", allow=() if raise_on_fail else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
@@ -318,6 +336,7 @@ class Handle:
             lead = (self.nbatch,) if self.batch else ()
             tau_all = t.empty(lead + (self.c, self.c) + self.shape, dtype=t.float64, device=self.device)
         o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every, graphs=graphs)
+        self._wait_inputs()
         st = self.lib.lsh_effective(self._h, ctypes.byref(o), A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                     ctypes.c_void_p(tau_all.data_ptr()) if tau_all is not None else None, infos)
         _check(st, "lsh_effective", allow=() if raise_on_fail else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
@@ -340,7 +359,88 @@ class Handle:
         t = self._torch
         w = np.ascontiguousarray(W, dtype=np.float64)
         g = out if out is not None else t.empty(self.grid_shape, dtype=t.float64, device=self.device)
+        self._wait_inputs()
         _check(self.lib.lsh_effective_grad(self._h, ctypes.c_void_p(tau_all.data_ptr()),
                                            w.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                            ctypes.c_void_p(g.data_ptr())), "lsh_effective_grad")
         return g
+
+
+def effective_batch(handles, tol=1e-10, maxit=10000, solver=SOLVER_AUTO, inner_tol=0.0, max_outer=0, check_every=0,
+                    raise_on_fail=True, graphs=True):
+    """lsh_effective on several handles at once (one host thread and one stream
+    per handle, so their kernels overlap).  Returns one A per handle (c x c, or
+    (nbatch, c, c) for a batch handle) and one list of info dicts per handle."""
+    handles = list(handles)
+    if not handles:
+        return [], []
+    lib = handles[0].lib
+    sizes = [h.nbatch * h.c * h.c for h in handles]
+    nsys = [h.nbatch * h.c for h in handles]
+    A = np.zeros(sum(sizes))
+    infos = (_Info * sum(nsys))()
+    for h in handles:
+        h._wait_inputs()
+    hs = (ctypes.c_void_p * len(handles))(*[h._h.value for h in handles])
+    o = _opts(tol, maxit, solver, inner_tol, max_outer, check_every, graphs=graphs)
+    st = lib.lsh_effective_batch(len(handles), hs, ctypes.byref(o), A.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 infos)
+    _check(st, "lsh_effective_batch", allow=() if raise_on_fail else (ERR_NOT_CONVERGED, ERR_BREAKDOWN))
+    outA, outI, a0, i0 = [], [], 0, 0
+    for h, na, ns in zip(handles, sizes, nsys):
+        blk = A[a0:a0 + na]
+        outA.append(blk.reshape((h.nbatch, h.c, h.c)) if h.batch else blk.reshape((h.c, h.c)))
+        outI.append([infos[i0 + k].as_dict() for k in range(ns)])
+        a0 += na
+        i0 += ns
+    return outA, outI
+
+
+class GridBatch:
+    """Many microstructures of uneven grids (Sec. 5 computes one effective
+    tensor per microstructure): one batch handle per distinct grid, each on its
+    own CUDA stream, all solved together by lsh_effective_batch.
+
+    phases: list of uint8 arrays / tensors (any grid each); the other arguments
+    as for Handle.  effective() returns the effective tensors in input order."""
+
+    def __init__(self, phases, phase_moduli, physics=ELASTIC, green=FILTERED, precision=MIXED, ref=None,
+                 device=None, max_systems=0):
+        import torch
+        self._torch = torch
+        groups = {}
+        for i, ph in enumerate(phases):
+            groups.setdefault(tuple(ph.shape), []).append(i)
+        self.order = []
+        self.handles = []
+        self.streams = []
+        for shape, idx in sorted(groups.items(), key=lambda kv: -int(np.prod(kv[0])) * len(kv[1])):
+            if isinstance(phases[idx[0]], np.ndarray):
+                stack = torch.from_numpy(np.stack([np.asarray(phases[i], dtype=np.uint8) for i in idx]))
+            else:
+                stack = torch.stack([phases[i] for i in idx])
+            dev = torch.device(device if device is not None else "cuda")
+            st = torch.cuda.Stream(device=dev)
+            self.streams.append(st)
+            self.handles.append(Handle(stack.to(dev), phase_moduli, physics=physics, green=green,
+                                       precision=precision, ref=ref, device=dev, stream=st, batch=True,
+                                       max_systems=max_systems))
+            self.order.append(idx)
+        self.n = len(phases)
+
+    def effective(self, **kw):
+        # the phase uploads ran on the handles' streams: wait for them before solving
+        for st in self.streams:
+            st.synchronize()
+        As, Is = effective_batch(self.handles, **kw)
+        A = [None] * self.n
+        infos = [None] * self.n
+        for idx, Ah, Ih, h in zip(self.order, As, Is, self.handles):
+            for k, i in enumerate(idx):
+                A[i] = Ah[k]
+                infos[i] = Ih[k * h.c:(k + 1) * h.c]
+        return A, infos
+
+    def close(self):
+        for h in self.handles:
+            h.close()
