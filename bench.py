@@ -316,6 +316,153 @@ def run_batch64(args):
     return 0
 
 
+def run_contrast256(args):
+    """The 128^3 sphere packing's centres at 256^3 (radius 16 voxels), inclusion
+    stiffness 10, 100 and 1000 x the matrix: C* of the mixed-precision solver
+    against the plain FP64 solver entry by entry, with both solvers' rates."""
+    import torch
+    from paper_1411_0330_gb300 import lsh
+    from paper_1411_0330_gb300 import microstructures as ms
+    torch.cuda.set_device(0)
+    n = 256
+    _, cen, r = ms.sphere_microstructure(N, 8.0, 0.3, seed=1411)
+    ph = ms.voxelize_spheres(n, cen, r)
+    ph_dev = torch.from_numpy(ph).cuda()
+    V = float(ph.size)
+    out = []
+    for contrast in (10.0, 100.0, 1000.0):
+        mods = np.array([k_mu(1.0, 0.3), k_mu(contrast, 0.2)])
+        row = {"contrast": contrast}
+        res = {}
+        for name, prec in (("mixed", lsh.MIXED), ("fp64", lsh.FP64)):
+            h = lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=prec)
+            h.profile_read(reset=True)
+            dt, (A, infos) = _wall(lambda: h.effective(tol=TOL, maxit=40000))
+            its = sum(i["iters"] for i in infos)
+            res[name] = (A, its, dt)
+            row[name] = {"s": dt, "iterations": its, "voxel_it_per_s": its * V / dt,
+                         "launches": h.profile_read(reset=True)["launches"],
+                         "max_relres": max(i["relres"] for i in infos),
+                         "outer": sum(i["outer"] for i in infos)}
+            h.close()
+            del h
+            torch.cuda.empty_cache()
+        A_mx, A_64 = res["mixed"][0], res["fp64"][0]
+        m = np.abs(A_64).max()
+        row["c_star_fp64_mandel"] = A_64.tolist()
+        row["c_star_abs_err_over_max"] = (np.abs(A_mx - A_64) / m).tolist()
+        e_max, e_true = _cstar_err(A_mx, A_64)
+        row["c_star_max_err"] = e_max
+        row["c_star_max_true_rel_err_entries_ge_1e-3max"] = e_true
+        row["fp64_equivalent_voxel_it_per_s"] = res["fp64"][1] * V / res["mixed"][2]
+        row["speedup_mixed_vs_fp64"] = res["fp64"][2] / res["mixed"][2]
+        out.append(row)
+        print(json.dumps({"contrast": contrast, "err": e_max, "mixed_s": res["mixed"][2],
+                          "fp64_s": res["fp64"][2]}), file=sys.stderr, flush=True)
+    line = {"metric": METRIC, "value": out[0]["fp64_equivalent_voxel_it_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": 1, "warmup": 0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"256^3 isotropic elasticity, the {len(cen)} sphere centres of the 128^3 packing "
+                                   f"at radius 16 vox (f={ph.mean():.4f}), E_i/E_m in 10/100/1000, nu 0.3/0.2, "
+                                   "filtered Gamma, 6 Mandel loads, CG rel.res 1e-10, mixed vs FP64",
+                       "value": "FP64-equivalent rate of the mixed solver at contrast 10",
+                       "timing": "wall clock around the synchronous lsh_effective call, one solve each "
+                                 "(first call: includes the CUDA-graph captures)"},
+            "sweep": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_gradient128(args, nfd=32, hfd=1e-6):
+    """dObj/ds for Obj = C*_1111 + C*_1212 with a per-voxel stiffness scale s ~
+    U(0.5, 2) on the 128^3 packing: the adjoint gradient (torch.autograd through
+    the library), timed, then checked by central differences of the variational
+    estimate of Obj on nfd random voxels (FP64 solves at rel.res 1e-13 warm-started
+    from the unperturbed polarisations)."""
+    import torch
+    from paper_1411_0330_gb300 import lsh, autograd
+    from paper_1411_0330_gb300 import microstructures as ms
+    torch.cuda.set_device(0)
+    ph, mods, nsph = workload()
+    s = ms.scale_field(ph.shape, seed=1412)
+    V = ph.size
+    # reference medium: the usual rule (mu0 = half the smallest shear modulus, nu0 = 0.3)
+    # over the scaled moduli, whose smallest scale is 0.5
+    mu0 = 0.5 * 0.5 * float(mods[:, 1].min())
+    ref = np.array([mu0 * 2.0 * 1.3 / (3.0 * 0.4), mu0])
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.ELASTIC, green=lsh.FILTERED, ref=ref,
+                   scale=torch.from_numpy(s).cuda())
+    # Obj = C*_1111 + C*_1212 = A[0,0] + A[5,5] / 2 in Mandel components
+    W = np.zeros((6, 6))
+    W[0, 0], W[5, 5] = 1.0, 0.5
+
+    def grad_once():
+        st = torch.from_numpy(s).cuda().requires_grad_(True)
+        A = autograd.effective_tensor(st, h, tol=1e-12)
+        obj = (A * torch.from_numpy(W).to(A)).sum()
+        obj.backward()
+        return float(obj), st.grad
+
+    grad_once()
+    dt, (obj, g) = _wall(grad_once)
+    g = g.double().cpu().numpy()
+
+    def obj_var(scale_np, taus):
+        """Variational estimate sum_p W_pp (p.A0 p + h^d (2 b_p.tau_p - tau_p.K tau_p)),
+        returned as per-voxel terms so that differences are taken voxel by voxel."""
+        h.set_microstructure(ph, scale_np)
+        terms = []
+        for j, tau0 in zip((0, 5), taus):
+            load = np.zeros(6)
+            load[j] = 1.0
+            tau, info = h.solve(load, tau=tau0.clone(), tol=1e-13, warm_start=True, maxit=20000)
+            Kt = h.apply(tau)
+            t_np, k_np = tau.cpu().numpy(), Kt.cpu().numpy()
+            # b = p on I0 and tau = 0 off I0, so b.tau = p.tau summed over all voxels
+            terms.append(W[j, j] * (2.0 * t_np[j] - (t_np * k_np).sum(axis=0)))
+        return terms[0] + terms[1]
+
+    rng = np.random.default_rng(1413)
+    vox = rng.choice(V, size=nfd, replace=False)
+    base = []
+    h.set_microstructure(ph, s)
+    for j in (0, 5):
+        load = np.zeros(6)
+        load[j] = 1.0
+        tau, _ = h.solve(load, tol=1e-13)
+        base.append(tau)
+    fd, ad = [], []
+    t0 = time.perf_counter()
+    for v in vox:
+        sp = s.copy().reshape(-1)
+        sm = s.copy().reshape(-1)
+        sp[v] += hfd
+        sm[v] -= hfd
+        # the scale field is stored in FP32: use the steps actually taken
+        step = float(sp[v]) - float(sm[v])
+        dp = obj_var(sp.reshape(s.shape), base)
+        dm = obj_var(sm.reshape(s.shape), base)
+        fd.append(float((dp - dm).sum()) / V / step)
+        ad.append(float(g.reshape(-1)[v]))
+    t_fd = time.perf_counter() - t0
+    fd, ad = np.array(fd), np.array(ad)
+    relerr = np.abs(fd - ad) / np.abs(ad).max()
+    line = {"metric": "adjoint gradient dObj/ds of C*_1111 + C*_1212 (128^3, FP64 solves)", "value": dt,
+            "unit": "s per gradient (6 solves + adjoint contraction)", "n_gpus": 1, "higher_is_better": False,
+            "dtype": "f64 (scale field f32)", "data": "synthetic",
+            "config": {"workload": f"128^3 sphere packing (seed 1411, {nsph} spheres), per-voxel scale "
+                                   "s ~ U(0.5,2) (seed 1412) on the phase moduli, filtered Gamma, tol 1e-12",
+                       "fd": f"central differences of the variational estimate on {nfd} voxels (seed 1413), "
+                             f"h={hfd:g}, FP64 solves at 1e-13 warm-started"},
+            "objective": obj, "fd_vs_adjoint_max_err_over_max_grad": float(relerr.max()),
+            "fd_vs_adjoint_median_err_over_max_grad": float(np.median(relerr)),
+            "grad_abs_max": float(np.abs(g).max()), "fd_seconds": t_fd,
+            "samples": [{"voxel": int(v), "adjoint": a, "fd": f} for v, a, f in zip(vox[:8], ad[:8], fd[:8])]}
+    print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 # ----------------------------------------------------------------- main arm
 def main():
     ap = argparse.ArgumentParser()
@@ -325,9 +472,11 @@ def main():
     ap.add_argument("--impl", default="lsh", choices=["lsh", "reference"])
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="spheres128", choices=["spheres128", "batch64"],
+    ap.add_argument("--workload", default="spheres128",
+                    choices=["spheres128", "batch64", "contrast256", "gradient128"],
                     help="spheres128: the 128^3 sphere packing (default); batch64: 64 microstructures "
-                         "of uneven grids solved together")
+                         "of uneven grids solved together; contrast256: 256^3 mixed vs FP64 at contrasts "
+                         "10/100/1000; gradient128: adjoint gradient of C* and its finite-difference check")
     ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
                     help="small case for ncu: 4 CG iterations of one 128^3 filtered solve, then exit")
     args = ap.parse_args()
@@ -341,6 +490,10 @@ def main():
         return profile_case(args.profile_case)
     if args.workload == "batch64":
         return run_batch64(args)
+    if args.workload == "contrast256":
+        return run_contrast256(args)
+    if args.workload == "gradient128":
+        return run_gradient128(args)
 
     import torch
     import torch.distributed as dist
