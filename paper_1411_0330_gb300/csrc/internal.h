@@ -1,6 +1,7 @@
 // internal.h -- host-side declarations shared by the liblsh translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -17,6 +18,7 @@ namespace lsh {
 // rows of a system) which keeps the per-system reductions block-aligned.
 template <typename T> struct OpArgs {
   int nx, ny, nz, nxh, c;
+  int hs;            // row stride of the half spectrum H (>= nxh; even, so FP32 rows are 16-byte aligned)
   long long V;       // voxels per system
   int S;             // systems in this launch
   int sys0;          // global index of system 0 of this launch
@@ -31,7 +33,7 @@ template <typename T> struct OpArgs {
   const C2<T>* twy;
   const C2<T>* twz;
   const int* posx;   // frequency kx -> position after the x DIF
-  C2<T>* H;          // half spectrum (y, z in digit-reversed positions)
+  C2<T>* H;          // half spectrum [S][c][nz][ny][hs] (kx < nxh used; y, z positions per kofy / kofz)
   const T* gtab;     // Gamma^h (internal basis, scaled by 1/V): [ncoef][nz][ny][nxh]
   int ncoef;
   // local term M_beta = (A_beta - A0)^{-1}, diagonal in the internal basis
@@ -53,6 +55,10 @@ template <typename T> struct OpArgs {
   T invV;
   // register-FFT passes (natural-order y / z frequencies) for lengths 16..256
   int yreg, zreg;
+  // FP32 y pass through the Tensor Memory Accelerator (host pointer to the map)
+  int ytma;
+  const CUtensorMap* tmy;
+  int* fault;  // set by a kernel whose bounded wait ran out
 };
 
 // Thread-block sizes and tile shapes, chosen at setup for one system count.
@@ -104,5 +110,8 @@ template <typename T> void set_smem_attrs_reg();
 template <typename T> void launch_yfft_reg(const OpArgs<T>& a, bool inv, const SolverState* st, cudaStream_t s);
 template <typename T> void launch_zgamma_reg(const OpArgs<T>& a, const SolverState* st, cudaStream_t s);
 bool reg_length(int n);
+void launch_yfft_tma(const OpArgs<float>& a, bool inv, const SolverState* st, cudaStream_t s);
+bool encode_y_map(CUtensorMap* out, void* H, int hs, int ny, long long planes);
+void tma_prepare();
 
 }  // namespace lsh

@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xfwd(OpArgs<T
     const C2<T> z1 = Z[lp * a.lsx + pos[kx]];
     const C2<T> z2 = Z[lp * a.lsx + pos[kx == 0 ? 0 : nx - kx]];
     const long long hrow = row0 + 2 * lp;
-    a.H[hrow * a.nxh + kx] = mkc<T>(h * (z1.x + z2.x), h * (z1.y - z2.y));
-    if (2 * lp + 1 < nr) a.H[(hrow + 1) * a.nxh + kx] = mkc<T>(h * (z1.y + z2.y), h * (z2.x - z1.x));
+    a.H[hrow * a.hs + kx] = mkc<T>(h * (z1.x + z2.x), h * (z1.y - z2.y));
+    if (2 * lp + 1 < nr) a.H[(hrow + 1) * a.hs + kx] = mkc<T>(h * (z1.y + z2.y), h * (z2.x - z1.x));
   }
 }
 
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_yfft(OpArgs<T
   const int kx0 = blockIdx.x * a.TY;
   const int nt = min(a.TY, a.nxh - kx0);
   const int TY = a.TY;
-  C2<T>* __restrict__ Hp = a.H + plane * a.ny * a.nxh + kx0;
+  C2<T>* __restrict__ Hp = a.H + plane * a.ny * a.hs + kx0;
   const int tot = a.ny * TY;
   for (int base = threadIdx.x; base < tot; base += 4 * blockDim.x) {
     C2<T> v[4];
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_yfft(OpArgs<T
     for (int u = 0; u < 4; ++u) {
       const int idx = base + u * blockDim.x;
       const int y = fdiv(idx, TY), t = idx - y * TY;
-      if (idx < tot && t < nt) v[u] = Hp[(long long)y * a.nxh + t];
+      if (idx < tot && t < nt) v[u] = Hp[(long long)y * a.hs + t];
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_yfft(OpArgs<T
   fft_lines<T, INV>(buf, nt, a.lsy, a.py, tw);
   for (int idx = threadIdx.x; idx < tot; idx += blockDim.x) {
     const int y = fdiv(idx, TY), t = idx - y * TY;
-    if (t < nt) Hp[(long long)y * a.nxh + t] = buf[t * a.lsy + y];
+    if (t < nt) Hp[(long long)y * a.hs + t] = buf[t * a.lsy + y];
   }
 }
 
@@ -214,9 +214,10 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs
   const int kx0 = blockIdx.y * a.TZ;
   const int nt = min(a.TZ, a.nxh - kx0);
   const int nz = a.nz, TZ = a.TZ;
-  const long long zstride = (long long)a.ny * a.nxh;  // distance between z planes
+  const long long zstride = (long long)a.ny * a.hs;  // distance between z planes of H
   const long long cstride = zstride * nz;
-  C2<T>* __restrict__ Hp = a.H + (long long)s * NC * cstride + (long long)yp * a.nxh + kx0;
+  const long long gzs = (long long)a.ny * a.nxh, gcs = gzs * nz;  // the same in the Gamma table
+  C2<T>* __restrict__ Hp = a.H + (long long)s * NC * cstride + (long long)yp * a.hs + kx0;
   const int tot = NC * nz * TZ;
   for (int base = threadIdx.x; base < tot; base += 4 * blockDim.x) {
     C2<T> v[4];
@@ -259,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs
       for (int i = 0; i < NC; ++i)
 #pragma unroll
         for (int j = i; j < NC; ++j, ++coef) {
-          const T g = G[coef * cstride + zp * zstride + t];
+          const T g = G[coef * gcs + zp * gzs + t];
           y[i].x += g * v[j].x;
           y[i].y += g * v[j].y;
           if (j != i) {
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xinv(OpArgs<T
   const int nr = a.RY;
   const int npair = (nr + 1) >> 1;
   const long long row0 = (long long)s * a.rps + rloc;
-  const C2<T>* __restrict__ Hb = a.H + row0 * a.nxh;
+  const C2<T>* __restrict__ Hb = a.H + row0 * a.hs;
   // Z = X_a + i X_b over the full line, X(nx - k) = conj X(k) beyond the half
   const int nz_items = npair * a.nxh;
   for (int base = threadIdx.x; base < nz_items; base += 4 * blockDim.x) {
@@ -323,8 +324,8 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xinv(OpArgs<T
       xa[u] = xb[u] = mkc<T>(0, 0);
       if (idx < nz_items) {
         const int lp = fdiv(idx, a.nxh), kx = idx - lp * a.nxh;
-        xa[u] = Hb[(2 * lp) * a.nxh + kx];
-        if (2 * lp + 1 < nr) xb[u] = Hb[(2 * lp + 1) * a.nxh + kx];
+        xa[u] = Hb[(2 * lp) * a.hs + kx];
+        if (2 * lp + 1 < nr) xb[u] = Hb[(2 * lp + 1) * a.hs + kx];
       }
     }
 #pragma unroll
@@ -855,6 +856,12 @@ void launch_xfwd(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* in, 
 
 template <typename T>
 void launch_yfft(const OpArgs<T>& a, const LaunchCfg& L, bool inv, const SolverState* st, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.ytma) {
+      launch_yfft_tma(a, inv, st, s);
+      return;
+    }
+  }
   if (a.yreg) {
     launch_yfft_reg<T>(a, inv, st, s);
     return;

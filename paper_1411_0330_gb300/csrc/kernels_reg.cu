@@ -44,8 +44,8 @@ __global__ void __launch_bounds__(16 * RegPlan<N>::P) k_yfft_reg(OpArgs<T> a, co
     kx = valid ? nreg + (int)(l - plane * nleft) : 0;
     if (valid && st != nullptr && st[plane / (a.c * a.nz)].done) valid = false;
   }
-  C2<T>* __restrict__ Hl = a.H + plane * a.ny * a.nxh + kx;
-  const int rs = a.nxh;  // row stride
+  C2<T>* __restrict__ Hl = a.H + plane * a.ny * a.hs + kx;
+  const int rs = a.hs;  // row stride
   C2<T> v[R1];
   __syncthreads();
   if (!INV) {
@@ -140,9 +140,10 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N>::THREADS, 2)
   const int i = threadIdx.x % TZ, comp = (threadIdx.x / TZ) % NC, t = threadIdx.x / (TZ * NC);
   const int yp = line_yp[i], kx = line_kx[i];
   const bool valid = yp >= 0;
-  const long long zstride = (long long)a.ny * a.nxh;
+  const long long zstride = (long long)a.ny * a.hs;  // z planes of H
   const long long cstride = zstride * N;
-  C2<T>* __restrict__ Hl = a.H + ((long long)s * NC + comp) * cstride + (valid ? (long long)yp * a.nxh + kx : 0);
+  const long long gzs = (long long)a.ny * a.nxh, gcs = gzs * N;  // the same in the Gamma table
+  C2<T>* __restrict__ Hl = a.H + ((long long)s * NC + comp) * cstride + (valid ? (long long)yp * a.hs + kx : 0);
   C2<T>* exl = buf + (comp * TZ + i) * RL::LS;
   C2<T> v[R1];
 #pragma unroll
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N>::THREADS, 2)
 #pragma unroll
     for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
     if (a.onfly) gamma_trunc_onfly<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g);
-    else gamma_table_apply<T, NC>(a.gtab, cstride, kz * zstride + (long long)lyp * a.nxh + line_kx[li], g);
+    else gamma_table_apply<T, NC>(a.gtab, gcs, kz * gzs + (long long)lyp * a.nxh + line_kx[li], g);
 #pragma unroll
     for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
   }

@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <thread>
@@ -78,7 +79,7 @@ template <typename T> void twiddles(int n, std::vector<T>& out) {
 
 // ---------------------------------------------------------------- derived problem data
 struct Derived {
-  int dim, c, nx, ny, nz, nxh, ncoef, physics, green, precision, nphase;
+  int dim, c, nx, ny, nz, nxh, hs, ncoef, physics, green, precision, nphase;
   int B;       // microstructures
   int Smax;    // systems per wave
   long long V;
@@ -112,6 +113,7 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
   if ((long long)d->nx * d->ny * d->nz > (1LL << 31)) return LSH_ERR_UNSUPPORTED_SIZE;
   d->V = (long long)d->nx * d->ny * d->nz;
   d->nxh = d->nx / 2 + 1;
+  d->hs = d->nxh + (d->nxh & 1);
   d->c = pr->physics == LSH_ELASTIC_ISO ? 6 : pr->dim;
   d->ncoef = d->c * (d->c + 1) / 2;
   d->B = pr->nbatch > 1 ? pr->nbatch : 1;
@@ -252,7 +254,7 @@ bool cfg_fits(const LaunchCfg& L) {
 // ---------------------------------------------------------------- workspace layout
 struct Layout {
   size_t off_state, off_partials, off_phase, off_scale, off_act, off_posx, off_kofy, off_kofz, off_sums, off_W;
-  size_t off_tabd, off_tabf, off_loads_d, off_loads_f, off_bb, off_flags;
+  size_t off_tabd, off_tabf, off_loads_d, off_loads_f, off_bb, off_flags, off_fault;
   size_t off_tw_d, off_tw_f;
   size_t off_fd[4], off_Hd, off_gd;
   size_t off_ff[4], off_Hf, off_gf;
@@ -270,7 +272,8 @@ Layout make_layout(const Derived& d) {
   };
   const int S = d.Smax;
   const long long n = (long long)d.c * d.V;  // elements per system
-  const long long nf = (long long)d.nz * d.ny * d.nxh;
+  const long long nf = (long long)d.nz * d.ny * d.nxh;   // Gamma table per coefficient
+  const long long nfh = (long long)d.nz * d.ny * d.hs;  // half spectrum per component
   LaunchCfg Ld = make_cfg<double>(d), Lf = make_cfg<float>(d);
   long long np = std::max<long long>({(long long)S * Ld.grid_x, (long long)S * Lf.grid_x, (long long)S * Ld.ew_per_sys,
                                       (long long)S * Lf.ew_per_sys, (long long)S * d.c * 152,
@@ -292,6 +295,7 @@ Layout make_layout(const Derived& d) {
   l.off_loads_f = take(sizeof(float) * 6 * (size_t)S);
   l.off_bb = take(sizeof(double) * (size_t)S);
   l.off_flags = take((size_t)S);
+  l.off_fault = take(sizeof(int));
   l.off_tw_d = take(sizeof(double2) * (size_t)(d.nx + d.ny + d.nz));
   l.off_tw_f = take(sizeof(float2) * (size_t)(d.nx + d.ny + d.nz));
   // FP64 fields: x, r always; p, q for the FP64 CG (one system's worth of p, q
@@ -301,11 +305,11 @@ Layout make_layout(const Derived& d) {
     const long long ns = (i < 2 || !mixed) ? S : 1;
     l.off_fd[i] = take(sizeof(double) * (size_t)(ns * n));
   }
-  l.off_Hd = take(sizeof(double2) * (size_t)(S * d.c * nf));
+  l.off_Hd = take(sizeof(double2) * (size_t)(S * d.c * nfh));
   l.off_gd = take(sizeof(double) * (size_t)(d.ncoef * nf));
   if (mixed) {
     for (int i = 0; i < 4; ++i) l.off_ff[i] = take(sizeof(float) * (size_t)(S * n));
-    l.off_Hf = take(sizeof(float2) * (size_t)(S * d.c * nf));
+    l.off_Hf = take(sizeof(float2) * (size_t)(S * d.c * nfh));
     l.off_gf = take(sizeof(float) * (size_t)(d.ncoef * nf));
   }
   l.total = o;
@@ -321,6 +325,7 @@ template <typename T> struct PrecBufs {
   SolverState* st = nullptr;  // Smax CG states
   LaunchCfg L{};
   OpArgs<T> a{};
+  CUtensorMap tmy{};          // y-pass tensor map over H (FP32)
 };
 
 }  // namespace
@@ -329,6 +334,8 @@ template <typename T> struct PrecBufs {
 struct lsh_handle {
   Derived d;
   int device = 0;
+  int* fault = nullptr;  // device word set by a kernel whose bounded wait ran out
+  bool no_tma = false;
   Layout lay;
   cudaStream_t stream;
   unsigned char* base;
@@ -414,6 +421,7 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.ny = d.ny;
   a.nz = d.nz;
   a.nxh = d.nxh;
+  a.hs = d.hs;
   a.c = d.c;
   a.V = d.V;
   a.S = d.Smax;
@@ -454,6 +462,11 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.invV = (T)invV;
   a.yreg = reg_length(d.ny) ? 1 : 0;
   a.zreg = (reg_length(d.nz)) ? 1 : 0;
+  a.fault = h->fault;
+  a.ytma = 0;
+  a.tmy = &P.tmy;
+  if (sizeof(T) == 4 && a.yreg && d.nz > 1 && !h->no_tma)
+    a.ytma = encode_y_map(&P.tmy, P.H, d.hs, d.ny, (long long)d.Smax * d.c * d.nz) ? 1 : 0;
   for (int i = 0; i < 6; ++i) a.g0[i] = (T)0;
   if (d.physics == LSH_ELASTIC_ISO) {
     const double K0 = d.ref_user[0], mu0 = d.ref_user[1], lam0 = K0 - 2.0 * mu0 / 3.0;
@@ -691,6 +704,18 @@ lsh_status cg_run(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int maxit, 
   return read_states(h, P.st, S, out.data());
 }
 
+// A kernel that gave up a bounded wait (TMA copies) set the fault word.
+lsh_status check_fault(lsh_handle* h) {
+  int f = 0;
+  LSH_CK(cudaMemcpyAsync(&f, h->fault, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  LSH_CK(cudaStreamSynchronize(h->stream));
+  if (f) {
+    LSH_CK(cudaMemsetAsync(h->fault, 0, sizeof(int), h->stream));
+    return LSH_ERR_CUDA;
+  }
+  return LSH_OK;
+}
+
 // Solve the systems of a wave; the solutions end in pd.x (internal basis).
 // warm: pd.x holds initial guesses.  infos: S entries.
 lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_opts* o, lsh_solve_info* infos) {
@@ -908,6 +933,16 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   h->tabd = (double*)(h->base + l.off_tabd);
   h->bbdev = (double*)(h->base + l.off_bb);
   h->flags = h->base + l.off_flags;
+  h->fault = (int*)(h->base + l.off_fault);
+  if (cudaMemsetAsync(h->fault, 0, sizeof(int), h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return LSH_ERR_CUDA;
+  }
+  {
+    const char* e = getenv("LSH_NO_TMA");
+    h->no_tma = e && e[0] == '1';
+  }
   init_prec<double>(h, h->pd, l.off_fd, l.off_Hd, l.off_gd, l.off_tw_d, l.off_tabd, l.off_loads_d, h->st);
   if (d.precision == LSH_MIXED)
     init_prec<float>(h, h->pf, l.off_ff, l.off_Hf, l.off_gf, l.off_tw_f, l.off_tabf, l.off_loads_f, h->st + d.Smax);
@@ -948,6 +983,7 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   if (copy_microstructure(h, prob->phase, prob->scale, prob->phase_on_host) != LSH_OK) { delete h; return LSH_ERR_CUDA; }
   set_smem_attrs<double>();
   set_smem_attrs<float>();
+  tma_prepare();
   launch_gamma_table<double>(h->pd.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st);
   if (d.precision == LSH_MIXED)
     launch_gamma_table<float>(h->pf.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st);
@@ -1031,6 +1067,7 @@ lsh_status lsh_solve(lsh_handle* h, const double* load, double* tau, const lsh_s
     std::vector<lsh_solve_info> inf(S);
     lsh_status r = solve_wave(h, w, warm, opts, inf.data());
     if (r) return r;
+    if ((r = check_fault(h))) return r;
     if ((r = rotate_or_copy(h, h->pd.x, tau + b0 * n, S, 0))) return r;
     for (int s = 0; s < S; ++s) {
       if (info) info[b0 + s] = inf[s];
@@ -1067,6 +1104,7 @@ lsh_status lsh_effective(lsh_handle* h, const lsh_solve_opts* opts, double* Asta
     std::vector<lsh_solve_info> inf(S);
     lsh_status r = solve_wave(h, w, false, &o, inf.data());
     if (r) return r;
+    if ((r = check_fault(h))) return r;
     // A*_h e_j = A0 e_j + h^d sum_beta tau_beta (Eq. (tau_Astar), Theorem 13)
     launch_comp_sums<double>(h->pd.x, c, d.V, S, h->partials, nblk, h->sums, h->stream);
     h->launches += 2;

@@ -261,6 +261,7 @@ extern "C" lsh_status lsh_apply_noalloc(const lsh_problem* pr, const double* x, 
   a.ny = ny;
   a.nz = nz;
   a.nxh = nxh;
+  a.hs = nxh;
   a.c = c;
   a.V = V;
   a.S = 1;

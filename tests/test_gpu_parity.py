@@ -389,3 +389,27 @@ def test_grid_batch_uneven_grids_match_oracle():
         for k, i in enumerate(idx):
             assert np.array_equal(Ah[k], A[i])
     gb.close()
+
+
+@pytest.mark.parametrize("shape,physics", [((8, 32, 20), 1), ((6, 16, 48), 1), ((12, 64, 10), 0), ((4, 128, 36), 0)])
+def test_fp32_tma_y_pass_matches_register_pass_and_oracle(shape, physics, monkeypatch):
+    """The FP32 y pass through the Tensor Memory Accelerator (whole-column tiles,
+    ragged last tile, padded rows) equals the register-FFT pass bit for bit (same
+    arithmetic) and the oracle to FP32 accuracy."""
+    rng = np.random.default_rng(sum(shape))
+    if physics == 1:
+        ph = (rng.random(shape) < 0.35).astype(np.uint8)
+        mods = EL
+    else:
+        ph = rng.integers(0, 3, shape).astype(np.uint8)
+        mods = _scalar_mods(3, 4)
+    P = oracle.Problem(ph, mods, physics=physics, green=1)
+    x = rng.standard_normal(P.field_shape)
+    xt = torch.from_numpy(x).float().cuda()
+    h_tma = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=1, precision=lsh.MIXED)
+    monkeypatch.setenv("LSH_NO_TMA", "1")
+    h_reg = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=1, precision=lsh.MIXED)
+    y_tma = h_tma.apply(xt)
+    y_reg = h_reg.apply(xt)
+    assert torch.equal(y_tma, y_reg)
+    assert rel(y_tma.cpu().numpy(), oracle.apply(P, x)) < 2e-5
