@@ -509,7 +509,7 @@ def main():
     V = ph.size
     greens = (lsh.FILTERED, lsh.TRUNCATED)
     h64 = [lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=g) for g in greens]
-    hmx = [lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=g, precision=lsh.MIXED) for g in greens]
+    hmx = [lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=g, precision=lsh.MIXED, tune=True) for g in greens]
 
     def step(handles):
         its, res = 0, []
@@ -613,6 +613,7 @@ def main():
                          "iterative-refinement residual), 6 loads batched per launch")
         cfg["value_counting"] = ("N^3 x CG iterations of the plain FP64 solver on the same 12 solves, divided by "
                                  "the mixed solver's time (accuracy-fair); raw inner-iteration rate in mixed")
+        cfg["autotune"] = {"filtered": hmx[0].tune_report, "truncated": hmx[1].tune_report}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_mx / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",

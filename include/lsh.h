@@ -113,6 +113,16 @@ typedef struct lsh_solve_info {
 
 typedef struct lsh_handle lsh_handle;
 
+/* Choices and timings of lsh_autotune. */
+typedef struct lsh_tune_report {
+  int y_variant;  /* FP32 y pass in use: 0 register FFT, 1 TMA tiles                    */
+  int z_variant;  /* FP32 z pass (with Gamma) in use: 0 register FFT; TMA tiles of
+                     1: 4 columns double-buffered, 2: 8 columns, 3: 8 columns double-
+                     buffered                                                          */
+  float y_ms[2];  /* measured time of one launch per candidate (-1: not available)   */
+  float z_ms[4];
+} lsh_tune_report;
+
 /* Bytes of device workspace lsh_setup needs for this problem. */
 lsh_status lsh_workspace_size(const lsh_problem *prob, size_t *bytes);
 
@@ -155,6 +165,21 @@ lsh_status lsh_solve(lsh_handle *h, const double *load, double *tau, const lsh_s
  * of nbatch*c lsh_solve_info.  Synchronous. */
 lsh_status lsh_effective(lsh_handle *h, const lsh_solve_opts *opts, double *Astar, double *tau_all,
                          lsh_solve_info *infos);
+
+/* Autotuner (no counterpart in the paper): times the candidate kernels of
+ * the FP32 y pass and z pass (tile shapes, register-only or TMA-staged, one or
+ * two tile buffers) on the handle's own buffers at its full system count, and
+ * keeps the fastest for the following calls.  Results do not change: the
+ * candidates do the same arithmetic.  Overwrites the handle's spectrum buffer
+ * (call it between solves, not inside one).  FP64 handles: no-op.  rep may be
+ * NULL.  Synchronous. */
+lsh_status lsh_autotune(lsh_handle *h, lsh_tune_report *rep);
+
+/* Select the FP32 y / z pass variants by hand (numbering of lsh_tune_report;
+ * no counterpart in the paper: for tests and measurements).  Returns
+ * LSH_ERR_UNSUPPORTED if a variant is not available for this problem (FP64
+ * handles accept only 0, 0). */
+lsh_status lsh_set_variants(lsh_handle *h, int y_variant, int z_variant);
 
 /* lsh_effective for several handles at once (microstructures of different
  * grids or phase sets; Sec. 5 computes one effective tensor per

@@ -1,5 +1,6 @@
-// gamma_onfly.cuh -- the truncated discrete Green operator evaluated at one
-// frequency inside the z pass (no table), shared by the z-pass kernels.
+// gamma_onfly.cuh -- the discrete Green operator applied at one frequency
+// inside the z pass: from the tabulated symmetric coefficients, or for the
+// truncated operator evaluated on the fly; shared by the z-pass kernels.
 #pragma once
 
 #include "common.cuh"
@@ -92,6 +93,30 @@ __device__ __forceinline__ void gamma_trunc_onfly(const OpArgs<T>& a, int kx, in
   v[3] = cscale<T>(S23, r2);
   v[4] = cscale<T>(S13, r2);
   v[5] = cscale<T>(S12, r2);
+}
+
+// c x c symmetric Gamma^h_k (packed upper triangle, coefficient stride cstride)
+// times the c components of one frequency, in place.
+template <typename T, int NC>
+__device__ __forceinline__ void gamma_table_apply(const T* __restrict__ G, long long cstride, long long off, C2<T>* v) {
+  C2<T> y[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) y[i] = mkc<T>(0, 0);
+  int coef = 0;
+#pragma unroll
+  for (int i = 0; i < NC; ++i)
+#pragma unroll
+    for (int j = i; j < NC; ++j, ++coef) {
+      const T g = G[coef * cstride + off];
+      y[i].x += g * v[j].x;
+      y[i].y += g * v[j].y;
+      if (j != i) {
+        y[j].x += g * v[i].x;
+        y[j].y += g * v[i].y;
+      }
+    }
+#pragma unroll
+  for (int i = 0; i < NC; ++i) v[i] = y[i];
 }
 
 }  // namespace lsh

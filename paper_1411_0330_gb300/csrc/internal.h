@@ -55,9 +55,13 @@ template <typename T> struct OpArgs {
   T invV;
   // register-FFT passes (natural-order y / z frequencies) for lengths 16..256
   int yreg, zreg;
-  // FP32 y pass through the Tensor Memory Accelerator (host pointer to the map)
-  int ytma;
+  // FP32 y and z passes through the Tensor Memory Accelerator (host pointers
+  // to the maps)
+  int ytma;           // 1: TMA y pass
+  int ztma;           // 0: no TMA z pass, else the variant of launch_zgamma_tma
   const CUtensorMap* tmy;
+  const CUtensorMap* tmz;   // z boxes of 4 columns
+  const CUtensorMap* tmz8;  // z boxes of 8 columns
   int* fault;  // set by a kernel whose bounded wait ran out
 };
 
@@ -112,6 +116,9 @@ template <typename T> void launch_zgamma_reg(const OpArgs<T>& a, const SolverSta
 bool reg_length(int n);
 void launch_yfft_tma(const OpArgs<float>& a, bool inv, const SolverState* st, cudaStream_t s);
 bool encode_y_map(CUtensorMap* out, void* H, int hs, int ny, long long planes);
+bool launch_zgamma_tma(const OpArgs<float>& a, int var, const SolverState* st, cudaStream_t s);
+bool tma_z_variant_fits(const OpArgs<float>& a, int var);
+bool encode_z_map(CUtensorMap* out, void* H, int hs, int ny, int nz, int c, long long nsys, int tz);
 void tma_prepare();
 
 }  // namespace lsh

@@ -83,28 +83,6 @@ template <typename T, int NC, int N> struct ZCfg {
   static constexpr int BUF = EXN > GBN ? EXN : GBN;
 };
 
-template <typename T, int NC>
-__device__ __forceinline__ void gamma_table_apply(const T* __restrict__ G, long long cstride, long long off, C2<T>* v) {
-  C2<T> y[NC];
-#pragma unroll
-  for (int i = 0; i < NC; ++i) y[i] = mkc<T>(0, 0);
-  int coef = 0;
-#pragma unroll
-  for (int i = 0; i < NC; ++i)
-#pragma unroll
-    for (int j = i; j < NC; ++j, ++coef) {
-      const T g = G[coef * cstride + off];
-      y[i].x += g * v[j].x;
-      y[i].y += g * v[j].y;
-      if (j != i) {
-        y[j].x += g * v[i].x;
-        y[j].y += g * v[i].y;
-      }
-    }
-#pragma unroll
-  for (int i = 0; i < NC; ++i) v[i] = y[i];
-}
-
 template <typename T, int NC, int N>
 __global__ void __launch_bounds__(ZCfg<T, NC, N>::THREADS, 2)
     k_zgamma_reg(OpArgs<T> a, const SolverState* __restrict__ st, int nrt, int nreg) {

@@ -326,6 +326,9 @@ template <typename T> struct PrecBufs {
   LaunchCfg L{};
   OpArgs<T> a{};
   CUtensorMap tmy{};          // y-pass tensor map over H (FP32)
+  CUtensorMap tmz{};          // z-pass tensor maps over H (FP32), boxes of 4 and 8 columns
+  CUtensorMap tmz8{};
+  bool ytma_ok = false, ztma_ok = false;
 };
 
 }  // namespace
@@ -466,7 +469,15 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.ytma = 0;
   a.tmy = &P.tmy;
   if (sizeof(T) == 4 && a.yreg && d.nz > 1 && !h->no_tma)
-    a.ytma = encode_y_map(&P.tmy, P.H, d.hs, d.ny, (long long)d.Smax * d.c * d.nz) ? 1 : 0;
+    P.ytma_ok = encode_y_map(&P.tmy, P.H, d.hs, d.ny, (long long)d.Smax * d.c * d.nz);
+  a.ytma = P.ytma_ok ? 1 : 0;
+  // the z pass keeps the register kernel unless lsh_autotune measures a TMA variant faster
+  a.ztma = 0;
+  a.tmz = &P.tmz;
+  a.tmz8 = &P.tmz8;
+  if (sizeof(T) == 4 && a.zreg && !h->no_tma)
+    P.ztma_ok = encode_z_map(&P.tmz, P.H, d.hs, d.ny, d.nz, d.c, d.Smax, 4) &&
+                encode_z_map(&P.tmz8, P.H, d.hs, d.ny, d.nz, d.c, d.Smax, 8);
   for (int i = 0; i < 6; ++i) a.g0[i] = (T)0;
   if (d.physics == LSH_ELASTIC_ISO) {
     const double K0 = d.ref_user[0], mu0 = d.ref_user[1], lam0 = K0 - 2.0 * mu0 / 3.0;
@@ -1173,6 +1184,99 @@ lsh_status lsh_effective_grad(lsh_handle* h, const double* tau_all, const double
   lsh_status s = last_launch();
   if (s) return s;
   LSH_CK(cudaStreamSynchronize(h->stream));
+  return LSH_OK;
+}
+
+lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
+  if (!h) return LSH_ERR_INVALID_ARG;
+  lsh_tune_report r;
+  r.y_variant = h->pf.a.ytma;
+  r.z_variant = h->pf.a.ztma;
+  for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
+  for (int k = 0; k < 4; ++k) r.z_ms[k] = -1.f;
+  const Derived& d = h->d;
+  if (d.precision == LSH_MIXED) {
+    PrecBufs<float>& P = h->pf;
+    cudaStream_t s = h->stream;
+    LSH_CK(cudaMemsetAsync(P.H, 0, sizeof(float2) * (size_t)d.Smax * d.c * d.nz * d.ny * d.hs, s));
+    OpArgs<float> a = P.a;
+    cudaEvent_t e0, e1;
+    LSH_CK(cudaEventCreate(&e0));
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+      cudaEventDestroy(e0);
+      cudaGetLastError();
+      return LSH_ERR_CUDA;
+    }
+    // average of 5 launches after 2 untimed ones; -1 if the variant does not run here
+    auto timeit = [&](auto launch) -> float {
+      for (int k = 0; k < 2; ++k)
+        if (!launch()) return -1.f;
+      cudaEventRecord(e0, s);
+      for (int k = 0; k < 5; ++k) launch();
+      cudaEventRecord(e1, s);
+      float ms = -1.f;
+      if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.f;
+      }
+      return ms / 5.f;
+    };
+    if (a.yreg && P.ytma_ok) {
+      for (int v = 0; v < 2; ++v) {
+        a.ytma = v;
+        r.y_ms[v] = timeit([&]() {
+          launch_yfft<float>(a, P.L, false, nullptr, s);
+          return true;
+        });
+      }
+      r.y_variant = (r.y_ms[1] > 0.f && (r.y_ms[0] < 0.f || r.y_ms[1] < r.y_ms[0])) ? 1 : 0;
+      a.ytma = r.y_variant;
+    }
+    if (a.zreg && P.ztma_ok) {
+      int best = 0;
+      for (int v = 0; v < 4; ++v) {
+        a.ztma = v;
+        r.z_ms[v] = timeit([&]() {
+          if (v == 0) {
+            launch_zgamma<float>(a, P.L, nullptr, s);
+            return true;
+          }
+          return launch_zgamma_tma(a, v, nullptr, s);
+        });
+        if (r.z_ms[v] > 0.f && (r.z_ms[best] < 0.f || r.z_ms[v] < r.z_ms[best])) best = v;
+      }
+      r.z_variant = best;
+      a.ztma = best;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    lsh_status st = last_launch();
+    if (st) return st;
+    if (h->fault && (st = check_fault(h))) return st;
+    P.a.ytma = a.ytma;
+    P.a.ztma = a.ztma;
+    h->drop_graphs();  // captured with the previous choices
+  }
+  if (rep) *rep = r;
+  return LSH_OK;
+}
+
+lsh_status lsh_set_variants(lsh_handle* h, int y_variant, int z_variant) {
+  if (!h) return LSH_ERR_INVALID_ARG;
+  if (y_variant < 0 || y_variant > 1 || z_variant < 0 || z_variant > 3) return LSH_ERR_INVALID_ARG;
+  PrecBufs<float>& P = h->pf;
+  if (h->d.precision != LSH_MIXED) return (y_variant || z_variant) ? LSH_ERR_UNSUPPORTED : LSH_OK;
+  if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;
+  if (z_variant > 0 && !P.ztma_ok) return LSH_ERR_UNSUPPORTED;
+  if (z_variant > 0) {
+    // the variant must have a kernel for this length and component count
+    OpArgs<float> a = P.a;
+    a.S = 0;
+    if (!tma_z_variant_fits(a, z_variant)) return LSH_ERR_UNSUPPORTED;
+  }
+  P.a.ytma = y_variant;
+  P.a.ztma = z_variant;
+  h->drop_graphs();
   return LSH_OK;
 }
 

@@ -54,6 +54,11 @@ class _Opts(ctypes.Structure):
                 ("warm_start", ctypes.c_int), ("no_graphs", ctypes.c_int)]
 
 
+class _TuneReport(ctypes.Structure):
+    _fields_ = [("y_variant", ctypes.c_int), ("z_variant", ctypes.c_int), ("y_ms", ctypes.c_float * 2),
+                ("z_ms", ctypes.c_float * 4)]
+
+
 class _Info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("applies64", ctypes.c_int),
                 ("status", ctypes.c_int), ("relres", ctypes.c_double)]
@@ -72,7 +77,8 @@ PASS_NAMES = ["x_forward", "y_forward", "z_gamma", "y_inverse", "x_inverse_local
 
 EXPORTS = ["lsh_workspace_size", "lsh_setup", "lsh_set_microstructure", "lsh_apply", "lsh_solve",
            "lsh_effective", "lsh_effective_grad", "lsh_profile_enable", "lsh_profile_read", "lsh_destroy",
-           "lsh_status_string", "lsh_apply_noalloc", "lsh_effective_batch"]
+           "lsh_status_string", "lsh_apply_noalloc", "lsh_effective_batch", "lsh_autotune",
+           "lsh_set_variants"]
 
 
 def library_path() -> str:
@@ -107,6 +113,8 @@ def load_library(build_if_missing: bool = True):
             lib.lsh_destroy.argtypes = [vp]
             lib.lsh_destroy.restype = None
             lib.lsh_apply_noalloc.argtypes = [P, vp, vp, vp]
+            lib.lsh_autotune.argtypes = [vp, ctypes.POINTER(_TuneReport)]
+            lib.lsh_set_variants.argtypes = [vp, ctypes.c_int, ctypes.c_int]
             lib.lsh_effective_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(_Opts), dp,
                                                 ctypes.POINTER(_Info)]
             _lib = lib
@@ -188,10 +196,11 @@ class Handle:
     ref: reference medium in the same format as one phase, or None (half the softest phase).
     scale: optional per-voxel float32 factor s (A_beta = s_beta A_phase), shaped like phase.
     max_systems: systems (microstructure x load) solved at once; bounds the workspace.
+    tune: run lsh_autotune after setup (times the FP32 y / z pass variants, keeps the fastest).
     """
 
     def __init__(self, phase, phase_moduli, physics=SCALAR, green=TRUNCATED, precision=FP64, ref=None,
-                 scale=None, device=None, stream=None, batch=False, max_systems=0):
+                 scale=None, device=None, stream=None, batch=False, max_systems=0, tune=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("liblsh needs a CUDA device; no CPU fallback exists")
@@ -239,6 +248,7 @@ class Handle:
             _check(self.lib.lsh_setup(ctypes.byref(s), ctypes.c_void_p(self.workspace.data_ptr()), nbytes.value,
                                       ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "lsh_setup")
         self._h = h
+        self.tune_report = self.autotune() if tune else None
 
     # ------------------------------------------------------------------ helpers
     @property
@@ -344,6 +354,19 @@ class Handle:
         out = (A, [i.as_dict() for i in infos])
         return out + (tau_all,) if tau_all is not None else out
 
+    def autotune(self):
+        """Time the FP32 y / z pass variants on this handle and keep the fastest."""
+        r = _TuneReport()
+        self._wait_inputs()
+        _check(self.lib.lsh_autotune(self._h, ctypes.byref(r)), "lsh_autotune")
+        self.tune_report = {"y_variant": r.y_variant, "z_variant": r.z_variant, "y_ms": list(r.y_ms),
+                            "z_ms": list(r.z_ms)}
+        return self.tune_report
+
+    def set_variants(self, y_variant, z_variant):
+        """Force the FP32 y / z pass variants (see lsh_tune_report)."""
+        _check(self.lib.lsh_set_variants(self._h, int(y_variant), int(z_variant)), "lsh_set_variants")
+
     def profile_enable(self, enable=True):
         _check(self.lib.lsh_profile_enable(self._h, 1 if enable else 0), "lsh_profile_enable")
 
@@ -405,7 +428,7 @@ class GridBatch:
     as for Handle.  effective() returns the effective tensors in input order."""
 
     def __init__(self, phases, phase_moduli, physics=ELASTIC, green=FILTERED, precision=MIXED, ref=None,
-                 device=None, max_systems=0):
+                 device=None, max_systems=0, tune=True):
         import torch
         self._torch = torch
         groups = {}
@@ -424,7 +447,7 @@ class GridBatch:
             self.streams.append(st)
             self.handles.append(Handle(stack.to(dev), phase_moduli, physics=physics, green=green,
                                        precision=precision, ref=ref, device=dev, stream=st, batch=True,
-                                       max_systems=max_systems))
+                                       max_systems=max_systems, tune=tune))
             self.order.append(idx)
         self.n = len(phases)
 

@@ -391,11 +391,14 @@ def test_grid_batch_uneven_grids_match_oracle():
     gb.close()
 
 
-@pytest.mark.parametrize("shape,physics", [((8, 32, 20), 1), ((6, 16, 48), 1), ((12, 64, 10), 0), ((4, 128, 36), 0)])
-def test_fp32_tma_y_pass_matches_register_pass_and_oracle(shape, physics, monkeypatch):
-    """The FP32 y pass through the Tensor Memory Accelerator (whole-column tiles,
-    ragged last tile, padded rows) equals the register-FFT pass bit for bit (same
-    arithmetic) and the oracle to FP32 accuracy."""
+@pytest.mark.parametrize("shape,physics", [((8, 32, 20), 1), ((6, 16, 48), 1), ((12, 64, 10), 0), ((4, 128, 36), 0),
+                                           ((16, 12, 10), 1), ((32, 16, 18), 1), ((16, 16, 16), 0),
+                                           ((64, 6, 12), 1)])
+def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkeypatch):
+    """The FP32 y and z passes through the Tensor Memory Accelerator (whole-column
+    tiles, ragged last tile, padded rows, Gamma between the z transforms) equal the
+    register-FFT passes bit for bit (same arithmetic) and the oracle to FP32
+    accuracy."""
     rng = np.random.default_rng(sum(shape))
     if physics == 1:
         ph = (rng.random(shape) < 0.35).astype(np.uint8)
@@ -409,7 +412,16 @@ def test_fp32_tma_y_pass_matches_register_pass_and_oracle(shape, physics, monkey
     h_tma = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=1, precision=lsh.MIXED)
     monkeypatch.setenv("LSH_NO_TMA", "1")
     h_reg = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=1, precision=lsh.MIXED)
-    y_tma = h_tma.apply(xt)
     y_reg = h_reg.apply(xt)
-    assert torch.equal(y_tma, y_reg)
-    assert rel(y_tma.cpu().numpy(), oracle.apply(P, x)) < 2e-5
+    assert rel(y_reg.cpu().numpy(), oracle.apply(P, x)) < 2e-5
+    for zv in range(4):
+        try:
+            h_tma.set_variants(1, zv)
+        except lsh.LSHError as e:
+            assert e.status == lsh.ERR_UNSUPPORTED
+            continue
+        y_tma = h_tma.apply(xt)
+        assert torch.equal(y_tma, y_reg), zv
+    rep = h_tma.autotune()
+    assert rep["z_variant"] in range(4) and rep["y_variant"] in (0, 1)
+    assert torch.equal(h_tma.apply(xt), y_reg)
