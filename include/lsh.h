@@ -118,9 +118,10 @@ typedef struct lsh_tune_report {
   int y_variant;  /* FP32 y pass in use: 0 register FFT, 1 TMA tiles                    */
   int z_variant;  /* FP32 z pass (with Gamma) in use: 0 register FFT; TMA tiles of
                      1: 4 columns double-buffered, 2: 8 columns, 3: 8 columns double-
-                     buffered                                                          */
+                     buffered, 4: 16 columns with the FFT exchange in the tile, 5: the
+                     same with two components per thread                             */
   float y_ms[2];  /* measured time of one launch per candidate (-1: not available)   */
-  float z_ms[4];
+  float z_ms[6];
 } lsh_tune_report;
 
 /* Bytes of device workspace lsh_setup needs for this problem. */

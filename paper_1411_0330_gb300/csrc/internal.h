@@ -62,6 +62,7 @@ template <typename T> struct OpArgs {
   const CUtensorMap* tmy;
   const CUtensorMap* tmz;   // z boxes of 4 columns
   const CUtensorMap* tmz8;  // z boxes of 8 columns
+  const CUtensorMap* tmz16; // z boxes of 16 columns
   int* fault;  // set by a kernel whose bounded wait ran out
 };
 

@@ -277,6 +277,154 @@ __global__ void __launch_bounds__(ZTma<NC, N, TZ, NB>::THREADS, ZTma<NC, N, TZ, 
   }
 }
 
+// Tiles of 16 columns (128-byte rows, the DRAM-friendly width along z): the
+// FFT exchange runs in place in the tile, whose rows of 16 complex values make
+// every warp access two whole 128-byte rows (no bank conflicts) and leave room
+// for two buffers.  CPT components per thread (1 or 2) trades threads for
+// registers.
+template <int NC, int N, int CPT> struct ZTma16 {
+  static constexpr int TZ = 16;
+  static constexpr int P = RegPlan<N>::P;
+  static constexpr int NCG = NC / CPT;  // component groups running together
+  static constexpr int THREADS = TZ * P * NCG;
+  static constexpr int TILE = NC * N * TZ;
+  static constexpr size_t TILE_BYTES = sizeof(float2) * TILE;
+  static constexpr int NB = 2 * TILE_BYTES + sizeof(float2) * N + 128 <= 200 * 1024 ? 2 : 1;
+  static constexpr size_t SMEM = NB * TILE_BYTES + sizeof(float2) * N + 128;
+  static constexpr bool FITS = SMEM <= 226 * 1024 && THREADS <= 1024 && NC % CPT == 0;
+};
+
+template <int NC, int N, int CPT>
+__global__ void __launch_bounds__(ZTma16<NC, N, CPT>::THREADS, 1)
+    k_zgamma_tma16(const __grid_constant__ CUtensorMap tm, OpArgs<float> a, const SolverState* __restrict__ st,
+                   int ntx, long long ntiles) {
+  typedef RegLine<float, N> RL;
+  typedef ZTma16<NC, N, CPT> ZC;
+  constexpr int TZ = 16, P = ZC::P, R1 = RL::R1, NB = ZC::NB, NCG = ZC::NCG;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  unsigned char* base = (unsigned char*)(((uintptr_t)smem_raw + 127) & ~(uintptr_t)127);
+  float2* tile[2] = {reinterpret_cast<float2*>(base),
+                     reinterpret_cast<float2*>(base + (NB - 1) * ZC::TILE_BYTES)};
+  float2* tw = reinterpret_cast<float2*>(base + NB * ZC::TILE_BYTES);
+  __shared__ __align__(8) uint64_t bar[2];
+  __shared__ int fault;
+  for (int u = threadIdx.x; u < N; u += blockDim.x) tw[u] = a.twz[u];
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+    fault = 0;
+  }
+  __syncthreads();
+  const int i = threadIdx.x % TZ, t = (threadIdx.x / TZ) % P, cg = threadIdx.x / (TZ * P);
+  const int S = a.S;
+  const long long gzs = (long long)a.ny * a.nxh, gcs = gzs * N;
+  auto live = [&](long long tl) {
+    if (tl >= ntiles) return false;
+    if (st == nullptr) return true;
+    return st[tl % S].done == 0;
+  };
+  auto coords = [&](long long tl, int& s, int& yp, int& kx0) {
+    s = (int)(tl % S);
+    const long long sp = tl / S;
+    yp = (int)(sp / ntx);
+    kx0 = (int)(sp - (long long)yp * ntx) * TZ;
+  };
+  auto issue = [&](long long tl, int b) {
+    int s, yp, kx0;
+    coords(tl, s, yp, kx0);
+    mbar_expect_tx(&bar[b], (uint32_t)ZC::TILE_BYTES);
+    tma_load_4d(tile[b], &tm, 2 * kx0, yp, 0, s * NC, &bar[b]);
+  };
+  uint32_t par[2] = {0, 0};
+  long long cur = blockIdx.x;
+  bool cur_live = live(cur);
+  if (cur_live && threadIdx.x == 0) issue(cur, 0);
+  int b = 0;
+  while (cur < ntiles) {
+    const long long nxt = cur + gridDim.x;
+    const bool nxt_live = live(nxt);
+    if (NB == 2 && nxt_live && threadIdx.x == 0) {
+      bulk_wait_read_all();
+      issue(nxt, b ^ 1);
+    }
+    if (cur_live) {
+      const bool ok = mbar_wait(&bar[b], par[b]);
+      par[b] ^= 1;
+      if (__syncthreads_or(!ok)) {
+        if (threadIdx.x == 0) fault = 1;
+        break;
+      }
+      int s, yp, kx0;
+      coords(cur, s, yp, kx0);
+      float2* T = tile[b];
+      float2 v[R1];
+#pragma unroll 1
+      for (int k = 0; k < CPT; ++k) {
+        float2* Tl = T + (cg + k * NCG) * N * TZ + i;
+#pragma unroll
+        for (int j = 0; j < R1; ++j) v[j] = Tl[(t + P * j) * TZ];
+        __syncthreads();
+        RL::template fwd_a_s<TZ>(v, t, tw, Tl);
+        __syncthreads();
+        RL::template fwd_b_s<TZ>(v, t, tw, Tl);
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < R1; ++m) Tl[RL::freq(t, m) * TZ] = v[m];
+      }
+      __syncthreads();
+      const int ky = a.kofy[yp];
+      for (int item = threadIdx.x; item < N * TZ; item += ZC::THREADS) {
+        const int kz = item / TZ, li = item - kz * TZ;
+        const int kx = kx0 + li;
+        if (kx >= a.nxh) continue;
+        float2 g[NC];
+#pragma unroll
+        for (int c2 = 0; c2 < NC; ++c2) g[c2] = T[(c2 * N + kz) * TZ + li];
+        if (a.onfly) gamma_trunc_onfly<float, NC>(a, kx, ky, kz, g);
+        else gamma_table_apply<float, NC>(a.gtab, gcs, kz * gzs + (long long)yp * a.nxh + kx, g);
+#pragma unroll
+        for (int c2 = 0; c2 < NC; ++c2) T[(c2 * N + kz) * TZ + li] = g[c2];
+      }
+      __syncthreads();
+#pragma unroll 1
+      for (int k = 0; k < CPT; ++k) {
+        float2* Tl = T + (cg + k * NCG) * N * TZ + i;
+#pragma unroll
+        for (int m = 0; m < R1; ++m) v[m] = Tl[RL::freq(t, m) * TZ];
+        __syncthreads();
+        RL::template inv_a_s<TZ>(v, t, tw, Tl);
+        __syncthreads();
+        RL::template inv_b_s<TZ>(v, t, tw, Tl);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < R1; ++j) Tl[(t + P * j) * TZ] = v[j];
+      }
+      fence_proxy_async();
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        tma_store_4d(&tm, 2 * kx0, yp, 0, s * NC, T);
+        bulk_commit();
+      }
+    }
+    if (NB == 1 && nxt_live && threadIdx.x == 0) {
+      bulk_wait_read_all();
+      issue(nxt, b ^ 1);
+    }
+    cur = nxt;
+    cur_live = nxt_live;
+    b ^= 1;
+  }
+  if (threadIdx.x == 0) {
+    bulk_wait_all();
+    if (fault) {
+      mbar_wait(&bar[0], par[0]);
+      mbar_wait(&bar[1], par[1]);
+      atomicOr(a.fault, 1);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ host side
 namespace {
 
@@ -347,8 +495,44 @@ template <int NC, int N, int TZ, int NB> int z_blocks_per_sm() {
   return n;
 }
 
+template <int NC, int N, int CPT> int z16_blocks_per_sm() {
+  typedef ZTma16<NC, N, CPT> ZC;
+  static int n = []() {
+    int v = 0;
+    if constexpr (ZC::FITS) {
+      cudaFuncSetAttribute(k_zgamma_tma16<NC, N, CPT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZC::SMEM);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_zgamma_tma16<NC, N, CPT>, ZC::THREADS, ZC::SMEM) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        v = 0;
+      }
+    }
+    return v;
+  }();
+  return n;
+}
+
+template <int NC, int N, int CPT>
+bool launch_z16(const OpArgs<float>& a, const SolverState* st, cudaStream_t s) {
+  typedef ZTma16<NC, N, CPT> ZC;
+  if constexpr (!ZC::FITS) {
+    return false;
+  } else {
+    const int bpsm = z16_blocks_per_sm<NC, N, CPT>();
+    if (bpsm < 1) return false;
+    const int ntx = (a.nxh + 15) / 16;
+    const long long ntiles = (long long)a.S * a.ny * ntx;
+    const long long cap = (long long)sm_count() * bpsm;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(ntiles, cap));
+    k_zgamma_tma16<NC, N, CPT><<<grid, ZC::THREADS, ZC::SMEM, s>>>(*a.tmz16, a, st, ntx, ntiles);
+    return true;
+  }
+}
+
 // Launch variant `var` (1: 4 columns double-buffered, 2: 8 columns single
-// buffer, 3: 8 columns double-buffered); false if it does not fit this length.
+// buffer, 3: 8 columns double-buffered, 4: 16 columns in-place exchange, 5:
+// the same with two components per thread); false if it does not fit this
+// length.
 template <int NC, int N, int TZ, int NB>
 bool launch_z_tma_v(const OpArgs<float>& a, const CUtensorMap* tm, const SolverState* st, cudaStream_t s) {
   typedef ZTma<NC, N, TZ, NB> ZC;
@@ -371,6 +555,8 @@ template <int NC, int N> bool launch_z_tma_n(const OpArgs<float>& a, int var, co
     case 1: return launch_z_tma_v<NC, N, 4, 2>(a, a.tmz, st, s);
     case 2: return launch_z_tma_v<NC, N, 8, 1>(a, a.tmz8, st, s);
     case 3: return launch_z_tma_v<NC, N, 8, 2>(a, a.tmz8, st, s);
+    case 4: return launch_z16<NC, N, 1>(a, st, s);
+    case 5: return (NC % 2 == 0) ? launch_z16<NC, N, (NC % 2 == 0 ? 2 : 1)>(a, st, s) : false;
     default: return false;
   }
 }
@@ -389,6 +575,8 @@ template <int NC, int N> void z_prepare_n() {
   z_blocks_per_sm<NC, N, 4, 2>();
   z_blocks_per_sm<NC, N, 8, 1>();
   z_blocks_per_sm<NC, N, 8, 2>();
+  z16_blocks_per_sm<NC, N, 1>();
+  z16_blocks_per_sm<NC, N, (NC % 2 == 0 ? 2 : 1)>();
 }
 
 template <int NC> void z_prepare() {
@@ -416,6 +604,9 @@ template <int NC, int N> bool z_fits_n(int var) {
     case 1: return ZTma<NC, N, 4, 2>::FITS && z_blocks_per_sm<NC, N, 4, 2>() > 0;
     case 2: return ZTma<NC, N, 8, 1>::FITS && z_blocks_per_sm<NC, N, 8, 1>() > 0;
     case 3: return ZTma<NC, N, 8, 2>::FITS && z_blocks_per_sm<NC, N, 8, 2>() > 0;
+    case 4: return ZTma16<NC, N, 1>::FITS && z16_blocks_per_sm<NC, N, 1>() > 0;
+    case 5: return NC % 2 == 0 && ZTma16<NC, N, (NC % 2 == 0 ? 2 : 1)>::FITS &&
+                   z16_blocks_per_sm<NC, N, (NC % 2 == 0 ? 2 : 1)>() > 0;
     default: return false;
   }
 }

@@ -328,6 +328,7 @@ template <typename T> struct PrecBufs {
   CUtensorMap tmy{};          // y-pass tensor map over H (FP32)
   CUtensorMap tmz{};          // z-pass tensor maps over H (FP32), boxes of 4 and 8 columns
   CUtensorMap tmz8{};
+  CUtensorMap tmz16{};
   bool ytma_ok = false, ztma_ok = false;
 };
 
@@ -475,9 +476,11 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.ztma = 0;
   a.tmz = &P.tmz;
   a.tmz8 = &P.tmz8;
+  a.tmz16 = &P.tmz16;
   if (sizeof(T) == 4 && a.zreg && !h->no_tma)
     P.ztma_ok = encode_z_map(&P.tmz, P.H, d.hs, d.ny, d.nz, d.c, d.Smax, 4) &&
-                encode_z_map(&P.tmz8, P.H, d.hs, d.ny, d.nz, d.c, d.Smax, 8);
+                encode_z_map(&P.tmz8, P.H, d.hs, d.ny, d.nz, d.c, d.Smax, 8) &&
+                encode_z_map(&P.tmz16, P.H, d.hs, d.ny, d.nz, d.c, d.Smax, 16);
   for (int i = 0; i < 6; ++i) a.g0[i] = (T)0;
   if (d.physics == LSH_ELASTIC_ISO) {
     const double K0 = d.ref_user[0], mu0 = d.ref_user[1], lam0 = K0 - 2.0 * mu0 / 3.0;
@@ -1193,7 +1196,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   r.y_variant = h->pf.a.ytma;
   r.z_variant = h->pf.a.ztma;
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
-  for (int k = 0; k < 4; ++k) r.z_ms[k] = -1.f;
+  for (int k = 0; k < 6; ++k) r.z_ms[k] = -1.f;
   const Derived& d = h->d;
   if (d.precision == LSH_MIXED) {
     PrecBufs<float>& P = h->pf;
@@ -1234,7 +1237,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
     }
     if (a.zreg && P.ztma_ok) {
       int best = 0;
-      for (int v = 0; v < 4; ++v) {
+      for (int v = 0; v < 6; ++v) {
         a.ztma = v;
         r.z_ms[v] = timeit([&]() {
           if (v == 0) {
@@ -1263,7 +1266,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
 
 lsh_status lsh_set_variants(lsh_handle* h, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
-  if (y_variant < 0 || y_variant > 1 || z_variant < 0 || z_variant > 3) return LSH_ERR_INVALID_ARG;
+  if (y_variant < 0 || y_variant > 1 || z_variant < 0 || z_variant > 5) return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;
   if (h->d.precision != LSH_MIXED) return (y_variant || z_variant) ? LSH_ERR_UNSUPPORTED : LSH_OK;
   if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;

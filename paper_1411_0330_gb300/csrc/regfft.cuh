@@ -75,6 +75,51 @@ template <typename T, int N> struct RegLine {
     }
     Dft<T, R1, true>::run(a, tw, N);
   }
+  // The same four steps with the exchange held in a line of N elements at
+  // stride ST (element e = k1 P + u at ex[e ST]), e.g. in place in a tile whose
+  // columns are ST apart.
+  template <int ST> static __device__ __forceinline__ void fwd_a_s(C2<T>* a, int t, const C2<T>* tw, C2<T>* ex) {
+    Dft<T, R1, false>::run(a, tw, N);
+    if (t != 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < R1; ++k1) a[k1] = cmul<T>(a[k1], tw[t * k1]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) ex[(k1 * P + t) * ST] = a[k1];
+  }
+  template <int ST> static __device__ __forceinline__ void fwd_b_s(C2<T>* a, int t, const C2<T>* tw, const C2<T>* ex) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int k1 = t * Q + q;
+      C2<T> b[P];
+#pragma unroll
+      for (int u = 0; u < P; ++u) b[u] = ex[(k1 * P + u) * ST];
+      Dft<T, P, false>::run(b, tw, N);
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) a[q * P + k2] = b[k2];
+    }
+  }
+  template <int ST> static __device__ __forceinline__ void inv_a_s(const C2<T>* a, int t, const C2<T>* tw, C2<T>* ex) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int k1 = t * Q + q;
+      C2<T> b[P];
+#pragma unroll
+      for (int u = 0; u < P; ++u) b[u] = a[q * P + u];
+      Dft<T, P, true>::run(b, tw, N);
+#pragma unroll
+      for (int u = 0; u < P; ++u) ex[(k1 * P + u) * ST] = b[u];
+    }
+  }
+  template <int ST> static __device__ __forceinline__ void inv_b_s(C2<T>* a, int t, const C2<T>* tw, const C2<T>* ex) {
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) a[k1] = ex[(k1 * P + t) * ST];
+    if (t != 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < R1; ++k1) a[k1] = cmulc<T>(a[k1], tw[t * k1]);
+    }
+    Dft<T, R1, true>::run(a, tw, N);
+  }
   // frequency held in slot m of thread t after fwd_b (and expected by inv_a)
   static __device__ __forceinline__ int freq(int t, int m) { return (t * Q + m / P) + R1 * (m % P); }
 };

@@ -56,7 +56,7 @@ class _Opts(ctypes.Structure):
 
 class _TuneReport(ctypes.Structure):
     _fields_ = [("y_variant", ctypes.c_int), ("z_variant", ctypes.c_int), ("y_ms", ctypes.c_float * 2),
-                ("z_ms", ctypes.c_float * 4)]
+                ("z_ms", ctypes.c_float * 6)]
 
 
 class _Info(ctypes.Structure):
