@@ -64,6 +64,7 @@ template <typename T> struct OpArgs {
   const CUtensorMap* tmz8;  // z boxes of 8 columns
   const CUtensorMap* tmz16; // z boxes of 16 columns
   int* fault;  // set by a kernel whose bounded wait ran out
+  int xreg;    // 1: FP32 inverse x pass on the register FFT (kernels_x.cu)
 };
 
 // Thread-block sizes and tile shapes, chosen at setup for one system count.
@@ -121,5 +122,9 @@ bool launch_zgamma_tma(const OpArgs<float>& a, int var, const SolverState* st, c
 bool tma_z_variant_fits(const OpArgs<float>& a, int var);
 bool encode_z_map(CUtensorMap* out, void* H, int hs, int ny, int nz, int c, long long nsys, int tz);
 void tma_prepare();
+bool launch_xinv_reg(const OpArgs<float>& a, int mode, const float* xin, float* out, SolverState* st,
+                     double* partials, cudaStream_t s);
+void xreg_prepare();
+bool xinv_reg_fits(const OpArgs<float>& a);
 
 }  // namespace lsh

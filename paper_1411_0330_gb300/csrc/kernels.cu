@@ -889,6 +889,9 @@ void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st
 template <typename T>
 void launch_xinv(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* xin, T* out, SolverState* st,
                  double* partials, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.xreg && launch_xinv_reg(a, mode, xin, out, st, partials, s)) return;
+  }
   const int grid = a.S * a.bps;
   constexpr int VV = 16 / sizeof(T);
   if (L.VEC == VV) {

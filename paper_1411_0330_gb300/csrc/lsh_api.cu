@@ -251,6 +251,8 @@ bool cfg_fits(const LaunchCfg& L) {
          L.grid_zy <= 65535;
 }
 
+int rps_of(const Derived& d) { return d.c * d.nz * d.ny; }
+
 // ---------------------------------------------------------------- workspace layout
 struct Layout {
   size_t off_state, off_partials, off_phase, off_scale, off_act, off_posx, off_kofy, off_kofz, off_sums, off_W;
@@ -277,7 +279,7 @@ Layout make_layout(const Derived& d) {
   LaunchCfg Ld = make_cfg<double>(d), Lf = make_cfg<float>(d);
   long long np = std::max<long long>({(long long)S * Ld.grid_x, (long long)S * Lf.grid_x, (long long)S * Ld.ew_per_sys,
                                       (long long)S * Lf.ew_per_sys, (long long)S * d.c * 152,
-                                      (long long)d.B * 1216});
+                                      (long long)d.B * 1216, (long long)S * (rps_of(d) / 2 + 1)});
   l.nparts = np;
   l.off_state = take(sizeof(SolverState) * (size_t)(3 * S + d.B));
   l.off_partials = take(sizeof(double) * (size_t)np);
@@ -467,6 +469,7 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.yreg = reg_length(d.ny) ? 1 : 0;
   a.zreg = (reg_length(d.nz)) ? 1 : 0;
   a.fault = h->fault;
+  a.xreg = 0;  // lsh_autotune measures the register inverse x pass against the shared-memory one
   a.ytma = 0;
   a.tmy = &P.tmy;
   if (sizeof(T) == 4 && a.yreg && d.nz > 1 && !h->no_tma)
@@ -998,6 +1001,7 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   set_smem_attrs<double>();
   set_smem_attrs<float>();
   tma_prepare();
+  xreg_prepare();
   launch_gamma_table<double>(h->pd.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st);
   if (d.precision == LSH_MIXED)
     launch_gamma_table<float>(h->pf.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st);
@@ -1193,8 +1197,10 @@ lsh_status lsh_effective_grad(lsh_handle* h, const double* tau_all, const double
 lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   if (!h) return LSH_ERR_INVALID_ARG;
   lsh_tune_report r;
+  r.x_variant = h->pf.a.xreg;
   r.y_variant = h->pf.a.ytma;
   r.z_variant = h->pf.a.ztma;
+  for (int k = 0; k < 2; ++k) r.x_ms[k] = -1.f;
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
   for (int k = 0; k < 6; ++k) r.z_ms[k] = -1.f;
   const Derived& d = h->d;
@@ -1224,6 +1230,19 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       }
       return ms / 5.f;
     };
+    {
+      // inverse x pass with the local term (apply mode: no reductions, no state)
+      for (int v = 0; v < 2; ++v) {
+        a.xreg = v;
+        r.x_ms[v] = timeit([&]() {
+          if (v == 1) return launch_xinv_reg(a, 0, P.x, P.q, nullptr, nullptr, s);
+          launch_xinv<float>(a, P.L, 0, P.x, P.q, nullptr, nullptr, s);
+          return true;
+        });
+      }
+      r.x_variant = (r.x_ms[1] > 0.f && r.x_ms[1] < r.x_ms[0]) ? 1 : 0;
+      a.xreg = r.x_variant;
+    }
     if (a.yreg && P.ytma_ok) {
       for (int v = 0; v < 2; ++v) {
         a.ytma = v;
@@ -1256,6 +1275,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
     lsh_status st = last_launch();
     if (st) return st;
     if (h->fault && (st = check_fault(h))) return st;
+    P.a.xreg = a.xreg;
     P.a.ytma = a.ytma;
     P.a.ztma = a.ztma;
     h->drop_graphs();  // captured with the previous choices
@@ -1264,11 +1284,13 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   return LSH_OK;
 }
 
-lsh_status lsh_set_variants(lsh_handle* h, int y_variant, int z_variant) {
+lsh_status lsh_set_variants(lsh_handle* h, int x_variant, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
-  if (y_variant < 0 || y_variant > 1 || z_variant < 0 || z_variant > 5) return LSH_ERR_INVALID_ARG;
+  if (x_variant < 0 || x_variant > 1 || y_variant < 0 || y_variant > 1 || z_variant < 0 || z_variant > 5)
+    return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;
-  if (h->d.precision != LSH_MIXED) return (y_variant || z_variant) ? LSH_ERR_UNSUPPORTED : LSH_OK;
+  if (h->d.precision != LSH_MIXED) return (x_variant || y_variant || z_variant) ? LSH_ERR_UNSUPPORTED : LSH_OK;
+  if (x_variant == 1 && !xinv_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;
   if (z_variant > 0 && !P.ztma_ok) return LSH_ERR_UNSUPPORTED;
   if (z_variant > 0) {
@@ -1277,6 +1299,7 @@ lsh_status lsh_set_variants(lsh_handle* h, int y_variant, int z_variant) {
     a.S = 0;
     if (!tma_z_variant_fits(a, z_variant)) return LSH_ERR_UNSUPPORTED;
   }
+  P.a.xreg = x_variant;
   P.a.ytma = y_variant;
   P.a.ztma = z_variant;
   h->drop_graphs();

@@ -94,6 +94,13 @@ __device__ __forceinline__ void tma_store_4d(const CUtensorMap* tm, int c0, int 
                : "memory");
 }
 
+// one contiguous global -> shared copy (addresses 16-byte aligned, bytes a multiple of 16)
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_addr(dst)), "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
 // the shared-memory sources of all committed stores have been read

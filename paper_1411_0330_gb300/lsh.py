@@ -55,8 +55,8 @@ class _Opts(ctypes.Structure):
 
 
 class _TuneReport(ctypes.Structure):
-    _fields_ = [("y_variant", ctypes.c_int), ("z_variant", ctypes.c_int), ("y_ms", ctypes.c_float * 2),
-                ("z_ms", ctypes.c_float * 6)]
+    _fields_ = [("x_variant", ctypes.c_int), ("y_variant", ctypes.c_int), ("z_variant", ctypes.c_int),
+                ("x_ms", ctypes.c_float * 2), ("y_ms", ctypes.c_float * 2), ("z_ms", ctypes.c_float * 6)]
 
 
 class _Info(ctypes.Structure):
@@ -114,7 +114,7 @@ def load_library(build_if_missing: bool = True):
             lib.lsh_destroy.restype = None
             lib.lsh_apply_noalloc.argtypes = [P, vp, vp, vp]
             lib.lsh_autotune.argtypes = [vp, ctypes.POINTER(_TuneReport)]
-            lib.lsh_set_variants.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+            lib.lsh_set_variants.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.lsh_effective_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(_Opts), dp,
                                                 ctypes.POINTER(_Info)]
             _lib = lib
@@ -359,13 +359,14 @@ class Handle:
         r = _TuneReport()
         self._wait_inputs()
         _check(self.lib.lsh_autotune(self._h, ctypes.byref(r)), "lsh_autotune")
-        self.tune_report = {"y_variant": r.y_variant, "z_variant": r.z_variant, "y_ms": list(r.y_ms),
-                            "z_ms": list(r.z_ms)}
+        self.tune_report = {"x_variant": r.x_variant, "y_variant": r.y_variant, "z_variant": r.z_variant,
+                            "x_ms": list(r.x_ms), "y_ms": list(r.y_ms), "z_ms": list(r.z_ms)}
         return self.tune_report
 
-    def set_variants(self, y_variant, z_variant):
-        """Force the FP32 y / z pass variants (see lsh_tune_report)."""
-        _check(self.lib.lsh_set_variants(self._h, int(y_variant), int(z_variant)), "lsh_set_variants")
+    def set_variants(self, x_variant, y_variant, z_variant):
+        """Force the FP32 x / y / z pass variants (see lsh_tune_report)."""
+        _check(self.lib.lsh_set_variants(self._h, int(x_variant), int(y_variant), int(z_variant)),
+               "lsh_set_variants")
 
     def profile_enable(self, enable=True):
         _check(self.lib.lsh_profile_enable(self._h, 1 if enable else 0), "lsh_profile_enable")

@@ -416,12 +416,19 @@ def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkey
     assert rel(y_reg.cpu().numpy(), oracle.apply(P, x)) < 2e-5
     for zv in range(6):
         try:
-            h_tma.set_variants(1, zv)
+            h_tma.set_variants(0, 1, zv)
         except lsh.LSHError as e:
             assert e.status == lsh.ERR_UNSUPPORTED
             continue
         y_tma = h_tma.apply(xt)
         assert torch.equal(y_tma, y_reg), zv
+    # the register inverse x pass: other rounding order than the staged one
+    try:
+        h_tma.set_variants(1, 1, 0)
+        y_x = h_tma.apply(xt)
+        assert rel(y_x.cpu().numpy(), oracle.apply(P, x)) < 2e-5
+    except lsh.LSHError as e:
+        assert e.status == lsh.ERR_UNSUPPORTED
     rep = h_tma.autotune()
-    assert rep["z_variant"] in range(6) and rep["y_variant"] in (0, 1)
-    assert torch.equal(h_tma.apply(xt), y_reg)
+    assert rep["z_variant"] in range(6) and rep["y_variant"] in (0, 1) and rep["x_variant"] in (0, 1)
+    assert rel(h_tma.apply(xt).cpu().numpy(), oracle.apply(P, x)) < 2e-5
