@@ -115,13 +115,15 @@ typedef struct lsh_handle lsh_handle;
 
 /* Choices and timings of lsh_autotune. */
 typedef struct lsh_tune_report {
+  int xf_variant; /* FP32 forward x pass in use: 0 shared-memory stages, 1 register FFT  */
   int x_variant;  /* FP32 inverse x pass in use: 0 shared-memory stages, 1 register FFT  */
   int y_variant;  /* FP32 y pass in use: 0 register FFT, 1 TMA tiles                    */
   int z_variant;  /* FP32 z pass (with Gamma) in use: 0 register FFT; TMA tiles of
                      1: 4 columns double-buffered, 2: 8 columns, 3: 8 columns double-
                      buffered, 4: 16 columns with the FFT exchange in the tile, 5: the
                      same with two components per thread                             */
-  float x_ms[2];  /* measured time of one launch per candidate (-1: not available)   */
+  float xf_ms[2]; /* measured time of one launch per candidate (-1: not available)   */
+  float x_ms[2];
   float y_ms[2];
   float z_ms[6];
 } lsh_tune_report;
@@ -170,7 +172,7 @@ lsh_status lsh_effective(lsh_handle *h, const lsh_solve_opts *opts, double *Asta
                          lsh_solve_info *infos);
 
 /* Autotuner (no counterpart in the paper): times the candidate kernels of
- * the FP32 inverse x pass (shared-memory stages or register FFT), y pass and z
+ * the FP32 x passes (shared-memory stages or register FFT), y pass and z
  * pass (tile shapes, register-only or TMA-staged, one or two tile buffers) on the handle's own buffers at its full system count, and
  * keeps the fastest for the following calls.  Results do not change: the
  * candidates do the same arithmetic.  Overwrites the handle's spectrum buffer
@@ -178,11 +180,11 @@ lsh_status lsh_effective(lsh_handle *h, const lsh_solve_opts *opts, double *Asta
  * NULL.  Synchronous. */
 lsh_status lsh_autotune(lsh_handle *h, lsh_tune_report *rep);
 
-/* Select the FP32 x / y / z pass variants by hand (numbering of lsh_tune_report;
+/* Select the FP32 forward x / inverse x / y / z pass variants by hand (numbering of lsh_tune_report;
  * no counterpart in the paper: for tests and measurements).  Returns
  * LSH_ERR_UNSUPPORTED if a variant is not available for this problem (FP64
- * handles accept only 0, 0, 0). */
-lsh_status lsh_set_variants(lsh_handle *h, int x_variant, int y_variant, int z_variant);
+ * handles accept only zeros). */
+lsh_status lsh_set_variants(lsh_handle *h, int xf_variant, int x_variant, int y_variant, int z_variant);
 
 /* lsh_effective for several handles at once (microstructures of different
  * grids or phase sets; Sec. 5 computes one effective tensor per

@@ -65,6 +65,7 @@ template <typename T> struct OpArgs {
   const CUtensorMap* tmz16; // z boxes of 16 columns
   int* fault;  // set by a kernel whose bounded wait ran out
   int xreg;    // 1: FP32 inverse x pass on the register FFT (kernels_x.cu)
+  int xfreg;   // 1: FP32 forward x pass on the register FFT (kernels_x.cu)
 };
 
 // Thread-block sizes and tile shapes, chosen at setup for one system count.
@@ -126,5 +127,8 @@ bool launch_xinv_reg(const OpArgs<float>& a, int mode, const float* xin, float* 
                      double* partials, cudaStream_t s);
 void xreg_prepare();
 bool xinv_reg_fits(const OpArgs<float>& a);
+bool launch_xfwd_reg(const OpArgs<float>& a, int mode, const float* in, float* x, const float* r, float* p,
+                     const SolverState* st, cudaStream_t s);
+bool xfwd_reg_fits(const OpArgs<float>& a);
 
 }  // namespace lsh

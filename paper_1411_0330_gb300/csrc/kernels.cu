@@ -843,6 +843,9 @@ template <typename T> void set_smem_attrs() {
 template <typename T>
 void launch_xfwd(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* in, T* x, const T* r, T* p,
                  const SolverState* st, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    if (a.xfreg && launch_xfwd_reg(a, mode, in, x, r, p, st, s)) return;
+  }
   const int grid = a.S * a.bps;
   constexpr int VV = 16 / sizeof(T);
   if (L.VEC == VV) {

@@ -1,6 +1,13 @@
-// kernels_x.cu -- the inverse x pass with the local term (FP32, lengths
-// 16..256) on the two-level register FFT.
+// kernels_x.cu -- the x passes (FP32, lengths 16..256) on the two-level
+// register FFT, with bulk copies between HBM and shared memory.
 //
+// Forward: a block owns RY consecutive rows of one system.  The CG prologue
+// (x += alpha p_old, p = r + beta p_old) or the projection on I0 (apply) runs
+// on rows brought in by bulk copies; two real rows form one complex line, the
+// register FFT transforms it, the two Hermitian half rows are split out and
+// one bulk store writes the block's contiguous range of the half spectrum.
+//
+// Inverse:
 // A block owns RY consecutive rows of one system (RY/2 packed lines, P threads
 // per line).  Its rows of the half spectrum are one contiguous range of H,
 // copied to shared memory with 16-byte loads; each thread gathers the R1
@@ -185,7 +192,184 @@ __global__ void __launch_bounds__(256, 2) k_xinv_reg(OpArgs<float> a, const floa
   }
 }
 
+
+template <int N> size_t xfwd_region(int hs) {
+  typedef XReg<N> XC;
+  const size_t a = std::max(sizeof(float) * (size_t)XC::RY * N, sizeof(float2) * (size_t)XC::RY * hs);
+  return (a + 15) & ~(size_t)15;
+}
+template <int N> size_t xfwd_smem(int hs) {
+  typedef XReg<N> XC;
+  const size_t ex = std::max(sizeof(float2) * (size_t)XC::LINES * XC::LS, sizeof(float) * (size_t)XC::RY * XC::OSTR);
+  return 2 * xfwd_region<N>(hs) + ((ex + 15) & ~(size_t)15) + sizeof(float2) * N;
+}
+
+// MODE 0: spectrum of P in (apply).  MODE 1 (CG): x += alpha p_old, p = r + beta
+// p_old (p = r at the first iteration), spectrum of p.
+template <int MODE, int N>
+__global__ void __launch_bounds__(256, 2) k_xfwd_reg(OpArgs<float> a, const float* __restrict__ in,
+                                                     float* __restrict__ x, const float* __restrict__ r,
+                                                     float* __restrict__ p, const SolverState* __restrict__ st,
+                                                     int bps, size_t region) {
+  typedef RegLine<float, N> RL;
+  typedef XReg<N> XC;
+  constexpr int P = XC::P, R1 = RL::R1, RY = XC::RY, OSTR = XC::OSTR, LINES = XC::LINES;
+  const int s = blockIdx.x / bps;
+  if (MODE == 1 && st[s].done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ unsigned char aloc[256];
+  __shared__ __align__(8) uint64_t bar;
+  unsigned char* R0 = smem_raw;           // p (or in) rows; later the packed spectra Zs
+  unsigned char* R1b = smem_raw + region;  // r rows (or phase bytes); later the half-spectrum rows
+  float* PN = reinterpret_cast<float*>(smem_raw + 2 * region);  // padded FFT input rows; later the exchange
+  float2* ex = reinterpret_cast<float2*>(PN);
+  constexpr size_t exa = sizeof(float2) * (size_t)LINES * XC::LS, exr = sizeof(float) * (size_t)RY * OSTR;
+  constexpr size_t exb = exa > exr ? exa : exr;
+  float2* tw = reinterpret_cast<float2*>(smem_raw + 2 * region + ((exb + 15) & ~(size_t)15));
+  for (int u = threadIdx.x; u < N; u += blockDim.x) tw[u] = a.twx[u];
+  if (MODE == 0)
+    for (int u = threadIdx.x; u < a.nphase; u += blockDim.x) aloc[u] = a.act[u];
+  const int blk = blockIdx.x - s * bps;
+  const int rloc = blk * RY;
+  const long long row0 = (long long)s * a.rps + rloc;
+  const int hs = a.hs;
+  const int rows_per_comp = a.nz * a.ny;
+  const int comp = rloc / rows_per_comp;  // the block's rows lie in one component plane
+  const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V;
+  const long long vox0 = (long long)(rloc - comp * rows_per_comp) * N;
+  int k = 0;
+  float alpha = 0.f, beta = 0.f;
+  if (MODE == 1) {
+    k = st[s].iter;
+    alpha = (float)st[s].alpha;
+    beta = (float)st[s].beta;
+  }
+  const uint32_t rows_bytes = (uint32_t)(sizeof(float) * RY * N);
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    if (MODE == 0) {
+      mbar_expect_tx(&bar, rows_bytes + (uint32_t)(RY * N));
+      bulk_load_1d(R0, in + row0 * N, rows_bytes, &bar);
+      bulk_load_1d(R1b, a.phase + pbase + vox0, (uint32_t)(RY * N), &bar);
+    } else if (k == 0) {
+      mbar_expect_tx(&bar, rows_bytes);
+      bulk_load_1d(R1b, r + row0 * N, rows_bytes, &bar);
+    } else {
+      mbar_expect_tx(&bar, 2 * rows_bytes);
+      bulk_load_1d(R0, p + row0 * N, rows_bytes, &bar);
+      bulk_load_1d(R1b, r + row0 * N, rows_bytes, &bar);
+    }
+  }
+  constexpr int NV = N / 4;
+  constexpr int IT = RY * NV / XC::THREADS;
+  static_assert(RY * NV % XC::THREADS == 0, "prologue tiling");
+  float4 x4s[IT];
+  if (MODE == 1 && k > 0) {
+#pragma unroll
+    for (int it = 0; it < IT; ++it) {
+      const int idx = threadIdx.x + it * XC::THREADS;
+      const int row = idx / NV, xx = (idx - row * NV) * 4;
+      x4s[it] = *reinterpret_cast<const float4*>(x + (row0 + row) * N + xx);
+    }
+  }
+  __syncthreads();
+  if (__syncthreads_or(!mbar_wait(&bar, 0))) {
+    if (threadIdx.x == 0) {
+      mbar_wait(&bar, 0);
+      atomicOr(a.fault, 1);
+    }
+    return;
+  }
+  // prologue: the FFT input rows into PN (padded rows)
+#pragma unroll
+  for (int it = 0; it < IT; ++it) {
+    const int idx = threadIdx.x + it * XC::THREADS;
+    const int row = idx / NV, xx = (idx - row * NV) * 4;
+    float4 v;
+    if (MODE == 0) {
+      v = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(R0) + row * N + xx);
+      const uchar4 ph = *reinterpret_cast<const uchar4*>(R1b + row * N + xx);
+      if (!aloc[ph.x]) v.x = 0.f;
+      if (!aloc[ph.y]) v.y = 0.f;
+      if (!aloc[ph.z]) v.z = 0.f;
+      if (!aloc[ph.w]) v.w = 0.f;
+    } else {
+      const float4 r4 = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(R1b) + row * N + xx);
+      const long long g = (row0 + row) * N + xx;
+      if (k == 0) {
+        v = r4;
+      } else {
+        const float4 p4 = *reinterpret_cast<const float4*>(reinterpret_cast<const float*>(R0) + row * N + xx);
+        float4 x4 = x4s[it];
+        x4.x += alpha * p4.x;
+        x4.y += alpha * p4.y;
+        x4.z += alpha * p4.z;
+        x4.w += alpha * p4.w;
+        *reinterpret_cast<float4*>(x + g) = x4;
+        v = make_float4(r4.x + beta * p4.x, r4.y + beta * p4.y, r4.z + beta * p4.z, r4.w + beta * p4.w);
+      }
+      *reinterpret_cast<float4*>(p + g) = v;
+    }
+    *reinterpret_cast<float4*>(PN + row * OSTR + xx) = v;
+  }
+  __syncthreads();
+  const int t = threadIdx.x % P, l = threadIdx.x / P;
+  float2 v[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j)
+    v[j] = make_float2(PN[(2 * l) * OSTR + t + P * j], PN[(2 * l + 1) * OSTR + t + P * j]);
+  __syncthreads();  // PN becomes the exchange area
+  float2* exl = ex + l * XC::LS;
+  RL::fwd_a(v, t, tw, exl);
+  __syncthreads();
+  RL::fwd_b(v, t, tw, exl);
+  // packed spectra of the lines, natural order, padded rows
+  constexpr int ZS = N + 4;
+  float2* Zs = reinterpret_cast<float2*>(R0);
+#pragma unroll
+  for (int m = 0; m < R1; ++m) Zs[l * ZS + RL::freq(t, m)] = v[m];
+  __syncthreads();
+  // split Z = X_a + i X_b into the two Hermitian half rows (zero padding columns)
+  float2* HSo = reinterpret_cast<float2*>(R1b);
+  const int nxh = a.nxh;
+  for (int item = threadIdx.x; item < LINES * hs; item += XC::THREADS) {
+    const int ln = item / hs, kx = item - ln * hs;
+    float2 xa = make_float2(0.f, 0.f), xb = xa;
+    if (kx < nxh) {
+      const float2 z1 = Zs[ln * ZS + kx];
+      const float2 z2 = Zs[ln * ZS + ((N - kx) & (N - 1))];
+      xa = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
+      xb = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
+    }
+    HSo[(2 * ln) * hs + kx] = xa;
+    HSo[(2 * ln + 1) * hs + kx] = xb;
+  }
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bulk_store_1d(a.H + row0 * hs, HSo, (uint32_t)(sizeof(float2) * (size_t)RY * hs));
+    bulk_commit();
+    bulk_wait_all();
+  }
+}
+
 namespace {
+
+template <int N> bool launch_xfwd_reg_n(const OpArgs<float>& a, int mode, const float* in, float* xx, const float* r,
+                                        float* p, const SolverState* st, cudaStream_t s) {
+  typedef XReg<N> XC;
+  if (a.rps % XC::RY != 0 || (a.nz * a.ny) % XC::RY != 0 || (a.hs & 1)) return false;
+  if (mode == 0 && ((uintptr_t)in & 15) != 0) return false;  // bulk copies need 16-byte addresses
+  const int bps = a.rps / XC::RY;
+  const size_t smem = xfwd_smem<N>(a.hs);
+  if (smem > 200 * 1024) return false;
+  const int grid = a.S * bps;
+  const size_t region = xfwd_region<N>(a.hs);
+  if (mode == 0) k_xfwd_reg<0, N><<<grid, XC::THREADS, smem, s>>>(a, in, xx, r, p, st, bps, region);
+  else k_xfwd_reg<1, N><<<grid, XC::THREADS, smem, s>>>(a, in, xx, r, p, st, bps, region);
+  return true;
+}
 
 template <int N> bool launch_xinv_reg_n(const OpArgs<float>& a, int mode, const float* xin, float* out,
                                         SolverState* st, double* partials, cudaStream_t s) {
@@ -205,12 +389,39 @@ template <int N> bool launch_xinv_reg_n(const OpArgs<float>& a, int mode, const 
 
 template <int N> void xreg_attrs() {
   const int mx = 200 * 1024;
+  cudaFuncSetAttribute(k_xfwd_reg<0, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xfwd_reg<1, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xinv_reg<0, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xinv_reg<1, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xinv_reg<2, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 }  // namespace
+
+bool launch_xfwd_reg(const OpArgs<float>& a, int mode, const float* in, float* x, const float* r, float* p,
+                     const SolverState* st, cudaStream_t s) {
+  switch (a.nx) {
+    case 16: return launch_xfwd_reg_n<16>(a, mode, in, x, r, p, st, s);
+    case 32: return launch_xfwd_reg_n<32>(a, mode, in, x, r, p, st, s);
+    case 64: return launch_xfwd_reg_n<64>(a, mode, in, x, r, p, st, s);
+    case 128: return launch_xfwd_reg_n<128>(a, mode, in, x, r, p, st, s);
+    case 256: return launch_xfwd_reg_n<256>(a, mode, in, x, r, p, st, s);
+    default: return false;
+  }
+}
+
+bool xfwd_reg_fits(const OpArgs<float>& a) {
+  switch (a.nx) {
+    case 16: return a.rps % XReg<16>::RY == 0 && (a.nz * a.ny) % XReg<16>::RY == 0 && xfwd_smem<16>(a.hs) <= 200 * 1024;
+    case 32: return a.rps % XReg<32>::RY == 0 && (a.nz * a.ny) % XReg<32>::RY == 0 && xfwd_smem<32>(a.hs) <= 200 * 1024;
+    case 64: return a.rps % XReg<64>::RY == 0 && (a.nz * a.ny) % XReg<64>::RY == 0 && xfwd_smem<64>(a.hs) <= 200 * 1024;
+    case 128:
+      return a.rps % XReg<128>::RY == 0 && (a.nz * a.ny) % XReg<128>::RY == 0 && xfwd_smem<128>(a.hs) <= 200 * 1024;
+    case 256:
+      return a.rps % XReg<256>::RY == 0 && (a.nz * a.ny) % XReg<256>::RY == 0 && xfwd_smem<256>(a.hs) <= 200 * 1024;
+    default: return false;
+  }
+}
 
 bool xinv_reg_fits(const OpArgs<float>& a) {
   switch (a.nx) {

@@ -469,7 +469,8 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.yreg = reg_length(d.ny) ? 1 : 0;
   a.zreg = (reg_length(d.nz)) ? 1 : 0;
   a.fault = h->fault;
-  a.xreg = 0;  // lsh_autotune measures the register inverse x pass against the shared-memory one
+  a.xreg = 0;  // lsh_autotune measures the register x passes against the shared-memory ones
+  a.xfreg = 0;
   a.ytma = 0;
   a.tmy = &P.tmy;
   if (sizeof(T) == 4 && a.yreg && d.nz > 1 && !h->no_tma)
@@ -1198,6 +1199,8 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   if (!h) return LSH_ERR_INVALID_ARG;
   lsh_tune_report r;
   r.x_variant = h->pf.a.xreg;
+  r.xf_variant = h->pf.a.xfreg;
+  for (int k = 0; k < 2; ++k) r.xf_ms[k] = -1.f;
   r.y_variant = h->pf.a.ytma;
   r.z_variant = h->pf.a.ztma;
   for (int k = 0; k < 2; ++k) r.x_ms[k] = -1.f;
@@ -1230,6 +1233,25 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       }
       return ms / 5.f;
     };
+    if (xfwd_reg_fits(a)) {
+      // forward x pass with the CG prologue, on states of a running solve
+      std::vector<SolverState> fake(d.Smax);
+      for (auto& f : fake) {
+        f = SolverState{};
+        f.iter = 1;
+      }
+      LSH_CK(cudaMemcpyAsync(P.st, fake.data(), sizeof(SolverState) * d.Smax, cudaMemcpyHostToDevice, s));
+      for (int v = 0; v < 2; ++v) {
+        a.xfreg = v;
+        r.xf_ms[v] = timeit([&]() {
+          if (v == 1) return launch_xfwd_reg(a, 1, nullptr, P.x, P.r, P.p, P.st, s);
+          launch_xfwd<float>(a, P.L, 1, nullptr, P.x, P.r, P.p, P.st, s);
+          return true;
+        });
+      }
+      r.xf_variant = (r.xf_ms[1] > 0.f && r.xf_ms[1] < r.xf_ms[0]) ? 1 : 0;
+      a.xfreg = r.xf_variant;
+    }
     {
       // inverse x pass with the local term (apply mode: no reductions, no state)
       for (int v = 0; v < 2; ++v) {
@@ -1276,6 +1298,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
     if (st) return st;
     if (h->fault && (st = check_fault(h))) return st;
     P.a.xreg = a.xreg;
+    P.a.xfreg = a.xfreg;
     P.a.ytma = a.ytma;
     P.a.ztma = a.ztma;
     h->drop_graphs();  // captured with the previous choices
@@ -1284,13 +1307,16 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   return LSH_OK;
 }
 
-lsh_status lsh_set_variants(lsh_handle* h, int x_variant, int y_variant, int z_variant) {
+lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
-  if (x_variant < 0 || x_variant > 1 || y_variant < 0 || y_variant > 1 || z_variant < 0 || z_variant > 5)
+  if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 1 || y_variant < 0 || y_variant > 1 ||
+      z_variant < 0 || z_variant > 5)
     return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;
-  if (h->d.precision != LSH_MIXED) return (x_variant || y_variant || z_variant) ? LSH_ERR_UNSUPPORTED : LSH_OK;
+  if (h->d.precision != LSH_MIXED)
+    return (xf_variant || x_variant || y_variant || z_variant) ? LSH_ERR_UNSUPPORTED : LSH_OK;
   if (x_variant == 1 && !xinv_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
+  if (xf_variant == 1 && !xfwd_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;
   if (z_variant > 0 && !P.ztma_ok) return LSH_ERR_UNSUPPORTED;
   if (z_variant > 0) {
@@ -1300,6 +1326,7 @@ lsh_status lsh_set_variants(lsh_handle* h, int x_variant, int y_variant, int z_v
     if (!tma_z_variant_fits(a, z_variant)) return LSH_ERR_UNSUPPORTED;
   }
   P.a.xreg = x_variant;
+  P.a.xfreg = xf_variant;
   P.a.ytma = y_variant;
   P.a.ztma = z_variant;
   h->drop_graphs();

@@ -55,8 +55,9 @@ class _Opts(ctypes.Structure):
 
 
 class _TuneReport(ctypes.Structure):
-    _fields_ = [("x_variant", ctypes.c_int), ("y_variant", ctypes.c_int), ("z_variant", ctypes.c_int),
-                ("x_ms", ctypes.c_float * 2), ("y_ms", ctypes.c_float * 2), ("z_ms", ctypes.c_float * 6)]
+    _fields_ = [("xf_variant", ctypes.c_int), ("x_variant", ctypes.c_int), ("y_variant", ctypes.c_int),
+                ("z_variant", ctypes.c_int), ("xf_ms", ctypes.c_float * 2), ("x_ms", ctypes.c_float * 2),
+                ("y_ms", ctypes.c_float * 2), ("z_ms", ctypes.c_float * 6)]
 
 
 class _Info(ctypes.Structure):
@@ -114,7 +115,7 @@ def load_library(build_if_missing: bool = True):
             lib.lsh_destroy.restype = None
             lib.lsh_apply_noalloc.argtypes = [P, vp, vp, vp]
             lib.lsh_autotune.argtypes = [vp, ctypes.POINTER(_TuneReport)]
-            lib.lsh_set_variants.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.lsh_set_variants.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
             lib.lsh_effective_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(_Opts), dp,
                                                 ctypes.POINTER(_Info)]
             _lib = lib
@@ -359,13 +360,14 @@ class Handle:
         r = _TuneReport()
         self._wait_inputs()
         _check(self.lib.lsh_autotune(self._h, ctypes.byref(r)), "lsh_autotune")
-        self.tune_report = {"x_variant": r.x_variant, "y_variant": r.y_variant, "z_variant": r.z_variant,
-                            "x_ms": list(r.x_ms), "y_ms": list(r.y_ms), "z_ms": list(r.z_ms)}
+        self.tune_report = {"xf_variant": r.xf_variant, "x_variant": r.x_variant, "y_variant": r.y_variant,
+                            "z_variant": r.z_variant, "xf_ms": list(r.xf_ms), "x_ms": list(r.x_ms),
+                            "y_ms": list(r.y_ms), "z_ms": list(r.z_ms)}
         return self.tune_report
 
-    def set_variants(self, x_variant, y_variant, z_variant):
-        """Force the FP32 x / y / z pass variants (see lsh_tune_report)."""
-        _check(self.lib.lsh_set_variants(self._h, int(x_variant), int(y_variant), int(z_variant)),
+    def set_variants(self, xf_variant, x_variant, y_variant, z_variant):
+        """Force the FP32 forward x / inverse x / y / z pass variants (see lsh_tune_report)."""
+        _check(self.lib.lsh_set_variants(self._h, int(xf_variant), int(x_variant), int(y_variant), int(z_variant)),
                "lsh_set_variants")
 
     def profile_enable(self, enable=True):

@@ -416,19 +416,40 @@ def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkey
     assert rel(y_reg.cpu().numpy(), oracle.apply(P, x)) < 2e-5
     for zv in range(6):
         try:
-            h_tma.set_variants(0, 1, zv)
+            h_tma.set_variants(0, 0, 1, zv)
         except lsh.LSHError as e:
             assert e.status == lsh.ERR_UNSUPPORTED
             continue
         y_tma = h_tma.apply(xt)
         assert torch.equal(y_tma, y_reg), zv
-    # the register inverse x pass: other rounding order than the staged one
-    try:
-        h_tma.set_variants(1, 1, 0)
+    # the register x passes: other rounding order than the staged ones
+    for xf, xv in ((1, 0), (0, 1), (1, 1)):
+        try:
+            h_tma.set_variants(xf, xv, 1, 0)
+        except lsh.LSHError as e:
+            assert e.status == lsh.ERR_UNSUPPORTED
+            continue
         y_x = h_tma.apply(xt)
-        assert rel(y_x.cpu().numpy(), oracle.apply(P, x)) < 2e-5
-    except lsh.LSHError as e:
-        assert e.status == lsh.ERR_UNSUPPORTED
+        assert rel(y_x.cpu().numpy(), oracle.apply(P, x)) < 2e-5, (xf, xv)
     rep = h_tma.autotune()
     assert rep["z_variant"] in range(6) and rep["y_variant"] in (0, 1) and rep["x_variant"] in (0, 1)
+    assert rep["xf_variant"] in (0, 1)
     assert rel(h_tma.apply(xt).cpu().numpy(), oracle.apply(P, x)) < 2e-5
+
+
+@pytest.mark.parametrize("variants", [(0, 0, 0, 0), (1, 1, 1, 0), (1, 1, 1, 4), (0, 1, 0, 1)])
+def test_mixed_solver_with_each_kernel_variant(variants):
+    """The mixed-precision solver (FP32 CG on the forced x / y / z kernel variants,
+    FP64 refinement) reaches the oracle's C* to the mixed tolerance whichever
+    variants run; unavailable ones are refused with LSH_ERR_UNSUPPORTED."""
+    ph, _, _ = ms.sphere_microstructure(32, 4.0, 0.25, seed=77)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
+    try:
+        h.set_variants(*variants)
+    except lsh.LSHError as e:
+        assert e.status == lsh.ERR_UNSUPPORTED
+        pytest.skip("variant not available for this grid")
+    A, infos = h.effective(tol=1e-10)
+    Ao, _ = oracle.effective(oracle.Problem(ph, EL, physics=1, green=1), tol=1e-13)
+    assert rel(A, Ao) < 1e-8, rel(A, Ao)
+    assert all(i["status"] == 0 for i in infos)
