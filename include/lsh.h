@@ -93,7 +93,8 @@ typedef struct lsh_solve_opts {
   int maxit;         /* iteration limit (FP64 CG iterations, or inner iterations summed) */
   int solver;        /* LSH_SOLVER_AUTO or LSH_SOLVER_CG                                 */
   double inner_tol;  /* LSH_MIXED: relative residual reduction of each inner solve
-                        (<= 0 selects 1e-4)                                              */
+                        (<= 0 selects 0.5 sqrt(tol) within [1e-6, 1e-3]: two
+                        refinement steps)                                               */
   int max_outer;     /* LSH_MIXED: refinement steps (<= 0 selects 30)                    */
   int check_every;   /* iterations between host convergence checks (<= 0 selects 8)     */
   int warm_start;    /* lsh_solve: tau holds the initial guess on entry                  */
@@ -125,7 +126,7 @@ typedef struct lsh_tune_report {
   float xf_ms[2]; /* measured time of one launch per candidate (-1: not available)   */
   float x_ms[2];
   float y_ms[2];
-  float z_ms[6];
+  float z_ms[7];
 } lsh_tune_report;
 
 /* Bytes of device workspace lsh_setup needs for this problem. */

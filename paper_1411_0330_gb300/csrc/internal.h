@@ -58,7 +58,7 @@ template <typename T> struct OpArgs {
   // FP32 y and z passes through the Tensor Memory Accelerator (host pointers
   // to the maps)
   int ytma;           // 1: TMA y pass
-  int ztma;           // 0: no TMA z pass, else the variant of launch_zgamma_tma
+  int ztma;           // 0: register z pass; 1..5: the variant of launch_zgamma_tma; 6: register, 4 columns
   const CUtensorMap* tmy;
   const CUtensorMap* tmz;   // z boxes of 4 columns
   const CUtensorMap* tmz8;  // z boxes of 8 columns
@@ -115,7 +115,7 @@ void launch_scale_grad(const double* tau_all, const double* W, const unsigned ch
 template <typename T> void set_smem_attrs();
 template <typename T> void set_smem_attrs_reg();
 template <typename T> void launch_yfft_reg(const OpArgs<T>& a, bool inv, const SolverState* st, cudaStream_t s);
-template <typename T> void launch_zgamma_reg(const OpArgs<T>& a, const SolverState* st, cudaStream_t s);
+template <typename T> void launch_zgamma_reg(const OpArgs<T>& a, const SolverState* st, cudaStream_t s, int tz);
 bool reg_length(int n);
 void launch_yfft_tma(const OpArgs<float>& a, bool inv, const SolverState* st, cudaStream_t s);
 bool encode_y_map(CUtensorMap* out, void* H, int hs, int ny, long long planes);

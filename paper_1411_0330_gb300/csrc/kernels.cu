@@ -877,10 +877,10 @@ void launch_yfft(const OpArgs<T>& a, const LaunchCfg& L, bool inv, const SolverS
 template <typename T>
 void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (a.ztma && launch_zgamma_tma(a, a.ztma, st, s)) return;
+    if (a.ztma >= 1 && a.ztma <= 5 && launch_zgamma_tma(a, a.ztma, st, s)) return;
   }
   if (a.zreg) {
-    launch_zgamma_reg<T>(a, st, s);
+    launch_zgamma_reg<T>(a, st, s, (sizeof(T) == 4 && a.ztma == 6) ? 4 : 0);
     return;
   }
   dim3 g(a.S, L.grid_zx, L.grid_zy);

@@ -72,8 +72,9 @@ __global__ void __launch_bounds__(16 * RegPlan<N>::P) k_yfft_reg(OpArgs<T> a, co
 }
 
 // ------------------------------------------------------------------ z pass + Gamma
-template <typename T, int NC, int N> struct ZCfg {
-  static constexpr int TZ = (sizeof(T) == 8 || N >= 256) ? 4 : 8;
+template <typename T, int NC, int N, int TZV = 0> struct ZCfg {
+  // TZV = 0: 8 columns per block (4 in FP64 or for length 256); else TZV columns
+  static constexpr int TZ = TZV > 0 ? TZV : ((sizeof(T) == 8 || N >= 256) ? 4 : 8);
   static constexpr int W = 128 / (int)sizeof(C2<T>);  // complex values per shared wavefront
   static constexpr int KS0 = NC * TZ;
   static constexpr int KS = KS0 + ((TZ - KS0 % W) % W + W) % W;  // KS = TZ (mod W)
@@ -83,11 +84,11 @@ template <typename T, int NC, int N> struct ZCfg {
   static constexpr int BUF = EXN > GBN ? EXN : GBN;
 };
 
-template <typename T, int NC, int N>
-__global__ void __launch_bounds__(ZCfg<T, NC, N>::THREADS, 2)
+template <typename T, int NC, int N, int TZV>
+__global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS, ZCfg<T, NC, N, TZV>::THREADS <= 192 ? 4 : 2)
     k_zgamma_reg(OpArgs<T> a, const SolverState* __restrict__ st, int nrt, int nreg) {
   typedef RegLine<T, N> RL;
-  typedef ZCfg<T, NC, N> ZC;
+  typedef ZCfg<T, NC, N, TZV> ZC;
   constexpr int TZ = ZC::TZ, P = RL::P, R1 = RL::R1, KS = ZC::KS;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
@@ -187,35 +188,45 @@ template <typename T> void launch_yfft_reg(const OpArgs<T>& a, bool inv, const S
   else launch_y_reg<T, false>(a, st, s);
 }
 
-template <typename T, int NC, int N> void launch_z_n(const OpArgs<T>& a, const SolverState* st, cudaStream_t s) {
-  typedef ZCfg<T, NC, N> ZC;
+template <typename T, int NC, int N, int TZV> void launch_z_n(const OpArgs<T>& a, const SolverState* st, cudaStream_t s) {
+  typedef ZCfg<T, NC, N, TZV> ZC;
   const int nrt = a.nxh / ZC::TZ, nreg = nrt * ZC::TZ;
   const int ntiles = a.ny * nrt + (a.ny * (a.nxh - nreg) + ZC::TZ - 1) / ZC::TZ;
   const size_t smem = sizeof(C2<T>) * (N + ZC::BUF);
-  k_zgamma_reg<T, NC, N><<<dim3(a.S, ntiles), ZC::THREADS, smem, s>>>(a, st, nrt, nreg);
+  k_zgamma_reg<T, NC, N, TZV><<<dim3(a.S, ntiles), ZC::THREADS, smem, s>>>(a, st, nrt, nreg);
 }
 
-template <typename T, int NC> void launch_z_nc(const OpArgs<T>& a, const SolverState* st, cudaStream_t s) {
+template <typename T, int NC, int TZV> void launch_z_nc(const OpArgs<T>& a, const SolverState* st, cudaStream_t s) {
   switch (a.nz) {
-    case 16: launch_z_n<T, NC, 16>(a, st, s); break;
-    case 32: launch_z_n<T, NC, 32>(a, st, s); break;
-    case 64: launch_z_n<T, NC, 64>(a, st, s); break;
-    case 128: launch_z_n<T, NC, 128>(a, st, s); break;
-    default: launch_z_n<T, NC, 256>(a, st, s); break;
+    case 16: launch_z_n<T, NC, 16, TZV>(a, st, s); break;
+    case 32: launch_z_n<T, NC, 32, TZV>(a, st, s); break;
+    case 64: launch_z_n<T, NC, 64, TZV>(a, st, s); break;
+    case 128: launch_z_n<T, NC, 128, TZV>(a, st, s); break;
+    default: launch_z_n<T, NC, 256, TZV>(a, st, s); break;
   }
 }
 
-template <typename T> void launch_zgamma_reg(const OpArgs<T>& a, const SolverState* st, cudaStream_t s) {
-  if (a.c == 6) launch_z_nc<T, 6>(a, st, s);
-  else if (a.c == 3) launch_z_nc<T, 3>(a, st, s);
-  else launch_z_nc<T, 2>(a, st, s);
+template <typename T, int TZV> void launch_z_tz(const OpArgs<T>& a, const SolverState* st, cudaStream_t s) {
+  if (a.c == 6) launch_z_nc<T, 6, TZV>(a, st, s);
+  else if (a.c == 3) launch_z_nc<T, 3, TZV>(a, st, s);
+  else launch_z_nc<T, 2, TZV>(a, st, s);
+}
+
+// tz = 4: blocks of 4 columns (FP32 autotuner candidate); otherwise the default width
+template <typename T> void launch_zgamma_reg(const OpArgs<T>& a, const SolverState* st, cudaStream_t s, int tz) {
+  if (sizeof(T) == 4 && tz == 4) launch_z_tz<T, 4>(a, st, s);
+  else launch_z_tz<T, 0>(a, st, s);
 }
 
 // dynamic shared memory of one instantiation (static shared memory comes on top
 // of it, so the attribute is set to exactly what the launch asks for)
 template <typename T, int NC, int N> void attr_z_n() {
-  const int bytes = (int)(sizeof(C2<T>) * (N + ZCfg<T, NC, N>::BUF));
-  cudaFuncSetAttribute(k_zgamma_reg<T, NC, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  const int bytes = (int)(sizeof(C2<T>) * (N + ZCfg<T, NC, N, 0>::BUF));
+  cudaFuncSetAttribute(k_zgamma_reg<T, NC, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (sizeof(T) == 4) {
+    const int b4 = (int)(sizeof(C2<T>) * (N + ZCfg<T, NC, N, 4>::BUF));
+    cudaFuncSetAttribute(k_zgamma_reg<T, NC, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b4);
+  }
 }
 template <typename T, bool INV, int N> void attr_y_n() {
   const int bytes = (int)(sizeof(C2<T>) * (N + 16 * RegLine<T, N>::LS));
@@ -247,7 +258,7 @@ template void set_smem_attrs_reg<float>();
 
 template void launch_yfft_reg<double>(const OpArgs<double>&, bool, const SolverState*, cudaStream_t);
 template void launch_yfft_reg<float>(const OpArgs<float>&, bool, const SolverState*, cudaStream_t);
-template void launch_zgamma_reg<double>(const OpArgs<double>&, const SolverState*, cudaStream_t);
-template void launch_zgamma_reg<float>(const OpArgs<float>&, const SolverState*, cudaStream_t);
+template void launch_zgamma_reg<double>(const OpArgs<double>&, const SolverState*, cudaStream_t, int);
+template void launch_zgamma_reg<float>(const OpArgs<float>&, const SolverState*, cudaStream_t, int);
 
 }  // namespace lsh

@@ -782,7 +782,9 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
     // mixed precision: iterative refinement, FP64 residual, FP32 inner CG
     PrecBufs<float>& Pf = h->pf;
     const OpArgs<float> af = wave_args<float>(h, w);
-    const double itol = o && o->inner_tol > 0 ? o->inner_tol : 1e-4;
+    // default: two refinement steps reach tol (each inner solve reduces the
+    // residual by 0.5 sqrt(tol)), within what FP32 CG resolves
+    const double itol = o && o->inner_tol > 0 ? o->inner_tol : std::min(1e-3, std::max(1e-6, 0.5 * std::sqrt(tol)));
     const int max_outer = o && o->max_outer > 0 ? o->max_outer : 30;
     std::vector<double> rr(S);
     SolverState* sres = h->st + 2 * d.Smax;
@@ -1205,7 +1207,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   r.z_variant = h->pf.a.ztma;
   for (int k = 0; k < 2; ++k) r.x_ms[k] = -1.f;
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
-  for (int k = 0; k < 6; ++k) r.z_ms[k] = -1.f;
+  for (int k = 0; k < 7; ++k) r.z_ms[k] = -1.f;
   const Derived& d = h->d;
   if (d.precision == LSH_MIXED) {
     PrecBufs<float>& P = h->pf;
@@ -1278,10 +1280,10 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
     }
     if (a.zreg && P.ztma_ok) {
       int best = 0;
-      for (int v = 0; v < 6; ++v) {
+      for (int v = 0; v < 7; ++v) {
         a.ztma = v;
         r.z_ms[v] = timeit([&]() {
-          if (v == 0) {
+          if (v == 0 || v == 6) {
             launch_zgamma<float>(a, P.L, nullptr, s);
             return true;
           }
@@ -1310,7 +1312,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
 lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
   if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 1 || y_variant < 0 || y_variant > 1 ||
-      z_variant < 0 || z_variant > 5)
+      z_variant < 0 || z_variant > 6)
     return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;
   if (h->d.precision != LSH_MIXED)
@@ -1318,8 +1320,9 @@ lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_
   if (x_variant == 1 && !xinv_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (xf_variant == 1 && !xfwd_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;
-  if (z_variant > 0 && !P.ztma_ok) return LSH_ERR_UNSUPPORTED;
-  if (z_variant > 0) {
+  if (z_variant == 6 && !P.a.zreg) return LSH_ERR_UNSUPPORTED;
+  if (z_variant >= 1 && z_variant <= 5 && !P.ztma_ok) return LSH_ERR_UNSUPPORTED;
+  if (z_variant >= 1 && z_variant <= 5) {
     // the variant must have a kernel for this length and component count
     OpArgs<float> a = P.a;
     a.S = 0;
