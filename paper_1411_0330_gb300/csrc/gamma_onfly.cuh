@@ -119,4 +119,34 @@ __device__ __forceinline__ void gamma_table_apply(const T* __restrict__ G, long 
   for (int i = 0; i < NC; ++i) v[i] = y[i];
 }
 
+// The same product split in two: the coefficients of one frequency loaded into
+// registers (so that the loads of the next frequency can be in flight while
+// this one is applied), then applied.
+template <typename T, int NC>
+__device__ __forceinline__ void gamma_coef_load(const T* __restrict__ G, long long cstride, long long off,
+                                                T* gc) {
+#pragma unroll
+  for (int c = 0; c < NC * (NC + 1) / 2; ++c) gc[c] = G[c * cstride + off];
+}
+template <typename T, int NC> __device__ __forceinline__ void gamma_coef_apply(const T* gc, C2<T>* v) {
+  C2<T> y[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) y[i] = mkc<T>(0, 0);
+  int coef = 0;
+#pragma unroll
+  for (int i = 0; i < NC; ++i)
+#pragma unroll
+    for (int j = i; j < NC; ++j, ++coef) {
+      const T g = gc[coef];
+      y[i].x += g * v[j].x;
+      y[i].y += g * v[j].y;
+      if (j != i) {
+        y[j].x += g * v[i].x;
+        y[j].y += g * v[i].y;
+      }
+    }
+#pragma unroll
+  for (int i = 0; i < NC; ++i) v[i] = y[i];
+}
+
 }  // namespace lsh

@@ -18,7 +18,7 @@ namespace lsh {
 // rows of a system) which keeps the per-system reductions block-aligned.
 template <typename T> struct OpArgs {
   int nx, ny, nz, nxh, c;
-  int hs;            // row stride of the half spectrum H (>= nxh; even, so FP32 rows are 16-byte aligned)
+  int hs;            // row stride of the half spectrum H (nxh rounded up to 4: 32-byte FP32 rows)
   long long V;       // voxels per system
   int S;             // systems in this launch
   int sys0;          // global index of system 0 of this launch

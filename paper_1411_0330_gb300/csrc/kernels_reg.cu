@@ -135,17 +135,49 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS, ZCfg<T, NC, N, T
 #pragma unroll
   for (int m = 0; m < R1; ++m) buf[RL::freq(t, m) * KS + comp * TZ + i] = v[m];
   __syncthreads();
-  for (int item = threadIdx.x; item < N * TZ; item += blockDim.x) {
-    const int kz = item / TZ, li = item - kz * TZ;
-    const int lyp = line_yp[li];
-    if (lyp < 0) continue;
-    C2<T> g[NC];
+  if (a.onfly) {
+    for (int item = threadIdx.x; item < N * TZ; item += blockDim.x) {
+      const int kz = item / TZ, li = item - kz * TZ;
+      const int lyp = line_yp[li];
+      if (lyp < 0) continue;
+      C2<T> g[NC];
 #pragma unroll
-    for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
-    if (a.onfly) gamma_trunc_onfly<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g);
-    else gamma_table_apply<T, NC>(a.gtab, gcs, kz * gzs + (long long)lyp * a.nxh + line_kx[li], g);
+      for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
+      gamma_trunc_onfly<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g);
 #pragma unroll
-    for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
+      for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
+    }
+  } else {
+    // tabulated Gamma^h_k: the coefficients of a thread's next frequency are
+    // loaded while the current one is applied
+    constexpr int NCO = NC * (NC + 1) / 2;
+    auto off = [&](int item) {
+      const int kz = item / TZ, li = item - kz * TZ;
+      return kz * gzs + (long long)line_yp[li] * a.nxh + line_kx[li];
+    };
+    auto ok = [&](int item) { return item < N * TZ && line_yp[item % TZ] >= 0; };
+    T gc[NCO], gn[NCO];
+    int item = threadIdx.x;
+    bool have = ok(item);
+    if (have) gamma_coef_load<T, NC>(a.gtab, gcs, off(item), gc);
+#pragma unroll 1
+    for (; item < N * TZ; item += blockDim.x) {
+      const int nxt = item + blockDim.x;
+      const bool hn = ok(nxt);
+      if (hn) gamma_coef_load<T, NC>(a.gtab, gcs, off(nxt), gn);
+      if (have) {
+        const int kz = item / TZ, li = item - kz * TZ;
+        C2<T> g[NC];
+#pragma unroll
+        for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
+        gamma_coef_apply<T, NC>(gc, g);
+#pragma unroll
+        for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
+      }
+#pragma unroll
+      for (int c = 0; c < NCO; ++c) gc[c] = gn[c];
+      have = hn;
+    }
   }
   __syncthreads();
 #pragma unroll

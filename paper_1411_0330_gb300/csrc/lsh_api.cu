@@ -113,7 +113,7 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
   if ((long long)d->nx * d->ny * d->nz > (1LL << 31)) return LSH_ERR_UNSUPPORTED_SIZE;
   d->V = (long long)d->nx * d->ny * d->nz;
   d->nxh = d->nx / 2 + 1;
-  d->hs = d->nxh + (d->nxh & 1);
+  d->hs = (d->nxh + 3) & ~3;  // 32-byte rows: z-pass column segments start on DRAM sectors
   d->c = pr->physics == LSH_ELASTIC_ISO ? 6 : pr->dim;
   d->ncoef = d->c * (d->c + 1) / 2;
   d->B = pr->nbatch > 1 ? pr->nbatch : 1;
