@@ -148,6 +148,14 @@ def pass_flops(kind, V, c, nx, ny, nz, nxh):
     raise KeyError(kind)
 
 
+# DRAM bytes (read + write) of one launch of each FP32 pass over the 6 load
+# systems of the 128^3 workload, from the ncu captures summarised in
+# profiles/fp32_passes_128cube_six_systems.md (filtered operator); to be
+# retaken whenever one of these kernels changes.
+NCU_TRAFFIC_FP32 = {"x_forward": 1771.1e6, "y_forward": 587.7e6, "z_gamma": 865.8e6, "y_inverse": 587.7e6,
+                    "x_inverse_local": 902.1e6, "cg_update": 862.1e6}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -596,7 +604,8 @@ def main():
                 for k in lsh.PASS_NAMES if p["pass_launches"][k]}
 
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "frac": achieved / peaks["hbm_gbs"], "traffic": NCU_TRAFFIC_FP32.get(dom),
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum, one launch (filtered)",
                 "kernel": f"{dom} (FP32, both operators)", "avg_launch_ms": avg_ms,
                 "algorithmic_bytes_per_launch": byts, "peak_source": peaks["source"] + " hbm_gbs (copy)",
                 "pass_avg_ms_fp32": {k: pf["pass_ms"][k] / max(pf["pass_launches"][k], 1) for k in lsh.PASS_NAMES},
