@@ -42,41 +42,26 @@ template <int N> size_t xreg_smem(int hs) {
   return rows16 + sizeof(float2) * ((size_t)XC::LINES * XC::LS + N);
 }
 
+// The work on one block of RY rows whose spectrum rows are being copied into
+// HS (bulk copy completing on `bar`, phase `parity`): gather, register inverse
+// FFT, epilogue, reduction.  False (uniform) if the copy did not land in time.
 // MODE 0: out = P (M xin + g).  MODE 1 (CG): q = P (M p + g), (p, q) -> alpha.
 // MODE 2 (residual): out = P (load - M xin - g), (r, r) -> st[s].aux[0].
 template <int MODE, int N>
-__global__ void __launch_bounds__(256, 2) k_xinv_reg(OpArgs<float> a, const float* __restrict__ xin,
-                                                     float* __restrict__ out, SolverState* __restrict__ st,
-                                                     double* __restrict__ partials, int bps, size_t rows_bytes) {
+__device__ __forceinline__ bool xinv_rows(const OpArgs<float>& a, const float* __restrict__ xin,
+                                          float* __restrict__ out, SolverState* __restrict__ st,
+                                          double* __restrict__ partials, int bps, long long rb, float2* HS,
+                                          float2* ex, const float2* tw, const float* mloc,
+                                          const unsigned char* aloc, uint64_t* bar, uint32_t parity) {
   typedef RegLine<float, N> RL;
   typedef XReg<N> XC;
   constexpr int P = XC::P, R1 = RL::R1, Q = RL::Q, RY = XC::RY, OSTR = XC::OSTR;
-  const int s = blockIdx.x / bps;
-  if (MODE == 1 && st[s].done) return;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float mloc[256 * 6];
-  __shared__ unsigned char aloc[256];
-  __shared__ __align__(8) uint64_t bar;
-  float2* HS = reinterpret_cast<float2*>(smem_raw);  // [RY][hs] spectrum rows, later [RY][OSTR] real rows
-  float* OS = reinterpret_cast<float*>(smem_raw);
-  float2* ex = reinterpret_cast<float2*>(smem_raw + rows_bytes);
-  float2* tw = ex + XC::LINES * XC::LS;
-  for (int u = threadIdx.x; u < N; u += blockDim.x) tw[u] = a.twx[u];
-  const int ntab = a.nphase * a.c;
-  for (int u = threadIdx.x; u < ntab; u += blockDim.x) mloc[u] = a.scale ? a.modtab[u] : a.mtab[u];
-  for (int u = threadIdx.x; u < a.nphase; u += blockDim.x) aloc[u] = a.act[u];
-  const int blk = blockIdx.x - s * bps;
+  float* OS = reinterpret_cast<float*>(HS);  // the real rows replace the spectrum rows
+  const int s = (int)(rb / bps);
+  const int blk = (int)(rb - (long long)s * bps);
   const int rloc = blk * RY;                            // first row inside the system
   const long long row0 = (long long)s * a.rps + rloc;  // global row
   const int hs = a.hs;
-  // the block's spectrum rows are one contiguous range: a single bulk copy
-  if (threadIdx.x == 0) {
-    mbar_init(&bar, 1);
-    mbar_init_fence();
-    const uint32_t bytes = (uint32_t)(sizeof(float2) * (size_t)RY * hs);
-    mbar_expect_tx(&bar, bytes);
-    bulk_load_1d(HS, a.H + row0 * hs, bytes, &bar);
-  }
   const int rows_per_comp = a.nz * a.ny;
   const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V;
   constexpr int NV = N / 4;
@@ -96,14 +81,7 @@ __global__ void __launch_bounds__(256, 2) k_xinv_reg(OpArgs<float> a, const floa
     xq4s[it] = *reinterpret_cast<const float4*>(xin + (row0 + row) * N + xx);
     ph4s[it] = *reinterpret_cast<const uchar4*>(a.phase + pbase + vox);
   }
-  __syncthreads();
-  if (__syncthreads_or(!mbar_wait(&bar, 0))) {
-    if (threadIdx.x == 0) {
-      mbar_wait(&bar, 0);
-      atomicOr(a.fault, 1);
-    }
-    return;
-  }
+  if (__syncthreads_or(!mbar_wait(bar, parity))) return false;
   const int t = threadIdx.x % P, l = threadIdx.x / P;
   float2 v[R1];
   {
@@ -190,8 +168,109 @@ __global__ void __launch_bounds__(256, 2) k_xinv_reg(OpArgs<float> a, const floa
       }
     }
   }
+  return true;
 }
 
+// One block per RY rows.
+template <int MODE, int N>
+__global__ void __launch_bounds__(256, 2) k_xinv_reg(OpArgs<float> a, const float* __restrict__ xin,
+                                                     float* __restrict__ out, SolverState* __restrict__ st,
+                                                     double* __restrict__ partials, int bps, size_t rows_bytes) {
+  typedef XReg<N> XC;
+  const int s = blockIdx.x / bps;
+  if (MODE == 1 && st[s].done) return;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ float mloc[256 * 6];
+  __shared__ unsigned char aloc[256];
+  __shared__ __align__(8) uint64_t bar;
+  float2* HS = reinterpret_cast<float2*>(smem_raw);
+  float2* ex = reinterpret_cast<float2*>(smem_raw + rows_bytes);
+  float2* tw = ex + XC::LINES * XC::LS;
+  for (int u = threadIdx.x; u < N; u += blockDim.x) tw[u] = a.twx[u];
+  const int ntab = a.nphase * a.c;
+  for (int u = threadIdx.x; u < ntab; u += blockDim.x) mloc[u] = a.scale ? a.modtab[u] : a.mtab[u];
+  for (int u = threadIdx.x; u < a.nphase; u += blockDim.x) aloc[u] = a.act[u];
+  // the block's spectrum rows are one contiguous range: a single bulk copy
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    mbar_init_fence();
+    const uint32_t bytes = (uint32_t)(sizeof(float2) * (size_t)XC::RY * a.hs);
+    mbar_expect_tx(&bar, bytes);
+    const long long row0 = (long long)s * a.rps + (long long)(blockIdx.x - s * bps) * XC::RY;
+    bulk_load_1d(HS, a.H + row0 * a.hs, bytes, &bar);
+  }
+  __syncthreads();
+  if (!xinv_rows<MODE, N>(a, xin, out, st, partials, bps, blockIdx.x, HS, ex, tw, mloc, aloc, &bar, 0)) {
+    if (threadIdx.x == 0) {
+      mbar_wait(&bar, 0);
+      atomicOr(a.fault, 1);
+    }
+  }
+}
+
+// Persistent: a block walks every gridDim.x-th row block and prefetches the
+// next one's spectrum rows into its second buffer while it works on the
+// current one.
+template <int MODE, int N>
+__global__ void __launch_bounds__(256, 2) k_xinv_regp(OpArgs<float> a, const float* __restrict__ xin,
+                                                      float* __restrict__ out, SolverState* __restrict__ st,
+                                                      double* __restrict__ partials, int bps, size_t rows_bytes,
+                                                      long long nrb) {
+  typedef XReg<N> XC;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t bar[2];
+  float2* HSb[2] = {reinterpret_cast<float2*>(smem_raw), reinterpret_cast<float2*>(smem_raw + rows_bytes)};
+  float2* ex = reinterpret_cast<float2*>(smem_raw + 2 * rows_bytes);
+  float2* tw = ex + XC::LINES * XC::LS;
+  float* mloc = reinterpret_cast<float*>(tw + N);
+  const int ntab = a.nphase * a.c;
+  unsigned char* aloc = reinterpret_cast<unsigned char*>(mloc + ntab);
+  for (int u = threadIdx.x; u < N; u += blockDim.x) tw[u] = a.twx[u];
+  for (int u = threadIdx.x; u < ntab; u += blockDim.x) mloc[u] = a.scale ? a.modtab[u] : a.mtab[u];
+  for (int u = threadIdx.x; u < a.nphase; u += blockDim.x) aloc[u] = a.act[u];
+  const uint32_t bytes = (uint32_t)(sizeof(float2) * (size_t)XC::RY * a.hs);
+  auto live = [&](long long rb) { return rb < nrb && (MODE != 1 || st[rb / bps].done == 0); };
+  auto issue = [&](long long rb, int b) {  // one thread
+    const int s = (int)(rb / bps);
+    const long long row0 = (long long)s * a.rps + (rb - (long long)s * bps) * XC::RY;
+    mbar_expect_tx(&bar[b], bytes);
+    bulk_load_1d(HSb[b], a.H + row0 * a.hs, bytes, &bar[b]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  uint32_t par[2] = {0, 0};
+  long long rb = blockIdx.x;
+  bool cur = live(rb);
+  if (cur && threadIdx.x == 0) issue(rb, 0);
+  int b = 0;
+  bool fault = false;
+  while (rb < nrb) {
+    const long long nxt = rb + gridDim.x;
+    const bool nl = live(nxt);
+    if (nl && threadIdx.x == 0) issue(nxt, b ^ 1);  // that buffer was released at the end of the last round
+    if (cur) {
+      if (!xinv_rows<MODE, N>(a, xin, out, st, partials, bps, rb, HSb[b], ex, tw, mloc, aloc, &bar[b], par[b])) {
+        fault = true;
+        break;
+      }
+      par[b] ^= 1;
+      fence_proxy_async();  // our reads of this buffer come before the next copy into it
+      __syncthreads();
+    }
+    rb = nxt;
+    cur = nl;
+    b ^= 1;
+  }
+  if (fault && threadIdx.x == 0) {
+    mbar_wait(&bar[0], par[0]);
+    mbar_wait(&bar[1], par[1]);
+    atomicOr(a.fault, 1);
+  }
+}
 
 template <int N> size_t xfwd_region(int hs) {
   typedef XReg<N> XC;
@@ -387,8 +466,50 @@ template <int N> bool launch_xinv_reg_n(const OpArgs<float>& a, int mode, const 
   return true;
 }
 
+template <int N> size_t xregp_smem(const OpArgs<float>& a, size_t* rows16) {
+  typedef XReg<N> XC;
+  const size_t rows = std::max(sizeof(float2) * (size_t)XC::RY * a.hs, sizeof(float) * (size_t)XC::RY * XC::OSTR);
+  *rows16 = (rows + 15) & ~(size_t)15;
+  return 2 * *rows16 + sizeof(float2) * ((size_t)XC::LINES * XC::LS + N) + sizeof(float) * a.nphase * a.c + a.nphase;
+}
+
+template <int N> int xregp_blocks_per_sm(size_t smem) {
+  int v = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_xinv_regp<1, N>, 256, smem) != cudaSuccess) {
+    cudaGetLastError();
+    v = 0;
+  }
+  return v;
+}
+
+template <int N> bool launch_xinv_regp_n(const OpArgs<float>& a, int mode, const float* xin, float* out,
+                                         SolverState* st, double* partials, cudaStream_t s) {
+  typedef XReg<N> XC;
+  if (a.rps % XC::RY != 0 || (a.hs & 1)) return false;
+  const int bps = a.rps / XC::RY;
+  size_t rows16 = 0;
+  const size_t smem = xregp_smem<N>(a, &rows16);
+  if (smem > 200 * 1024) return false;
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const int bpsm = std::max(1, xregp_blocks_per_sm<N>(smem));
+  const long long nrb = (long long)a.S * bps;
+  const int grid = (int)std::min<long long>(nrb, (long long)nsm * bpsm);
+  if (mode == 0) k_xinv_regp<0, N><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16, nrb);
+  else if (mode == 1) k_xinv_regp<1, N><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16, nrb);
+  else k_xinv_regp<2, N><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16, nrb);
+  return true;
+}
+
 template <int N> void xreg_attrs() {
   const int mx = 200 * 1024;
+  cudaFuncSetAttribute(k_xinv_regp<0, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv_regp<1, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv_regp<2, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xfwd_reg<0, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xfwd_reg<1, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xinv_reg<0, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -435,9 +556,19 @@ bool xinv_reg_fits(const OpArgs<float>& a) {
 }
 
 // False when this grid has no register inverse x pass (the caller keeps the
-// shared-memory kernel).
+// shared-memory kernel).  persistent: the double-buffered persistent kernel.
 bool launch_xinv_reg(const OpArgs<float>& a, int mode, const float* xin, float* out, SolverState* st,
-                     double* partials, cudaStream_t s) {
+                     double* partials, cudaStream_t s, bool persistent) {
+  if (persistent) {
+    switch (a.nx) {
+      case 16: return launch_xinv_regp_n<16>(a, mode, xin, out, st, partials, s);
+      case 32: return launch_xinv_regp_n<32>(a, mode, xin, out, st, partials, s);
+      case 64: return launch_xinv_regp_n<64>(a, mode, xin, out, st, partials, s);
+      case 128: return launch_xinv_regp_n<128>(a, mode, xin, out, st, partials, s);
+      case 256: return launch_xinv_regp_n<256>(a, mode, xin, out, st, partials, s);
+      default: return false;
+    }
+  }
   switch (a.nx) {
     case 16: return launch_xinv_reg_n<16>(a, mode, xin, out, st, partials, s);
     case 32: return launch_xinv_reg_n<32>(a, mode, xin, out, st, partials, s);

@@ -1205,7 +1205,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   for (int k = 0; k < 2; ++k) r.xf_ms[k] = -1.f;
   r.y_variant = h->pf.a.ytma;
   r.z_variant = h->pf.a.ztma;
-  for (int k = 0; k < 2; ++k) r.x_ms[k] = -1.f;
+  for (int k = 0; k < 3; ++k) r.x_ms[k] = -1.f;
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
   for (int k = 0; k < 7; ++k) r.z_ms[k] = -1.f;
   const Derived& d = h->d;
@@ -1256,15 +1256,17 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
     }
     {
       // inverse x pass with the local term (apply mode: no reductions, no state)
-      for (int v = 0; v < 2; ++v) {
+      int bx = 0;
+      for (int v = 0; v < 3; ++v) {
         a.xreg = v;
         r.x_ms[v] = timeit([&]() {
-          if (v == 1) return launch_xinv_reg(a, 0, P.x, P.q, nullptr, nullptr, s);
+          if (v >= 1) return launch_xinv_reg(a, 0, P.x, P.q, nullptr, nullptr, s, v == 2);
           launch_xinv<float>(a, P.L, 0, P.x, P.q, nullptr, nullptr, s);
           return true;
         });
+        if (r.x_ms[v] > 0.f && r.x_ms[v] < r.x_ms[bx]) bx = v;
       }
-      r.x_variant = (r.x_ms[1] > 0.f && r.x_ms[1] < r.x_ms[0]) ? 1 : 0;
+      r.x_variant = bx;
       a.xreg = r.x_variant;
     }
     if (a.yreg && P.ytma_ok) {
@@ -1311,13 +1313,13 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
 
 lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
-  if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 1 || y_variant < 0 || y_variant > 1 ||
+  if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 2 || y_variant < 0 || y_variant > 1 ||
       z_variant < 0 || z_variant > 6)
     return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;
   if (h->d.precision != LSH_MIXED)
     return (xf_variant || x_variant || y_variant || z_variant) ? LSH_ERR_UNSUPPORTED : LSH_OK;
-  if (x_variant == 1 && !xinv_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
+  if (x_variant >= 1 && !xinv_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (xf_variant == 1 && !xfwd_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;
   if (z_variant == 6 && !P.a.zreg) return LSH_ERR_UNSUPPORTED;

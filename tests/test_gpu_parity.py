@@ -423,7 +423,7 @@ def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkey
         y_tma = h_tma.apply(xt)
         assert torch.equal(y_tma, y_reg), zv
     # the register x passes: other rounding order than the staged ones
-    for xf, xv in ((1, 0), (0, 1), (1, 1)):
+    for xf, xv in ((1, 0), (0, 1), (1, 1), (1, 2)):
         try:
             h_tma.set_variants(xf, xv, 1, 0)
         except lsh.LSHError as e:
@@ -432,12 +432,12 @@ def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkey
         y_x = h_tma.apply(xt)
         assert rel(y_x.cpu().numpy(), oracle.apply(P, x)) < 2e-5, (xf, xv)
     rep = h_tma.autotune()
-    assert rep["z_variant"] in range(7) and rep["y_variant"] in (0, 1) and rep["x_variant"] in (0, 1)
+    assert rep["z_variant"] in range(7) and rep["y_variant"] in (0, 1) and rep["x_variant"] in (0, 1, 2)
     assert rep["xf_variant"] in (0, 1)
     assert rel(h_tma.apply(xt).cpu().numpy(), oracle.apply(P, x)) < 2e-5
 
 
-@pytest.mark.parametrize("variants", [(0, 0, 0, 0), (1, 1, 1, 0), (1, 1, 1, 4), (0, 1, 0, 1)])
+@pytest.mark.parametrize("variants", [(0, 0, 0, 0), (1, 1, 1, 0), (1, 1, 1, 4), (0, 1, 0, 1), (1, 2, 1, 0)])
 def test_mixed_solver_with_each_kernel_variant(variants):
     """The mixed-precision solver (FP32 CG on the forced x / y / z kernel variants,
     FP64 refinement) reaches the oracle's C* to the mixed tolerance whichever
