@@ -453,3 +453,23 @@ def test_mixed_solver_with_each_kernel_variant(variants):
     Ao, _ = oracle.effective(oracle.Problem(ph, EL, physics=1, green=1), tol=1e-13)
     assert rel(A, Ao) < 1e-8, rel(A, Ao)
     assert all(i["status"] == 0 for i in infos)
+
+
+@pytest.mark.parametrize("shape,physics", [((16, 256, 32), 1), ((256, 16, 16), 1), ((8, 256, 256), 0)])
+def test_length_256_passes_fp64_and_fp32(shape, physics):
+    """Lines of 256 points (the largest register-FFT length: 16 x 16 split) along each
+    axis, FP64 and FP32 (tuned variants), against the oracle."""
+    rng = np.random.default_rng(sum(shape) + physics)
+    if physics == 1:
+        ph = (rng.random(shape) < 0.3).astype(np.uint8)
+        mods = EL
+    else:
+        ph = rng.integers(0, 2, shape).astype(np.uint8)
+        mods = _scalar_mods(3, 6, nphase=2)
+    P = oracle.Problem(ph, mods, physics=physics, green=1)
+    x = rng.standard_normal(P.field_shape)
+    yo = oracle.apply(P, x)
+    h64 = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=1)
+    assert rel(h64.apply(torch.from_numpy(x).cuda()).cpu().numpy(), yo) < 1e-12
+    h32 = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=1, precision=lsh.MIXED, tune=True)
+    assert rel(h32.apply(torch.from_numpy(x).float().cuda()).cpu().numpy(), yo) < 2e-5
