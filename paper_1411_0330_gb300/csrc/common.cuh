@@ -196,4 +196,14 @@ __device__ __forceinline__ double gather_partials_sys(const double* partials, un
   return s;
 }
 
+// Scalars of one system's MINRES recurrence (Lanczos + Givens, Paige-Saunders),
+// kept on the device next to its SolverState.
+struct MinresScalars {
+  double beta1, beta, oldb, alfa;
+  double dbar, epsln, oldeps, phibar;
+  double cs, sn, phi, delta, denom;
+  int pending;  // converged after this iteration's update of x
+  int pad;
+};
+
 }  // namespace lsh

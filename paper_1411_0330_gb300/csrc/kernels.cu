@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xinv(OpArgs<T
                                                                         SolverState* __restrict__ st,
                                                                         double* __restrict__ partials) {
   const int s = blockIdx.x / a.bps;
-  if (MODE == 1 && st[s].done) return;
+  if ((MODE == 1 || MODE == 3) && st[s].done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ T mloc[256 * 6];  // local coefficients (no scale field) or A_phase diagonal
   __shared__ unsigned char aloc[256];
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xinv(OpArgs<T
         const T xq = xv[h2][u];
         if (MODE == 0) {
           ov[u] = active ? m * xq + gv : (T)0;
-        } else if (MODE == 1) {
+        } else if (MODE == 1 || MODE == 3) {
           ov[u] = active ? m * xq + gv : (T)0;
           acc.add(xq * ov[u]);
         } else {
@@ -418,12 +418,145 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xinv(OpArgs<T
           } else {
             sst->alpha = sst->rr / sum;
           }
+        } else if (MODE == 3) {
+          sst->pq = sum;  // (v, K v) for MINRES: any sign, no breakdown test
         } else {
           sst->aux[0] = sum;
         }
       }
     }
   }
+}
+
+// ------------------------------------------------------------------ MINRES vector kernels
+// One MINRES iteration after q = K r2 (r2 = beta v, so K v = q / beta) and
+// pq = (r2, q) from the inverse x pass:
+//   A: y = K v - (beta / oldb) r1, alfa = (v, y)
+//   B: y -= (alfa / beta) r2, r1 <- r2, r2 <- y, beta <- |y|, Givens rotation
+//   C: w_k = (v - oldeps w_{k-2} - delta w_{k-1}) / gamma, x += phi w_k
+// (x0 = 0, r1 = r2 = b; Paige-Saunders recurrences).  Grid (G, S).
+__global__ void __launch_bounds__(kThreads) k_mr_a(double* __restrict__ q, const double* __restrict__ r1,
+                                                   const double* __restrict__ r2, long long n,
+                                                   SolverState* __restrict__ st, MinresScalars* __restrict__ ms,
+                                                   double* __restrict__ partials) {
+  const int s = blockIdx.y;
+  SolverState* sst = st + s;
+  if (sst->done) return;
+  const double beta = ms[s].beta;
+  const double coef = sst->iter > 0 ? beta / ms[s].oldb : 0.0;
+  const double ib = 1.0 / beta;
+  double* qs = q + s * n;
+  const double* r1s = r1 + s * n;
+  const double* r2s = r2 + s * n;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    qs[i] = qs[i] * ib - coef * r1s[i];
+    acc += r2s[i] * r1s[i];
+  }
+  const double tot = block_sum(acc);
+  double* part = partials + (long long)s * gridDim.x;
+  if (publish_partial_sys(part, blockIdx.x, gridDim.x, tot, &sst->counter[1])) {
+    const double t2 = gather_partials_sys(part, gridDim.x, &sst->counter[1]);
+    if (threadIdx.x == 0) ms[s].alfa = sst->pq * ib * ib - coef * t2 * ib;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mr_b(double* __restrict__ q, double* __restrict__ r1,
+                                                   double* __restrict__ r2, long long n,
+                                                   SolverState* __restrict__ st, MinresScalars* __restrict__ ms,
+                                                   double* __restrict__ partials) {
+  const int s = blockIdx.y;
+  SolverState* sst = st + s;
+  if (sst->done) return;
+  const double c2 = ms[s].alfa / ms[s].beta;
+  double* qs = q + s * n;
+  double* r1s = r1 + s * n;
+  double* r2s = r2 + s * n;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double y = qs[i] - c2 * r2s[i];
+    r1s[i] = r2s[i];
+    r2s[i] = y;
+    acc += y * y;
+  }
+  const double tot = block_sum(acc);
+  double* part = partials + (long long)s * gridDim.x;
+  if (publish_partial_sys(part, blockIdx.x, gridDim.x, tot, &sst->counter[2])) {
+    const double yy = gather_partials_sys(part, gridDim.x, &sst->counter[2]);
+    if (threadIdx.x == 0) {
+      MinresScalars& m = ms[s];
+      const double bnew = sqrt(fmax(yy, 0.0));
+      m.oldb = m.beta;
+      m.beta = bnew;
+      m.oldeps = m.epsln;
+      m.delta = m.cs * m.dbar + m.sn * m.alfa;
+      const double gbar = m.sn * m.dbar - m.cs * m.alfa;
+      m.epsln = m.sn * bnew;
+      m.dbar = -m.cs * bnew;
+      const double gamma = fmax(hypot(gbar, bnew), 1e-300);
+      m.cs = gbar / gamma;
+      m.sn = bnew / gamma;
+      m.phi = m.cs * m.phibar;
+      m.phibar = m.sn * m.phibar;
+      m.denom = 1.0 / gamma;
+      sst->iter += 1;
+      sst->rr = m.phibar * m.phibar;  // residual norm estimate, squared
+      if (!isfinite(yy) || !isfinite(m.phibar)) {
+        sst->status = 5;
+        sst->done = 1;
+      } else if (m.phibar * m.phibar <= sst->tol2 || bnew == 0.0) {
+        m.pending = 1;  // x gets this iteration's update in C, then the system stops
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_mr_c(double* __restrict__ x, double* __restrict__ wa,
+                                                   double* __restrict__ wb, const double* __restrict__ r1, long long n,
+                                                   SolverState* __restrict__ st, MinresScalars* __restrict__ ms,
+                                                   double* __restrict__ partials) {
+  const int s = blockIdx.y;
+  SolverState* sst = st + s;
+  if (sst->done) return;
+  const MinresScalars m = ms[s];
+  const double iv = 1.0 / m.oldb;  // v = r1 / oldb (r1 holds the previous r2)
+  double* xs = x + s * n;
+  double* was = wa + s * n;  // w_{k-1}
+  double* wbs = wb + s * n;  // w_{k-2}
+  const double* r1s = r1 + s * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double a = was[i];
+    const double wn = (r1s[i] * iv - m.oldeps * wbs[i] - m.delta * a) * m.denom;
+    wbs[i] = a;
+    was[i] = wn;
+    xs[i] += m.phi * wn;
+  }
+  double* part = partials + (long long)s * gridDim.x;
+  if (publish_partial_sys(part, blockIdx.x, gridDim.x, 0.0, &sst->counter[3])) {
+    gather_partials_sys(part, gridDim.x, &sst->counter[3]);
+    if (threadIdx.x == 0 && ms[s].pending) sst->done = 1;
+  }
+}
+
+// Start: beta1 = |r0| (the right-hand side of this MINRES run: b, or b - K x0
+// for a warm start), zero recurrence scalars; the tolerance is relative to |b|.
+__global__ void k_mr_begin(SolverState* __restrict__ st, MinresScalars* __restrict__ ms,
+                           const double* __restrict__ rhs2, const double* __restrict__ bb, double tol, int S) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= S) return;
+  SolverState& t = st[s];
+  t = SolverState{};
+  MinresScalars& m = ms[s];
+  m = MinresScalars{};
+  const double b1 = sqrt(fmax(rhs2[s], 0.0));
+  m.beta1 = b1;
+  m.beta = b1;
+  m.phibar = b1;
+  m.cs = -1.0;
+  t.bb = bb[s];
+  t.tol2 = tol * tol * bb[s];
+  t.rr = rhs2[s];
+  if (!(b1 > 0.0) || rhs2[s] <= t.tol2) t.done = 1;
 }
 
 // ------------------------------------------------------------------ CG vector kernels
@@ -822,6 +955,8 @@ __global__ void k_scale_grad(const double* __restrict__ tau_all, const double* _
 template <typename T> void set_smem_attrs() {
   const int mx = 227 * 1024;
   constexpr int VV = 16 / sizeof(T);
+  cudaFuncSetAttribute(k_xinv<T, 3, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv<T, 3, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xfwd<T, 0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xfwd<T, 1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xfwd<T, 0, VV>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -893,19 +1028,32 @@ template <typename T>
 void launch_xinv(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* xin, T* out, SolverState* st,
                  double* partials, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (a.xreg && launch_xinv_reg(a, mode, xin, out, st, partials, s, a.xreg == 2)) return;
+    if (a.xreg && mode <= 2 && launch_xinv_reg(a, mode, xin, out, st, partials, s, a.xreg == 2)) return;
   }
   const int grid = a.S * a.bps;
   constexpr int VV = 16 / sizeof(T);
   if (L.VEC == VV) {
     if (mode == 0) k_xinv<T, 0, VV><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
     else if (mode == 1) k_xinv<T, 1, VV><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
+    else if (mode == 3) k_xinv<T, 3, VV><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
     else k_xinv<T, 2, VV><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
   } else {
     if (mode == 0) k_xinv<T, 0, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
     else if (mode == 1) k_xinv<T, 1, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
+    else if (mode == 3) k_xinv<T, 3, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
     else k_xinv<T, 2, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
   }
+}
+
+void launch_minres_begin(SolverState* st, MinresScalars* ms, const double* rhs2, const double* bb, double tol, int S,
+                         cudaStream_t s) {
+  k_mr_begin<<<(S + 127) / 128, 128, 0, s>>>(st, ms, rhs2, bb, tol, S);
+}
+void launch_minres_step(double* x, double* r1, double* r2, double* q, double* wa, double* wb, long long n, int S,
+                        SolverState* st, MinresScalars* ms, double* partials, int G, cudaStream_t s) {
+  k_mr_a<<<dim3(G, S), kThreads, 0, s>>>(q, r1, r2, n, st, ms, partials);
+  k_mr_b<<<dim3(G, S), kThreads, 0, s>>>(q, r1, r2, n, st, ms, partials);
+  k_mr_c<<<dim3(G, S), kThreads, 0, s>>>(x, wa, wb, r1, n, st, ms, partials);
 }
 
 template <typename T>

@@ -260,6 +260,8 @@ struct Layout {
   size_t off_tw_d, off_tw_f;
   size_t off_fd[4], off_Hd, off_gd;
   size_t off_ff[4], off_Hf, off_gf;
+  size_t off_wa, off_wb, off_ms;  // MINRES: two direction fields (FP64) and per-system scalars
+  bool minres;                    // MINRES buffers present
   size_t total;
   long long nparts;
 };
@@ -303,10 +305,16 @@ Layout make_layout(const Derived& d) {
   // FP64 fields: x, r always; p, q for the FP64 CG (one system's worth of p, q
   // suffices for the Mandel rotations of lsh_apply on a mixed handle)
   const bool mixed = d.precision == LSH_MIXED;
+  // MINRES (FP64) needs full-size p, q and two more fields: always for an
+  // indefinite operator, otherwise only where they are small (tests, small grids)
+  l.minres = d.definite == 0 || (long long)S * n <= (1ll << 22);
   for (int i = 0; i < 4; ++i) {
-    const long long ns = (i < 2 || !mixed) ? S : 1;
+    const long long ns = (i < 2 || !mixed || l.minres) ? S : 1;
     l.off_fd[i] = take(sizeof(double) * (size_t)(ns * n));
   }
+  l.off_wa = take(l.minres ? sizeof(double) * (size_t)(S * n) : 0);
+  l.off_wb = take(l.minres ? sizeof(double) * (size_t)(S * n) : 0);
+  l.off_ms = take(sizeof(MinresScalars) * (size_t)S);
   l.off_Hd = take(sizeof(double2) * (size_t)(S * d.c * nfh));
   l.off_gd = take(sizeof(double) * (size_t)(d.ncoef * nf));
   if (mixed) {
@@ -340,6 +348,8 @@ template <typename T> struct PrecBufs {
 struct lsh_handle {
   Derived d;
   int device = 0;
+  double *wa = nullptr, *wb = nullptr;  // MINRES direction fields (null: not available)
+  MinresScalars* ms = nullptr;
   int* fault = nullptr;  // device word set by a kernel whose bounded wait ran out
   bool no_tma = false;
   Layout lay;
@@ -722,6 +732,50 @@ lsh_status cg_run(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int maxit, 
   return read_states(h, P.st, S, out.data());
 }
 
+// MINRES on the FP64 operator for the systems of a wave, whose right-hand
+// sides are in pd.r and initial guesses in pd.x (x0 + the MINRES updates);
+// rhs2: device (r0, r0) per system, bb: device (b, b) per system (tolerance
+// base).  Eight launches per iteration: the five operator passes on r2 and the
+// three recurrence kernels.
+lsh_status minres_run(lsh_handle* h, const OpArgs<double>& a, int maxit, int check_every, const double* rhs2,
+                      double tol, std::vector<SolverState>& out) {
+  PrecBufs<double>& P = h->pd;
+  cudaStream_t s = h->stream;
+  const int S = a.S;
+  const long long n = (long long)a.c * a.V;
+  const int G = P.L.ew_per_sys;
+  LSH_CK(cudaMemcpyAsync(P.p, P.r, sizeof(double) * (size_t)(S * n), cudaMemcpyDeviceToDevice, s));
+  LSH_CK(cudaMemsetAsync(h->wa, 0, sizeof(double) * (size_t)(S * n), s));
+  LSH_CK(cudaMemsetAsync(h->wb, 0, sizeof(double) * (size_t)(S * n), s));
+  launch_minres_begin(P.st, h->ms, rhs2, h->bbdev, tol, S, s);
+  h->launches += 1;
+  lsh_status stt;
+  out.resize(S);
+  if ((stt = read_states(h, P.st, S, out.data()))) return stt;
+  auto all_done = [&]() {
+    for (int k = 0; k < S; ++k)
+      if (!out[k].done) return false;
+    return true;
+  };
+  int it = 0;
+  while (!all_done() && it < maxit) {
+    const int chunk = std::min(check_every, maxit - it);
+    for (int j = 0; j < chunk; ++j) {
+      launch_xfwd<double>(a, P.L, 0, P.p, nullptr, nullptr, nullptr, nullptr, s);
+      launch_yfft<double>(a, P.L, false, P.st, s);
+      launch_zgamma<double>(a, P.L, P.st, s);
+      launch_yfft<double>(a, P.L, true, P.st, s);
+      launch_xinv<double>(a, P.L, 3, P.p, P.q, P.st, h->partials, s);
+      launch_minres_step(P.x, P.r, P.p, P.q, h->wa, h->wb, n, S, P.st, h->ms, h->partials, G, s);
+      h->launches += 8;
+    }
+    if ((stt = last_launch())) return stt;
+    it += chunk;
+    if ((stt = read_states(h, P.st, S, out.data()))) return stt;
+  }
+  return LSH_OK;
+}
+
 // A kernel that gave up a bounded wait (TMA copies) set the fault word.
 lsh_status check_fault(lsh_handle* h) {
   int f = 0;
@@ -759,7 +813,36 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
   const OpArgs<double> ad = wave_args<double>(h, w);
   const int G = Pd.L.ew_per_sys;
   std::vector<SolverState> st;
-  if (d.precision == LSH_FP64) {
+  const int solver = o ? o->solver : LSH_SOLVER_AUTO;
+  const bool use_minres = solver == LSH_SOLVER_MINRES || (solver == LSH_SOLVER_AUTO && d.definite == 0);
+  if (use_minres) {
+    // indefinite operator (or asked for): MINRES in FP64 whatever the precision
+    if (!h->wa) return LSH_ERR_UNSUPPORTED;
+    const double* rhs2 = h->bbdev;
+    if (!warm) {
+      launch_fill_rhs<double>(ad, Pd.r, Pd.x, G, h->stream);
+      h->launches += 1;
+    } else {
+      if ((stt = residual64(h, ad, Pd.x, Pd.r))) return stt;
+      std::vector<SolverState> s2(S);
+      if ((stt = read_states(h, h->st + 2 * d.Smax, S, s2.data()))) return stt;
+      std::vector<double> r2(S);
+      for (int s = 0; s < S; ++s) {
+        r2[s] = s2[s].aux[0];
+        infos[s].applies64 += 1;
+      }
+      LSH_CK(cudaMemcpyAsync(h->sums, r2.data(), sizeof(double) * S, cudaMemcpyHostToDevice, h->stream));
+      rhs2 = h->sums;
+    }
+    if ((stt = last_launch())) return stt;
+    if ((stt = minres_run(h, ad, maxit, check, rhs2, tol, st))) return stt;
+    for (int s = 0; s < S; ++s) {
+      infos[s].iters = st[s].iter;
+      infos[s].applies64 += st[s].iter;
+      infos[s].relres = st[s].bb > 0 ? std::sqrt(std::max(st[s].rr, 0.0) / st[s].bb) : 0.0;
+      infos[s].status = st[s].status ? st[s].status : (st[s].done ? LSH_OK : LSH_ERR_NOT_CONVERGED);
+    }
+  } else if (d.precision == LSH_FP64) {
     if (!warm) {
       launch_fill_rhs<double>(ad, Pd.r, Pd.x, G, h->stream);
       launch_cg_begin<double>(Pd.r, n, S, Pd.st, h->partials, tol, h->bbdev, G, h->stream);
@@ -954,6 +1037,11 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   h->bbdev = (double*)(h->base + l.off_bb);
   h->flags = h->base + l.off_flags;
   h->fault = (int*)(h->base + l.off_fault);
+  h->ms = (MinresScalars*)(h->base + l.off_ms);
+  if (l.minres) {
+    h->wa = (double*)(h->base + l.off_wa);
+    h->wb = (double*)(h->base + l.off_wb);
+  }
   if (cudaMemsetAsync(h->fault, 0, sizeof(int), h->stream) != cudaSuccess) {
     cudaGetLastError();
     delete h;

@@ -103,10 +103,38 @@ def test_config1_square_inclusion_indefinite_reference():
     mods = np.array([np.eye(2), 10 * np.eye(2)])
     ref = 5.5 * np.eye(2)
     h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.TRUNCATED, ref=ref)
-    A, infos = h.effective(tol=1e-10)
     Ao, _ = oracle.effective(oracle.Problem(ph, mods, green=0, ref=ref), tol=1e-13)
-    assert rel(A, Ao) < 1e-10, (A, Ao, infos)
-    assert abs(A[0, 1]) < 1e-10 and abs(A[0, 0] - A[1, 1]) < 1e-10
+    # AUTO runs MINRES here (phases on both sides of k0); CG as the configuration states
+    for solver in (lsh.SOLVER_AUTO, lsh.SOLVER_CG, lsh.SOLVER_MINRES):
+        A, infos = h.effective(tol=1e-10, solver=solver)
+        assert rel(A, Ao) < 1e-10, (solver, A, Ao, infos)
+        assert abs(A[0, 1]) < 1e-10 and abs(A[0, 0] - A[1, 1]) < 1e-10
+        assert all(i["status"] == 0 and i["relres"] <= 1e-10 for i in infos)
+    # truncated Gamma: A* does not depend on the reference medium (Table 1)
+    h2 = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.TRUNCATED, ref=0.5 * np.eye(2))
+    A2, _ = h2.effective(tol=1e-12)
+    assert rel(A2, Ao) < 1e-9
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_minres_indefinite_elastic_matches_oracle(precision):
+    """Elastic spheres with the reference between the phases (mu0 above the matrix,
+    below the inclusions): K is indefinite, AUTO solves with MINRES (FP64 also on a
+    mixed handle), batched over the 6 loads, warm start included."""
+    ph, _, _ = ms.sphere_microstructure(12, 1.5, 0.25, seed=31)
+    ref = np.array([2.0 * KM, 2.0 * MUM])  # between the matrix and inclusion moduli
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, ref=ref,
+                   precision=precision)
+    A, infos = h.effective(tol=1e-11)
+    Ao, _ = oracle.effective(oracle.Problem(ph, EL, physics=1, green=1, ref=ref), tol=1e-13)
+    assert rel(A, Ao) < 1e-10, rel(A, Ao)
+    assert all(i["status"] == 0 for i in infos)
+    load = np.array([0.2, -0.1, 0.4, 0.0, 0.3, 0.1])
+    tau, info = h.solve(load, tol=1e-11)
+    to, _, _ = oracle.solve(oracle.Problem(ph, EL, physics=1, green=1, ref=ref), load, tol=1e-13)
+    assert rel(tau.cpu().numpy(), to) < 1e-9
+    tau2, info2 = h.solve(load, tau=tau.clone(), tol=1e-11, warm_start=True)
+    assert info2["iters"] <= 2 and rel(tau2.cpu().numpy(), to) < 1e-9
 
 
 @pytest.mark.parametrize("green", [0, 1])
