@@ -53,7 +53,10 @@ typedef enum {
 } lsh_status;
 
 enum { LSH_SCALAR = 0, LSH_ELASTIC_ISO = 1 };
-enum { LSH_GREEN_TRUNCATED = 0, LSH_GREEN_FILTERED = 1 };
+/* Discrete Green operators of Sec. 3.2: truncated (Moulinec-Suquet, with the
+ * Nyquist rule), filtered, and the finite-difference one of Sec. 3.2.3
+ * (scalar problems only). */
+enum { LSH_GREEN_TRUNCATED = 0, LSH_GREEN_FILTERED = 1, LSH_GREEN_FD = 2 };
 /* Arithmetic of the solve.  LSH_FP64: every step in double precision.
  * LSH_MIXED: FFTs, Gamma apply and CG vectors in single precision, inner
  * products and CG scalars in double, wrapped in iterative refinement whose
@@ -72,7 +75,7 @@ typedef struct lsh_problem {
   int dim;                     /* 2 or 3                                                  */
   int n[3];                    /* cells per axis; n[2] ignored (treated as 1) for dim 2   */
   int physics;                 /* LSH_SCALAR or LSH_ELASTIC_ISO (requires dim 3)          */
-  int green;                   /* LSH_GREEN_TRUNCATED or LSH_GREEN_FILTERED               */
+  int green;                   /* LSH_GREEN_TRUNCATED, _FILTERED or _FD (scalar)          */
   int precision;               /* LSH_FP64 or LSH_MIXED                                   */
   int nphase;                  /* 1..256                                                  */
   const double *phase_moduli;  /* host.  Scalar: dim*dim row-major conductivity per phase

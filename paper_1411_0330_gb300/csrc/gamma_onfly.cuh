@@ -95,6 +95,21 @@ __device__ __forceinline__ void gamma_trunc_onfly(const OpArgs<T>& a, int kx, in
   v[5] = cscale<T>(S12, r2);
 }
 
+// Finite-difference operator: rotate component i (axis i) by sign * pi k_i / N_i
+// (k unsigned, as in the table), before (sign -1) and after (+1) the real table.
+template <typename T, int NC>
+__device__ __forceinline__ void fd_rotate(const OpArgs<T>& a, int kx, int ky, int kz, C2<T>* v, T sign) {
+  const int kk[3] = {kx, ky, kz};
+  const int nn[3] = {a.nx, a.ny, a.nz};
+#pragma unroll
+  for (int i = 0; i < NC && i < 3; ++i) {
+    T s, c;
+    sincospi((T)kk[i] / (T)nn[i], &s, &c);
+    s *= sign;
+    v[i] = mkc<T>(c * v[i].x - s * v[i].y, s * v[i].x + c * v[i].y);
+  }
+}
+
 // c x c symmetric Gamma^h_k (packed upper triangle, coefficient stride cstride)
 // times the c components of one frequency, in place.
 template <typename T, int NC>

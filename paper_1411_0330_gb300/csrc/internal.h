@@ -48,6 +48,8 @@ template <typename T> struct OpArgs {
   // Green operator computed in the z pass instead of read from gtab (truncated
   // operator, FP32): physics, grid lengths, signed-frequency tables, constants
   int onfly;                   // 1: compute Gamma^h_k on the fly
+  int fdphase;                 // finite-difference operator: the table holds the real part
+                               // u u^T / (u^T A0 u); components rotate by -/+ pi k_i / N_i around it
   int physics;
   const int* kofy;             // y position -> frequency
   const int* kofz;             // z position -> frequency

@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs
   if (nz > 1) fft_lines<T, false>(buf, NC * TZ, a.lsz, a.pz, tw);
   // per-frequency product with Gamma^h_k
   const T* __restrict__ G = a.gtab + (long long)yp * a.nxh + kx0;
-  const int ky = a.onfly ? a.kofy[yp] : 0;
+  const int ky = (a.onfly || a.fdphase) ? a.kofy[yp] : 0;
   for (int idx = threadIdx.x; idx < nz * TZ; idx += blockDim.x) {
     const int zp = fdiv(idx, TZ), t = idx - zp * TZ;
     if (t >= nt) continue;
@@ -251,6 +251,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs
     if (a.onfly) {
       gamma_trunc_onfly<T, NC>(a, kx0 + t, ky, a.kofz[zp], v);
     } else {
+      if (a.fdphase) fd_rotate<T, NC>(a, kx0 + t, ky, a.kofz[zp], v, (T)-1);
       // symmetric c x c table, packed upper triangle
       C2<T> y[NC];
 #pragma unroll
@@ -270,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs
         }
 #pragma unroll
       for (int i = 0; i < NC; ++i) v[i] = y[i];
+      if (a.fdphase) fd_rotate<T, NC>(a, kx0 + t, ky, a.kofz[zp], v, (T)1);
     }
 #pragma unroll
     for (int i = 0; i < NC; ++i) buf[(i * TZ + t) * a.lsz + zp] = v[i];
@@ -784,6 +786,21 @@ __global__ void k_gamma_table(OpArgs<T> a, GammaCtx g, const int* __restrict__ k
       }
       if (zero) nyq = false;
       else if (!nyq) gamma0_acc(g, xi, 1.0, G);
+    } else if (g.green == 2) {
+      // finite differences, Sec. 3.2.3 (scalar): V V^H / (V^H A0 V) with
+      // V_i = exp(2 i pi k_i / N_i) - 1 = i exp(i pi k_i / N_i) u_i,
+      // u_i = 2 sin(pi k_i / N_i).  For diagonal A0 this is D (u u^T / u^T A0 u) D^H
+      // with D = diag(i exp(i pi k_i / N_i)): the table holds the real middle factor,
+      // the z pass applies the phases.
+      double u[3] = {0, 0, 0};
+      double q = 0.0;
+      for (int i = 0; i < g.dim; ++i) {
+        u[i] = 2.0 * sinpi((double)k[i] / g.n[i]);
+        q += g.ref[i] * u[i] * u[i];
+      }
+      if (q > 0.0)
+        for (int i = 0; i < c; ++i)
+          for (int j = 0; j < c; ++j) G[i * c + j] = u[i] * u[j] / q;
     } else {
       // filtered, Sec. 3.2.2: weights cos^2 / sin^2 (pi k_i / (2 N_i))
       const int nterm = 1 << g.dim;

@@ -170,7 +170,9 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS, ZCfg<T, NC, N, T
         C2<T> g[NC];
 #pragma unroll
         for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
+        if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[line_yp[li]], kz, g, (T)-1);
         gamma_coef_apply<T, NC>(gc, g);
+        if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[line_yp[li]], kz, g, (T)1);
 #pragma unroll
         for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
       }

@@ -239,8 +239,13 @@ __global__ void __launch_bounds__(ZTma<NC, N, TZ, NB>::THREADS, ZTma<NC, N, TZ, 
         float2 g[NC];
 #pragma unroll
         for (int c2 = 0; c2 < NC; ++c2) g[c2] = T[(c2 * N + kz) * TZ + li];
-        if (a.onfly) gamma_trunc_onfly<float, NC>(a, kx, ky, kz, g);
-        else gamma_table_apply<float, NC>(a.gtab, gcs, kz * gzs + (long long)yp * a.nxh + kx, g);
+        if (a.onfly) {
+          gamma_trunc_onfly<float, NC>(a, kx, ky, kz, g);
+        } else {
+          if (a.fdphase) fd_rotate<float, NC>(a, kx, ky, kz, g, -1.f);
+          gamma_table_apply<float, NC>(a.gtab, gcs, kz * gzs + (long long)yp * a.nxh + kx, g);
+          if (a.fdphase) fd_rotate<float, NC>(a, kx, ky, kz, g, 1.f);
+        }
 #pragma unroll
         for (int c2 = 0; c2 < NC; ++c2) T[(c2 * N + kz) * TZ + li] = g[c2];
       }
@@ -381,8 +386,13 @@ __global__ void __launch_bounds__(ZTma16<NC, N, CPT>::THREADS, 1)
         float2 g[NC];
 #pragma unroll
         for (int c2 = 0; c2 < NC; ++c2) g[c2] = T[(c2 * N + kz) * TZ + li];
-        if (a.onfly) gamma_trunc_onfly<float, NC>(a, kx, ky, kz, g);
-        else gamma_table_apply<float, NC>(a.gtab, gcs, kz * gzs + (long long)yp * a.nxh + kx, g);
+        if (a.onfly) {
+          gamma_trunc_onfly<float, NC>(a, kx, ky, kz, g);
+        } else {
+          if (a.fdphase) fd_rotate<float, NC>(a, kx, ky, kz, g, -1.f);
+          gamma_table_apply<float, NC>(a.gtab, gcs, kz * gzs + (long long)yp * a.nxh + kx, g);
+          if (a.fdphase) fd_rotate<float, NC>(a, kx, ky, kz, g, 1.f);
+        }
 #pragma unroll
         for (int c2 = 0; c2 < NC; ++c2) T[(c2 * N + kz) * TZ + li] = g[c2];
       }

@@ -98,7 +98,9 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
   if (pr->dim != 2 && pr->dim != 3) return LSH_ERR_INVALID_ARG;
   if (pr->physics != LSH_SCALAR && pr->physics != LSH_ELASTIC_ISO) return LSH_ERR_INVALID_ARG;
   if (pr->physics == LSH_ELASTIC_ISO && pr->dim != 3) return LSH_ERR_INVALID_ARG;
-  if (pr->green != LSH_GREEN_TRUNCATED && pr->green != LSH_GREEN_FILTERED) return LSH_ERR_INVALID_ARG;
+  if (pr->green != LSH_GREEN_TRUNCATED && pr->green != LSH_GREEN_FILTERED && pr->green != LSH_GREEN_FD)
+    return LSH_ERR_INVALID_ARG;
+  if (pr->green == LSH_GREEN_FD && pr->physics != LSH_SCALAR) return LSH_ERR_UNSUPPORTED;
   if (pr->precision != LSH_FP64 && pr->precision != LSH_MIXED) return LSH_ERR_INVALID_ARG;
   if (pr->nphase < 1 || pr->nphase > 256 || !pr->phase_moduli || !pr->phase) return LSH_ERR_INVALID_ARG;
   d->dim = pr->dim;
@@ -471,6 +473,7 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.loads = P.loads;
   // FP32 truncated operator: computed on the fly in the z pass (no table read)
   a.onfly = (sizeof(T) == 4 && d.green == LSH_GREEN_TRUNCATED) ? 1 : 0;
+  a.fdphase = d.green == LSH_GREEN_FD ? 1 : 0;
   a.physics = d.physics;
   a.kofy = h->kofy;
   a.kofz = h->kofz;

@@ -121,7 +121,9 @@ extern "C" lsh_status lsh_apply_noalloc(const lsh_problem* pr, const double* x, 
   if (pr->dim != 2 && pr->dim != 3) return LSH_ERR_INVALID_ARG;
   if (pr->physics != LSH_SCALAR && pr->physics != LSH_ELASTIC_ISO) return LSH_ERR_INVALID_ARG;
   if (pr->physics == LSH_ELASTIC_ISO && pr->dim != 3) return LSH_ERR_INVALID_ARG;
-  if (pr->green != LSH_GREEN_TRUNCATED && pr->green != LSH_GREEN_FILTERED) return LSH_ERR_INVALID_ARG;
+  if (pr->green != LSH_GREEN_TRUNCATED && pr->green != LSH_GREEN_FILTERED && pr->green != LSH_GREEN_FD)
+    return LSH_ERR_INVALID_ARG;
+  if (pr->green == LSH_GREEN_FD && pr->physics != LSH_SCALAR) return LSH_ERR_UNSUPPORTED;
   if (pr->nphase < 1 || pr->nphase > 256) return LSH_ERR_INVALID_ARG;
   if (pr->scale && !pr->ref_moduli) return LSH_ERR_INVALID_ARG;
   const int dim = pr->dim, nx = pr->n[0], ny = pr->n[1], nz = dim == 3 ? pr->n[2] : 1;
@@ -262,6 +264,9 @@ extern "C" lsh_status lsh_apply_noalloc(const lsh_problem* pr, const double* x, 
   a.nz = nz;
   a.nxh = nxh;
   a.hs = nxh;
+  a.fdphase = pr->green == LSH_GREEN_FD ? 1 : 0;
+  a.kofy = (const int*)(base + o_kofy);  // frequency of each y / z position (phase rotations)
+  a.kofz = (const int*)(base + o_kofz);
   a.c = c;
   a.V = V;
   a.S = 1;

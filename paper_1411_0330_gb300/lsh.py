@@ -20,7 +20,7 @@ import numpy as np
 from . import build as _build
 
 SCALAR, ELASTIC = 0, 1
-TRUNCATED, FILTERED = 0, 1
+TRUNCATED, FILTERED, FD = 0, 1, 2
 FP64, MIXED = 0, 1
 F64, F32 = 0, 1
 SOLVER_AUTO, SOLVER_CG, SOLVER_MINRES = 0, 1, 2

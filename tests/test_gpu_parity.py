@@ -501,3 +501,41 @@ def test_length_256_passes_fp64_and_fp32(shape, physics):
     assert rel(h64.apply(torch.from_numpy(x).cuda()).cpu().numpy(), yo) < 1e-12
     h32 = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=1, precision=lsh.MIXED, tune=True)
     assert rel(h32.apply(torch.from_numpy(x).float().cuda()).cpu().numpy(), yo) < 2e-5
+
+
+FD_CASES = [((32, 32), 0), ((12, 10), 0), ((9, 15), 0), ((10, 12, 16), 0), ((16, 16, 16), 1), ((5, 7, 9), 0),
+            ((32, 64, 16), 1)]
+
+
+@pytest.mark.parametrize("shape,mixed", FD_CASES)
+def test_fd_green_operator_apply_matches_oracle(shape, mixed):
+    """The finite-difference Green operator (Sec. 3.2.3, scalar): Hermitian per
+    frequency, applied as a real table between half-angle phase rotations; FP64
+    (and FP32 on mixed handles) against the oracle's complex formula."""
+    rng = np.random.default_rng(sum(shape) + 7)
+    d = len(shape)
+    ph = rng.integers(0, 3, shape).astype(np.uint8)
+    mods = _scalar_mods(d, 5)
+    P = oracle.Problem(ph, mods, physics=0, green=2)
+    x = rng.standard_normal(P.field_shape)
+    yo = oracle.apply(P, x)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.FD, precision=lsh.MIXED if mixed else lsh.FP64,
+                   tune=bool(mixed))
+    assert rel(h.apply(torch.from_numpy(x).cuda()).cpu().numpy(), yo) < 1e-12
+    if mixed:
+        assert rel(h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy(), yo) < 2e-5
+
+
+def test_fd_green_operator_effective_and_reference_independence():
+    """A*_h with the finite-difference operator equals the oracle's (FP64 and mixed)
+    and, like the truncated one, does not depend on the reference medium (Table 1)."""
+    ph = ms.square_inclusion(32)
+    mods = np.array([np.eye(2), 10 * np.eye(2)])
+    Ao, _ = oracle.effective(oracle.Problem(ph, mods, green=2), tol=1e-13)
+    for prec in (lsh.FP64, lsh.MIXED):
+        h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.FD, precision=prec)
+        A, infos = h.effective(tol=1e-11)
+        assert rel(A, Ao) < (1e-10 if prec == lsh.FP64 else 1e-8), (prec, rel(A, Ao))
+    h2 = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.FD, ref=0.9 * np.eye(2))
+    A2, _ = h2.effective(tol=1e-12)
+    assert rel(A2, Ao) < 1e-9
