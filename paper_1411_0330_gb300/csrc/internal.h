@@ -104,7 +104,11 @@ template <typename T>
 void launch_comp_sums(const T* x, int c, long long V, int S, double* partials, int nblk, double* out, cudaStream_t s);
 template <typename T>
 void launch_gamma_table(const OpArgs<T>& a, int dim, int physics, int green, const double* ref_mandel,
-                        const int* kofy, const int* kofz, cudaStream_t s);
+                        const int* kofy, const int* kofz, cudaStream_t s, const double* a0full = nullptr,
+                        const double* rot = nullptr);
+template <typename T>
+void launch_rotate_scalar(const T* in, T* out, long long V, int nsys, int d, const double* R, int to_internal,
+                          cudaStream_t s);
 void launch_d2f_begin(const double* r64, float* r32, float* x32, long long n, int S, SolverState* st,
                       double* partials, double tol, const unsigned char* active, int G, cudaStream_t s);
 void launch_f2d_axpy(double* x64, const float* x32, long long n, cudaStream_t s);

@@ -574,7 +574,8 @@ __global__ void __launch_bounds__(kThreads) k_cg_update(T* __restrict__ r, const
   const T* qs = q + s * n;
   Acc<T> acc;
   constexpr int VEC = 16 / sizeof(T);
-  const long long nv = n / VEC;
+  // 16-byte accesses only when every system's range starts on a 16-byte boundary
+  const long long nv = (n % VEC == 0) ? n / VEC : 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv; i += (long long)gridDim.x * blockDim.x) {
     T rv[VEC], qv[VEC];
     vload<T, VEC>(rs + i * VEC, rv);
@@ -698,6 +699,25 @@ __global__ void k_rotate(const T* in, T* out, long long V, long long nvox, int t
   }
 }
 
+// Scalar fields between the caller's axes and the common eigenbasis of the
+// reference and phase tensors: u_int = R^T u (to_internal) or u = R u_int.
+struct Rot3 {
+  double r[9];
+};
+template <typename T>
+__global__ void k_rotate_scalar(const T* in, T* out, long long V, long long nvox, int d, Rot3 R, int to_internal) {
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < nvox; q += (long long)gridDim.x * blockDim.x) {
+    const long long sys = q / V, v = q - sys * V;
+    const T* i0 = in + sys * d * V;
+    T* o0 = out + sys * d * V;
+    double a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    for (int i = 0; i < d; ++i) a[i] = i0[i * V + v];
+    for (int i = 0; i < d; ++i)
+      for (int k = 0; k < d; ++k) b[i] += (to_internal ? R.r[k * d + i] : R.r[i * d + k]) * a[k];
+    for (int i = 0; i < d; ++i) o0[i * V + v] = (T)b[i];
+  }
+}
+
 // Per-system, per-component sums, deterministic: partials[(s c + comp) nblk + blk].
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_comp_partials(const T* __restrict__ x, long long V, int c,
@@ -726,13 +746,23 @@ __global__ void __launch_bounds__(kThreads) k_comp_final(const double* __restric
 struct GammaCtx {
   int dim, physics, green, c;
   int n[3];
-  double ref[6];  // scalar: diagonal of A0; elastic: (K0, mu0)
+  double ref[6];  // scalar: diagonal of A0 in the internal basis; elastic: (K0, mu0)
+  // scalar problems in a rotated basis: the full A0 and the rotation R (columns =
+  // internal basis vectors); the table then holds R^T Gamma R
+  int rotated;
+  double A0[9];
+  double R[9];
 };
 
 __device__ void gamma0_acc(const GammaCtx& g, const double xi[3], double w, double* G) {
   if (g.physics == 0) {
     double q = 0.0;
-    for (int i = 0; i < g.dim; ++i) q += g.ref[i] * xi[i] * xi[i];
+    if (g.rotated) {
+      for (int i = 0; i < g.dim; ++i)
+        for (int j = 0; j < g.dim; ++j) q += g.A0[i * g.dim + j] * xi[i] * xi[j];
+    } else {
+      for (int i = 0; i < g.dim; ++i) q += g.ref[i] * xi[i] * xi[i];
+    }
     for (int i = 0; i < g.c; ++i)
       for (int j = 0; j < g.c; ++j) G[i * g.c + j] += w * xi[i] * xi[j] / q;
     return;
@@ -827,6 +857,15 @@ __global__ void k_gamma_table(OpArgs<T> a, GammaCtx g, const int* __restrict__ k
       for (int i = 0; i < c * c; ++i) Gi[i] = 0.0;
       for (int i = 0; i < c; ++i)
         Gi[i * c + i] = g.physics == 0 ? 1.0 / g.ref[i] : (i == 0 ? 1.0 / (3.0 * g.ref[0]) : 1.0 / (2.0 * g.ref[1]));
+    } else if (g.physics == 0 && g.rotated) {
+      // R^T G R: the operator in the common eigenbasis of A0 and the phases
+      for (int i = 0; i < c; ++i)
+        for (int j = 0; j < c; ++j) {
+          double s = 0.0;
+          for (int p = 0; p < c; ++p)
+            for (int q = 0; q < c; ++q) s += g.R[p * c + i] * G[p * c + q] * g.R[q * c + j];
+          Gi[i * c + j] = s;
+        }
     } else if (g.physics == 0) {
       for (int i = 0; i < c * c; ++i) Gi[i] = G[i];
     } else {
@@ -1074,6 +1113,16 @@ void launch_minres_step(double* x, double* r1, double* r2, double* q, double* wa
 }
 
 template <typename T>
+void launch_rotate_scalar(const T* in, T* out, long long V, int nsys, int d, const double* R, int to_internal,
+                          cudaStream_t s) {
+  Rot3 r;
+  for (int i = 0; i < 9; ++i) r.r[i] = R[i];
+  const long long nvox = V * nsys;
+  const int grid = (int)std::max(1LL, std::min((nvox + 255) / 256, 152LL * 8));
+  k_rotate_scalar<T><<<grid, 256, 0, s>>>(in, out, V, nvox, d, r, to_internal);
+}
+
+template <typename T>
 void launch_cg_update(T* r, const T* q, long long n, int S, SolverState* st, double* partials, int G, cudaStream_t s) {
   k_cg_update<T><<<dim3(G, S), kThreads, 0, s>>>(r, q, n, st, partials);
 }
@@ -1101,8 +1150,13 @@ void launch_comp_sums(const T* x, int c, long long V, int S, double* partials, i
 }
 template <typename T>
 void launch_gamma_table(const OpArgs<T>& a, int dim, int physics, int green, const double* ref_mandel,
-                        const int* kofy, const int* kofz, cudaStream_t s) {
+                        const int* kofy, const int* kofz, cudaStream_t s, const double* a0full, const double* rot) {
   GammaCtx g;
+  g.rotated = (a0full && rot) ? 1 : 0;
+  for (int i = 0; i < 9; ++i) {
+    g.A0[i] = g.rotated ? a0full[i] : 0.0;
+    g.R[i] = g.rotated ? rot[i] : 0.0;
+  }
   g.dim = dim;
   g.physics = physics;
   g.green = green;
@@ -1150,7 +1204,8 @@ void launch_scale_grad(const double* tau_all, const double* W, const unsigned ch
   template void launch_rotate<T>(const T*, T*, long long, int, int, cudaStream_t);                                 \
   template void launch_comp_sums<T>(const T*, int, long long, int, double*, int, double*, cudaStream_t);           \
   template void launch_gamma_table<T>(const OpArgs<T>&, int, int, int, const double*, const int*, const int*,      \
-                                      cudaStream_t);
+                                      cudaStream_t, const double*, const double*);                                 \
+  template void launch_rotate_scalar<T>(const T*, T*, long long, int, int, const double*, int, cudaStream_t);
 
 LSH_INSTANTIATE(double)
 LSH_INSTANTIATE(float)

@@ -16,6 +16,7 @@
 #include <cstring>
 #include <new>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "internal.h"
@@ -91,7 +92,59 @@ struct Derived {
   std::vector<double> m_in;    // nphase * c diagonal of M (0 when inactive)
   std::vector<unsigned char> act;
   int definite;          // +1 / -1: all active phases same sign; 0: indefinite
+  // scalar problems whose A0 and phase tensors are not all diagonal but commute
+  // (share eigenvectors): fields are carried in the common eigenbasis,
+  // u_internal = R^T u (R's columns are the eigenvectors)
+  bool rotated = false;
+  double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+  double A0full[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
+
+// Eigenvectors of a symmetric n x n matrix (n <= 3) by cyclic Jacobi rotations:
+// on return A is (numerically) diagonal and V holds the eigenvectors as columns.
+void jacobi_eigen(int n, double* A, double* V) {
+  for (int i = 0; i < n * n; ++i) V[i] = (i % (n + 1) == 0) ? 1.0 : 0.0;
+  for (int sweep = 0; sweep < 50; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) off += A[p * n + q] * A[p * n + q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = A[p * n + q];
+        if (apq == 0.0) continue;
+        const double theta = (A[q * n + q] - A[p * n + p]) / (2.0 * apq);
+        const double t = (theta >= 0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), s = t * c;
+        for (int k = 0; k < n; ++k) {  // A <- J^T A J
+          const double akp = A[k * n + p], akq = A[k * n + q];
+          A[k * n + p] = c * akp - s * akq;
+          A[k * n + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {
+          const double apk = A[p * n + k], aqk = A[q * n + k];
+          A[p * n + k] = c * apk - s * aqk;
+          A[q * n + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < n; ++k) {  // V <- V J
+          const double vkp = V[k * n + p], vkq = V[k * n + q];
+          V[k * n + p] = c * vkp - s * vkq;
+          V[k * n + q] = s * vkp + c * vkq;
+        }
+      }
+  }
+}
+
+// R^T M R for n x n matrices
+void rot_sandwich(int n, const double* R, const double* M, double* out) {
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < n; ++k)
+        for (int l = 0; l < n; ++l) s += R[k * n + i] * M[k * n + l] * R[l * n + j];
+      out[i * n + j] = s;
+    }
+}
 
 lsh_status derive(const lsh_problem* pr, Derived* d) {
   if (!pr) return LSH_ERR_INVALID_ARG;
@@ -146,20 +199,64 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
     d->ref_in[0] = 3.0 * K0;
     for (int i = 1; i < 6; ++i) d->ref_in[i] = 2.0 * mu0;
   } else {
+    // full d x d reference (given, or a0 I with a0 half the smallest diagonal entry)
+    double A0[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    bool diag = true;
     for (int ph = 0; ph < pr->nphase; ++ph)
       for (int i = 0; i < dim; ++i)
-        for (int j = 0; j < dim; ++j)
-          if (i != j && pr->phase_moduli[ph * dim * dim + i * dim + j] != 0.0) return LSH_ERR_UNSUPPORTED;
+        for (int j = 0; j < dim; ++j) {
+          const double v = pr->phase_moduli[ph * dim * dim + i * dim + j];
+          if (i != j && v != 0.0) diag = false;
+          if (v != pr->phase_moduli[ph * dim * dim + j * dim + i]) return LSH_ERR_INVALID_ARG;  // symmetric
+        }
     if (pr->ref_moduli) {
+      for (int i = 0; i < dim * dim; ++i) A0[i] = pr->ref_moduli[i];
       for (int i = 0; i < dim; ++i)
-        for (int j = 0; j < dim; ++j)
-          if (i != j && pr->ref_moduli[i * dim + j] != 0.0) return LSH_ERR_UNSUPPORTED;
-      for (int i = 0; i < dim; ++i) d->ref_in[i] = pr->ref_moduli[i * dim + i];
+        for (int j = 0; j < dim; ++j) {
+          if (A0[i * dim + j] != A0[j * dim + i]) return LSH_ERR_INVALID_ARG;
+          if (i != j && A0[i * dim + j] != 0.0) diag = false;
+        }
     } else {
       double amin = pr->phase_moduli[0];
       for (int ph = 0; ph < pr->nphase; ++ph)
         for (int i = 0; i < dim; ++i) amin = std::min(amin, pr->phase_moduli[ph * dim * dim + i * dim + i]);
-      for (int i = 0; i < dim; ++i) d->ref_in[i] = 0.5 * amin;
+      for (int i = 0; i < dim; ++i) A0[i * dim + i] = 0.5 * amin;
+    }
+    for (int i = 0; i < 9; ++i) d->A0full[i] = i < dim * dim ? A0[i] : 0.0;
+    if (diag) {
+      for (int i = 0; i < dim; ++i) d->ref_in[i] = A0[i * dim + i];
+    } else {
+      // tensors that commute share eigenvectors: take those of a generic
+      // combination, and check that every tensor is diagonal in them
+      if (d->has_scale || pr->green == LSH_GREEN_FD) return LSH_ERR_UNSUPPORTED;
+      double Sm[9], R[9];
+      double scale = 0.0;
+      for (int i = 0; i < dim * dim; ++i) {
+        Sm[i] = A0[i];
+        scale = std::max(scale, std::fabs(A0[i]));
+      }
+      for (int ph = 0; ph < pr->nphase; ++ph) {
+        const double w = 1.0 / std::sqrt(2.0 + ph * 1.6180339887498949);
+        for (int i = 0; i < dim * dim; ++i) {
+          Sm[i] += w * pr->phase_moduli[ph * dim * dim + i];
+          scale = std::max(scale, std::fabs(pr->phase_moduli[ph * dim * dim + i]));
+        }
+      }
+      jacobi_eigen(dim, Sm, R);
+      double D[9];
+      rot_sandwich(dim, R, A0, D);
+      for (int i = 0; i < dim; ++i)
+        for (int j = 0; j < dim; ++j)
+          if (i != j && std::fabs(D[i * dim + j]) > 1e-12 * scale) return LSH_ERR_UNSUPPORTED;
+      for (int i = 0; i < dim; ++i) d->ref_in[i] = D[i * dim + i];
+      for (int ph = 0; ph < pr->nphase; ++ph) {
+        rot_sandwich(dim, R, pr->phase_moduli + ph * dim * dim, D);
+        for (int i = 0; i < dim; ++i)
+          for (int j = 0; j < dim; ++j)
+            if (i != j && std::fabs(D[i * dim + j]) > 1e-12 * scale) return LSH_ERR_UNSUPPORTED;
+      }
+      d->rotated = true;
+      for (int i = 0; i < 9; ++i) d->R[i] = i < dim * dim ? R[i] : 0.0;
     }
     for (int i = 0; i < dim; ++i) {
       if (!(d->ref_in[i] > 0.0)) return LSH_ERR_REFERENCE_INDEFINITE;
@@ -177,6 +274,10 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
       const double K = pr->phase_moduli[2 * ph], mu = pr->phase_moduli[2 * ph + 1];
       md[0] = 3.0 * K;
       for (int i = 1; i < 6; ++i) md[i] = 2.0 * mu;
+    } else if (d->rotated) {
+      double D[9];
+      rot_sandwich(dim, d->R, pr->phase_moduli + ph * dim * dim, D);
+      for (int i = 0; i < dim; ++i) md[i] = D[i * dim + i];
     } else {
       for (int i = 0; i < dim; ++i) md[i] = pr->phase_moduli[ph * dim * dim + i * dim + i];
     }
@@ -472,7 +573,7 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   for (int i = 0; i < 6; ++i) a.ref[i] = (T)(i < d.c ? d.ref_in[i] : 0.0);
   a.loads = P.loads;
   // FP32 truncated operator: computed on the fly in the z pass (no table read)
-  a.onfly = (sizeof(T) == 4 && d.green == LSH_GREEN_TRUNCATED) ? 1 : 0;
+  a.onfly = (sizeof(T) == 4 && d.green == LSH_GREEN_TRUNCATED && !d.rotated) ? 1 : 0;
   a.fdphase = d.green == LSH_GREEN_FD ? 1 : 0;
   a.physics = d.physics;
   a.kofy = h->kofy;
@@ -513,6 +614,13 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
 // internal basis <-> Mandel for elasticity (see k_rotate)
 void to_internal(const Derived& d, const double* m, double* out) {
   for (int i = 0; i < d.c; ++i) out[i] = m[i];
+  if (d.rotated) {
+    for (int k = 0; k < d.c; ++k) {
+      double s = 0.0;
+      for (int i = 0; i < d.c; ++i) s += d.R[i * d.c + k] * m[i];
+      out[k] = s;
+    }
+  }
   if (d.physics == LSH_ELASTIC_ISO) {
     const double s3 = 1.0 / std::sqrt(3.0), s2 = 1.0 / std::sqrt(2.0), s6 = 1.0 / std::sqrt(6.0);
     out[0] = (m[0] + m[1] + m[2]) * s3;
@@ -522,6 +630,13 @@ void to_internal(const Derived& d, const double* m, double* out) {
 }
 void to_mandel(const Derived& d, const double* v, double* out) {
   for (int i = 0; i < d.c; ++i) out[i] = v[i];
+  if (d.rotated) {
+    for (int i = 0; i < d.c; ++i) {
+      double s = 0.0;
+      for (int k = 0; k < d.c; ++k) s += d.R[i * d.c + k] * v[k];
+      out[i] = s;
+    }
+  }
   if (d.physics == LSH_ELASTIC_ISO) {
     const double s3 = 1.0 / std::sqrt(3.0), s2 = 1.0 / std::sqrt(2.0), s6 = 1.0 / std::sqrt(6.0);
     out[0] = v[0] * s3 + v[1] * s2 + v[2] * s6;
@@ -540,7 +655,7 @@ void ref_matrix(const Derived& d, double* A0) {
       for (int j = 0; j < 3; ++j) A0[i * 6 + j] = lam0 + (i == j ? 2.0 * mu0 : 0.0);
     for (int i = 3; i < 6; ++i) A0[i * 6 + i] = 2.0 * mu0;
   } else {
-    for (int i = 0; i < c; ++i) A0[i * c + i] = d.ref_user[i];
+    for (int i = 0; i < c * c; ++i) A0[i] = d.A0full[i];
   }
 }
 
@@ -973,6 +1088,11 @@ lsh_status rotate_or_copy(lsh_handle* h, const double* in, double* out, int nsys
     h->launches += 1;
     return last_launch();
   }
+  if (d.rotated) {
+    launch_rotate_scalar<double>(in, out, d.V, nsys, d.c, d.R, to_internal, h->stream);
+    h->launches += 1;
+    return last_launch();
+  }
   if (in != out) LSH_CK(cudaMemcpyAsync(out, in, sizeof(double) * d.c * d.V * nsys, cudaMemcpyDeviceToDevice, h->stream));
   return LSH_OK;
 }
@@ -1096,9 +1216,11 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   set_smem_attrs<float>();
   tma_prepare();
   xreg_prepare();
-  launch_gamma_table<double>(h->pd.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st);
+  launch_gamma_table<double>(h->pd.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st,
+                             d.rotated ? d.A0full : nullptr, d.rotated ? d.R : nullptr);
   if (d.precision == LSH_MIXED)
-    launch_gamma_table<float>(h->pf.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st);
+    launch_gamma_table<float>(h->pf.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st,
+                              d.rotated ? d.A0full : nullptr, d.rotated ? d.R : nullptr);
   if (last_launch() != LSH_OK) { delete h; return LSH_ERR_CUDA; }
   s = scan_microstructure(h);  // synchronises the stream (host vectors may go)
   if (s) { delete h; return s; }
@@ -1129,28 +1251,35 @@ lsh_status lsh_apply(lsh_handle* h, int dtype, const void* x, void* y) {
     const int S = std::min(per_wave, d.B - b0);
     std::vector<double> zl(6 * (size_t)S, 0.0);
     Wave w{S, b0, 1, zl.data()};
+    // fields enter and leave in the caller's basis; the kernels work in the internal one
+    const bool rot = el || d.rotated;
+    auto rotate = [&](auto* in, auto* out, int to_internal) {
+      typedef std::remove_const_t<std::remove_pointer_t<decltype(in)>> TT;
+      if (el) launch_rotate<TT>(in, out, d.V, S, to_internal, h->stream);
+      else launch_rotate_scalar<TT>(in, out, d.V, S, d.c, d.R, to_internal, h->stream);
+    };
     if (dtype == LSH_F64) {
       PrecBufs<double>& P = h->pd;
       const double* in = (const double*)x + b0 * n;
       double* o = (double*)y + b0 * n;
-      if (el) {
-        launch_rotate<double>(in, P.p, d.V, S, 1, h->stream);
+      if (rot) {
+        rotate(in, P.p, 1);
         in = P.p;
       }
-      lsh_status s = apply_internal<double>(h, wave_args<double>(h, w), in, el ? P.q : o);
+      lsh_status s = apply_internal<double>(h, wave_args<double>(h, w), in, rot ? P.q : o);
       if (s) return s;
-      if (el) launch_rotate<double>(P.q, o, d.V, S, 0, h->stream);
+      if (rot) rotate((const double*)P.q, o, 0);
     } else {
       PrecBufs<float>& P = h->pf;
       const float* in = (const float*)x + b0 * n;
       float* o = (float*)y + b0 * n;
-      if (el) {
-        launch_rotate<float>(in, P.p, d.V, S, 1, h->stream);
+      if (rot) {
+        rotate(in, P.p, 1);
         in = P.p;
       }
-      lsh_status s = apply_internal<float>(h, wave_args<float>(h, w), in, el ? P.q : o);
+      lsh_status s = apply_internal<float>(h, wave_args<float>(h, w), in, rot ? P.q : o);
       if (s) return s;
-      if (el) launch_rotate<float>(P.q, o, d.V, S, 0, h->stream);
+      if (rot) rotate((const float*)P.q, o, 0);
     }
   }
   return last_launch();

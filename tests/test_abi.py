@@ -76,8 +76,10 @@ def test_invalid_arguments(lib):
     with pytest.raises(lsh.LSHError) as e:  # elasticity needs dim 3
         lsh.workspace_size((8, 8), EL, physics=lsh.ELASTIC)
     assert e.value.status == lsh.ERR_INVALID_ARG
-    with pytest.raises(lsh.LSHError) as e:  # non-diagonal conductivity
-        lsh.workspace_size((8, 8), np.array([[[2.0, 0.5], [0.5, 1.0]]]))
+    # anisotropic conductivities that share eigenvectors with A0 are accepted ...
+    lsh.workspace_size((8, 8), np.array([[[2.0, 0.5], [0.5, 1.0]]]))
+    with pytest.raises(lsh.LSHError) as e:  # ... tensors without common eigenvectors are not
+        lsh.workspace_size((8, 8), np.array([[[2.0, 0.5], [0.5, 1.0]], [[2.0, 0.0], [0.0, 1.0]]]))
     assert e.value.status == lsh.ERR_UNSUPPORTED
     with pytest.raises(lsh.LSHError) as e:  # reference not positive definite
         lsh.workspace_size((8, 8), np.array([np.eye(2)]), ref=-np.eye(2))

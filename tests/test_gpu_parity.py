@@ -539,3 +539,59 @@ def test_fd_green_operator_effective_and_reference_independence():
     h2 = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.FD, ref=0.9 * np.eye(2))
     A2, _ = h2.effective(tol=1e-12)
     assert rel(A2, Ao) < 1e-9
+
+
+def _rotation(d, seed):
+    q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((d, d)))
+    return q
+
+
+@pytest.mark.parametrize("shape,green,given_ref", [((24, 20), 1, True), ((10, 12, 16), 0, True),
+                                                    ((16, 16, 16), 1, False), ((9, 15), 0, False)])
+def test_anisotropic_commuting_reference(shape, green, given_ref):
+    """Scalar conductivity with anisotropic phase tensors that commute with an
+    anisotropic reference (common eigenvectors, Eq. (hyp3)): the library works in
+    their eigenbasis; apply and A* equal the oracle's full-tensor computation."""
+    d = len(shape)
+    Q = _rotation(d, sum(shape))
+    rng = np.random.default_rng(len(shape) + green)
+    mods = np.array([Q @ np.diag(rng.uniform(1.0, 8.0, d)) @ Q.T for _ in range(3)])
+    mods = 0.5 * (mods + mods.transpose(0, 2, 1))
+    ref = Q @ np.diag(rng.uniform(0.3, 0.6, d)) @ Q.T if given_ref else None
+    if ref is not None:
+        ref = 0.5 * (ref + ref.T)
+    ph = rng.integers(0, 3, shape).astype(np.uint8)
+    P = oracle.Problem(ph, mods, physics=0, green=green, ref=ref)
+    x = rng.standard_normal(P.field_shape)
+    for prec in (lsh.FP64, lsh.MIXED):
+        h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=green, ref=ref, precision=prec)
+        assert rel(h.apply(torch.from_numpy(x).cuda()).cpu().numpy(), oracle.apply(P, x)) < 1e-12
+        A, infos = h.effective(tol=1e-11)
+        Ao, _ = oracle.effective(P, tol=1e-13)
+        assert rel(A, Ao) < (1e-10 if prec == lsh.FP64 else 1e-8), (prec, rel(A, Ao))
+        assert np.allclose(A, A.T, atol=1e-9 * np.abs(A).max())
+
+
+def test_non_commuting_anisotropy_is_refused():
+    d = 2
+    Q = _rotation(d, 3)
+    mods = np.array([np.diag([1.0, 4.0]), Q @ np.diag([2.0, 5.0]) @ Q.T])
+    mods = 0.5 * (mods + mods.transpose(0, 2, 1))
+    ph = (np.arange(64).reshape(8, 8) % 2).astype(np.uint8)
+    with pytest.raises(lsh.LSHError) as e:
+        lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=0, ref=np.eye(2) * 0.4)
+    assert e.value.status == lsh.ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("shape", [(9, 15), (5, 7, 9), (3, 5, 6)])
+def test_mixed_solve_with_odd_field_lengths(shape):
+    """Mixed-precision solves where c V is not a multiple of 4 (FP32 systems do not
+    start on 16-byte boundaries): the vector kernels fall back to scalar accesses."""
+    rng = np.random.default_rng(sum(shape))
+    d = len(shape)
+    ph = rng.integers(0, 2, shape).astype(np.uint8)
+    mods = _scalar_mods(d, 9, nphase=2)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=1, precision=lsh.MIXED)
+    A, infos = h.effective(tol=1e-11)
+    Ao, _ = oracle.effective(oracle.Problem(ph, mods, physics=0, green=1), tol=1e-13)
+    assert rel(A, Ao) < 1e-8 and all(i["status"] == 0 for i in infos)
