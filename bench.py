@@ -484,6 +484,8 @@ def main():
     ap.add_argument("--impl", default="lsh", choices=["lsh", "reference"])
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--concurrent", action="store_true",
+                    help="solve the filtered and truncated handles together, one stream each")
     ap.add_argument("--workload", default="spheres128",
                     choices=["spheres128", "batch64", "contrast256", "gradient128"],
                     help="spheres128: the 128^3 sphere packing (default); batch64: 64 microstructures "
@@ -520,11 +522,21 @@ def main():
     ph_dev = torch.from_numpy(ph).to(dev)
     V = ph.size
     greens = (lsh.FILTERED, lsh.TRUNCATED)
-    h64 = [lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=g) for g in greens]
-    hmx = [lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=g, precision=lsh.MIXED, tune=True) for g in greens]
+    # with --concurrent each handle has its own stream and the two operators'
+    # solves run together (lsh_effective_batch: one host thread per handle)
+    streams = [torch.cuda.Stream(dev) if args.concurrent else None for _ in range(4)]
+    h64 = [lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=g, stream=streams[i]) for i, g in enumerate(greens)]
+    hmx = [lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=g, precision=lsh.MIXED, tune=True,
+                      stream=streams[2 + i]) for i, g in enumerate(greens)]
 
     def step(handles):
         its, res = 0, []
+        if args.concurrent:
+            As, Is = lsh.effective_batch(handles, tol=TOL)
+            for A, infos in zip(As, Is):
+                its += sum(i["iters"] for i in infos)
+                res.append((A, infos))
+            return its, res
         for h in handles:
             A, infos = h.effective(tol=TOL)
             its += sum(i["iters"] for i in infos)
