@@ -125,14 +125,15 @@ typedef struct lsh_handle lsh_handle;
 typedef struct lsh_tune_report {
   int xf_variant; /* FP32 forward x pass in use: 0 shared-memory stages, 1 register FFT  */
   int x_variant;  /* FP32 inverse x pass in use: 0 shared-memory stages, 1 register FFT,
-                     2 register FFT in a persistent double-buffered kernel             */
+                     2 register FFT in a persistent double-buffered kernel, 3 register
+                     FFT in blocks of 128 threads                                      */
   int y_variant;  /* FP32 y pass in use: 0 register FFT, 1 TMA tiles                    */
   int z_variant;  /* FP32 z pass (with Gamma) in use: 0 register FFT; TMA tiles of
                      1: 4 columns double-buffered, 2: 8 columns, 3: 8 columns double-
                      buffered, 4: 16 columns with the FFT exchange in the tile, 5: the
                      same with two components per thread                             */
   float xf_ms[2]; /* measured time of one launch per candidate (-1: not available)   */
-  float x_ms[3];
+  float x_ms[4];
   float y_ms[2];
   float z_ms[7];
 } lsh_tune_report;

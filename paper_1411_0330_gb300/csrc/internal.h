@@ -66,7 +66,8 @@ template <typename T> struct OpArgs {
   const CUtensorMap* tmz8;  // z boxes of 8 columns
   const CUtensorMap* tmz16; // z boxes of 16 columns
   int* fault;  // set by a kernel whose bounded wait ran out
-  int xreg;    // FP32 inverse x pass: 0 shared-memory stages, 1 register FFT, 2 register FFT persistent
+  int xreg;    // FP32 inverse x pass: 0 shared-memory stages, 1 register FFT, 2 register FFT persistent,
+               // 3 register FFT in blocks of 128 threads
   int xfreg;   // 1: FP32 forward x pass on the register FFT (kernels_x.cu)
 };
 
@@ -134,7 +135,7 @@ bool tma_z_variant_fits(const OpArgs<float>& a, int var);
 bool encode_z_map(CUtensorMap* out, void* H, int hs, int ny, int nz, int c, long long nsys, int tz);
 void tma_prepare();
 bool launch_xinv_reg(const OpArgs<float>& a, int mode, const float* xin, float* out, SolverState* st,
-                     double* partials, cudaStream_t s, bool persistent);
+                     double* partials, cudaStream_t s, bool persistent, bool small = false);
 void xreg_prepare();
 bool xinv_reg_fits(const OpArgs<float>& a);
 bool launch_xfwd_reg(const OpArgs<float>& a, int mode, const float* in, float* x, const float* r, float* p,

@@ -1084,7 +1084,7 @@ template <typename T>
 void launch_xinv(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* xin, T* out, SolverState* st,
                  double* partials, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (a.xreg && mode <= 2 && launch_xinv_reg(a, mode, xin, out, st, partials, s, a.xreg == 2)) return;
+    if (a.xreg && mode <= 2 && launch_xinv_reg(a, mode, xin, out, st, partials, s, a.xreg == 2, a.xreg == 3)) return;
   }
   const int grid = a.S * a.bps;
   constexpr int VV = 16 / sizeof(T);

@@ -26,17 +26,17 @@
 
 namespace lsh {
 
-template <int N> struct XReg {
+template <int N, int TH = 256> struct XReg {
   static constexpr int P = RegPlan<N>::P;
-  static constexpr int THREADS = 256;
+  static constexpr int THREADS = TH;
   static constexpr int LINES = THREADS / P;  // packed lines (row pairs) per block
   static constexpr int RY = 2 * LINES;       // rows per block
   static constexpr int OSTR = N + 4;         // shared row stride of the real output (floats)
   static constexpr int LS = RegLine<float, N>::LS;
 };
 
-template <int N> size_t xreg_smem(int hs) {
-  typedef XReg<N> XC;
+template <int N, int TH = 256> size_t xreg_smem(int hs) {
+  typedef XReg<N, TH> XC;
   const size_t rows = std::max(sizeof(float2) * (size_t)XC::RY * hs, sizeof(float) * (size_t)XC::RY * XC::OSTR);
   const size_t rows16 = (rows + 15) & ~(size_t)15;
   return rows16 + sizeof(float2) * ((size_t)XC::LINES * XC::LS + N);
@@ -47,14 +47,14 @@ template <int N> size_t xreg_smem(int hs) {
 // FFT, epilogue, reduction.  False (uniform) if the copy did not land in time.
 // MODE 0: out = P (M xin + g).  MODE 1 (CG): q = P (M p + g), (p, q) -> alpha.
 // MODE 2 (residual): out = P (load - M xin - g), (r, r) -> st[s].aux[0].
-template <int MODE, int N>
+template <int MODE, int N, int TH = 256>
 __device__ __forceinline__ bool xinv_rows(const OpArgs<float>& a, const float* __restrict__ xin,
                                           float* __restrict__ out, SolverState* __restrict__ st,
                                           double* __restrict__ partials, int bps, long long rb, float2* HS,
                                           float2* ex, const float2* tw, const float* mloc,
                                           const unsigned char* aloc, uint64_t* bar, uint32_t parity) {
   typedef RegLine<float, N> RL;
-  typedef XReg<N> XC;
+  typedef XReg<N, TH> XC;
   constexpr int P = XC::P, R1 = RL::R1, Q = RL::Q, RY = XC::RY, OSTR = XC::OSTR;
   float* OS = reinterpret_cast<float*>(HS);  // the real rows replace the spectrum rows
   const int s = (int)(rb / bps);
@@ -172,11 +172,13 @@ __device__ __forceinline__ bool xinv_rows(const OpArgs<float>& a, const float* _
 }
 
 // One block per RY rows.
-template <int MODE, int N>
-__global__ void __launch_bounds__(256, 2) k_xinv_reg(OpArgs<float> a, const float* __restrict__ xin,
-                                                     float* __restrict__ out, SolverState* __restrict__ st,
-                                                     double* __restrict__ partials, int bps, size_t rows_bytes) {
-  typedef XReg<N> XC;
+template <int MODE, int N, int TH = 256>
+__global__ void __launch_bounds__(TH, TH == 256 ? 2 : 4) k_xinv_reg(OpArgs<float> a, const float* __restrict__ xin,
+                                                                   float* __restrict__ out,
+                                                                   SolverState* __restrict__ st,
+                                                                   double* __restrict__ partials, int bps,
+                                                                   size_t rows_bytes) {
+  typedef XReg<N, TH> XC;
   const int s = blockIdx.x / bps;
   if (MODE == 1 && st[s].done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -200,7 +202,7 @@ __global__ void __launch_bounds__(256, 2) k_xinv_reg(OpArgs<float> a, const floa
     bulk_load_1d(HS, a.H + row0 * a.hs, bytes, &bar);
   }
   __syncthreads();
-  if (!xinv_rows<MODE, N>(a, xin, out, st, partials, bps, blockIdx.x, HS, ex, tw, mloc, aloc, &bar, 0)) {
+  if (!xinv_rows<MODE, N, TH>(a, xin, out, st, partials, bps, blockIdx.x, HS, ex, tw, mloc, aloc, &bar, 0)) {
     if (threadIdx.x == 0) {
       mbar_wait(&bar, 0);
       atomicOr(a.fault, 1);
@@ -450,19 +452,19 @@ template <int N> bool launch_xfwd_reg_n(const OpArgs<float>& a, int mode, const 
   return true;
 }
 
-template <int N> bool launch_xinv_reg_n(const OpArgs<float>& a, int mode, const float* xin, float* out,
-                                        SolverState* st, double* partials, cudaStream_t s) {
-  typedef XReg<N> XC;
+template <int N, int TH = 256> bool launch_xinv_reg_n(const OpArgs<float>& a, int mode, const float* xin, float* out,
+                                                      SolverState* st, double* partials, cudaStream_t s) {
+  typedef XReg<N, TH> XC;
   if (a.rps % XC::RY != 0 || (a.hs & 1)) return false;
   const int bps = a.rps / XC::RY;
   const size_t rows = std::max(sizeof(float2) * (size_t)XC::RY * a.hs, sizeof(float) * (size_t)XC::RY * XC::OSTR);
   const size_t rows16 = (rows + 15) & ~(size_t)15;
-  const size_t smem = xreg_smem<N>(a.hs);
+  const size_t smem = xreg_smem<N, TH>(a.hs);
   if (smem > 200 * 1024) return false;
   const int grid = a.S * bps;
-  if (mode == 0) k_xinv_reg<0, N><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
-  else if (mode == 1) k_xinv_reg<1, N><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
-  else k_xinv_reg<2, N><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
+  if (mode == 0) k_xinv_reg<0, N, TH><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
+  else if (mode == 1) k_xinv_reg<1, N, TH><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
+  else k_xinv_reg<2, N, TH><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
   return true;
 }
 
@@ -507,6 +509,9 @@ template <int N> bool launch_xinv_regp_n(const OpArgs<float>& a, int mode, const
 
 template <int N> void xreg_attrs() {
   const int mx = 200 * 1024;
+  cudaFuncSetAttribute(k_xinv_reg<0, N, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv_reg<1, N, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv_reg<2, N, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xinv_regp<0, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xinv_regp<1, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xinv_regp<2, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
@@ -558,7 +563,17 @@ bool xinv_reg_fits(const OpArgs<float>& a) {
 // False when this grid has no register inverse x pass (the caller keeps the
 // shared-memory kernel).  persistent: the double-buffered persistent kernel.
 bool launch_xinv_reg(const OpArgs<float>& a, int mode, const float* xin, float* out, SolverState* st,
-                     double* partials, cudaStream_t s, bool persistent) {
+                     double* partials, cudaStream_t s, bool persistent, bool small) {
+  if (small) {
+    switch (a.nx) {
+      case 16: return launch_xinv_reg_n<16, 128>(a, mode, xin, out, st, partials, s);
+      case 32: return launch_xinv_reg_n<32, 128>(a, mode, xin, out, st, partials, s);
+      case 64: return launch_xinv_reg_n<64, 128>(a, mode, xin, out, st, partials, s);
+      case 128: return launch_xinv_reg_n<128, 128>(a, mode, xin, out, st, partials, s);
+      case 256: return launch_xinv_reg_n<256, 128>(a, mode, xin, out, st, partials, s);
+      default: return false;
+    }
+  }
   if (persistent) {
     switch (a.nx) {
       case 16: return launch_xinv_regp_n<16>(a, mode, xin, out, st, partials, s);

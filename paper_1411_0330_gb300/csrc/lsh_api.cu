@@ -1425,7 +1425,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   for (int k = 0; k < 2; ++k) r.xf_ms[k] = -1.f;
   r.y_variant = h->pf.a.ytma;
   r.z_variant = h->pf.a.ztma;
-  for (int k = 0; k < 3; ++k) r.x_ms[k] = -1.f;
+  for (int k = 0; k < 4; ++k) r.x_ms[k] = -1.f;
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
   for (int k = 0; k < 7; ++k) r.z_ms[k] = -1.f;
   const Derived& d = h->d;
@@ -1455,17 +1455,19 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       }
       return ms / 5.f;
     };
+    // the x passes are timed as in a CG iteration, on states of a running solve
+    std::vector<SolverState> fake(d.Smax);
+    for (auto& f : fake) {
+      f = SolverState{};
+      f.iter = 1;
+      f.rr = 1.0;
+    }
+    LSH_CK(cudaMemcpyAsync(P.st, fake.data(), sizeof(SolverState) * d.Smax, cudaMemcpyHostToDevice, s));
     if (xfwd_reg_fits(a)) {
-      // forward x pass with the CG prologue, on states of a running solve
-      std::vector<SolverState> fake(d.Smax);
-      for (auto& f : fake) {
-        f = SolverState{};
-        f.iter = 1;
-      }
-      LSH_CK(cudaMemcpyAsync(P.st, fake.data(), sizeof(SolverState) * d.Smax, cudaMemcpyHostToDevice, s));
       for (int v = 0; v < 2; ++v) {
         a.xfreg = v;
         r.xf_ms[v] = timeit([&]() {
+          cudaMemcpyAsync(P.st, fake.data(), sizeof(SolverState) * d.Smax, cudaMemcpyHostToDevice, s);
           if (v == 1) return launch_xfwd_reg(a, 1, nullptr, P.x, P.r, P.p, P.st, s);
           launch_xfwd<float>(a, P.L, 1, nullptr, P.x, P.r, P.p, P.st, s);
           return true;
@@ -1475,13 +1477,15 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       a.xfreg = r.xf_variant;
     }
     {
-      // inverse x pass with the local term (apply mode: no reductions, no state)
+      // inverse x pass with the local term and the (p, Kp) reduction
       int bx = 0;
-      for (int v = 0; v < 3; ++v) {
+      for (int v = 0; v < 4; ++v) {
         a.xreg = v;
         r.x_ms[v] = timeit([&]() {
-          if (v >= 1) return launch_xinv_reg(a, 0, P.x, P.q, nullptr, nullptr, s, v == 2);
-          launch_xinv<float>(a, P.L, 0, P.x, P.q, nullptr, nullptr, s);
+          // fresh states each time: a breakdown flagged on the arbitrary data would stop the next launch
+          cudaMemcpyAsync(P.st, fake.data(), sizeof(SolverState) * d.Smax, cudaMemcpyHostToDevice, s);
+          if (v >= 1) return launch_xinv_reg(a, 1, P.p, P.q, P.st, h->partials, s, v == 2, v == 3);
+          launch_xinv<float>(a, P.L, 1, P.p, P.q, P.st, h->partials, s);
           return true;
         });
         if (r.x_ms[v] > 0.f && r.x_ms[v] < r.x_ms[bx]) bx = v;
@@ -1533,7 +1537,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
 
 lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
-  if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 2 || y_variant < 0 || y_variant > 1 ||
+  if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 3 || y_variant < 0 || y_variant > 1 ||
       z_variant < 0 || z_variant > 6)
     return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;

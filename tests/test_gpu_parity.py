@@ -451,7 +451,7 @@ def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkey
         y_tma = h_tma.apply(xt)
         assert torch.equal(y_tma, y_reg), zv
     # the register x passes: other rounding order than the staged ones
-    for xf, xv in ((1, 0), (0, 1), (1, 1), (1, 2)):
+    for xf, xv in ((1, 0), (0, 1), (1, 1), (1, 2), (1, 3)):
         try:
             h_tma.set_variants(xf, xv, 1, 0)
         except lsh.LSHError as e:
@@ -460,7 +460,7 @@ def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkey
         y_x = h_tma.apply(xt)
         assert rel(y_x.cpu().numpy(), oracle.apply(P, x)) < 2e-5, (xf, xv)
     rep = h_tma.autotune()
-    assert rep["z_variant"] in range(7) and rep["y_variant"] in (0, 1) and rep["x_variant"] in (0, 1, 2)
+    assert rep["z_variant"] in range(7) and rep["y_variant"] in (0, 1) and rep["x_variant"] in (0, 1, 2, 3)
     assert rep["xf_variant"] in (0, 1)
     assert rel(h_tma.apply(xt).cpu().numpy(), oracle.apply(P, x)) < 2e-5
 
