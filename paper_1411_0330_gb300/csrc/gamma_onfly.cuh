@@ -99,6 +99,7 @@ __device__ __forceinline__ void gamma_trunc_onfly(const OpArgs<T>& a, int kx, in
 // (k unsigned, as in the table), before (sign -1) and after (+1) the real table.
 template <typename T, int NC>
 __device__ __forceinline__ void fd_rotate(const OpArgs<T>& a, int kx, int ky, int kz, C2<T>* v, T sign) {
+  if constexpr (NC == 6) return;  // scalar operator only: nothing in the elastic kernels
   const int kk[3] = {kx, ky, kz};
   const int nn[3] = {a.nx, a.ny, a.nz};
 #pragma unroll
