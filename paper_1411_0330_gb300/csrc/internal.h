@@ -19,6 +19,7 @@ namespace lsh {
 template <typename T> struct OpArgs {
   int nx, ny, nz, nxh, c;
   int hs;            // row stride of the half spectrum H (nxh rounded up to 4: 32-byte FP32 rows)
+  int ts;            // row stride of the Gamma table (nxh rounded up to 8: 32-byte FP32 rows)
   long long V;       // voxels per system
   int S;             // systems in this launch
   int sys0;          // global index of system 0 of this launch
@@ -34,7 +35,7 @@ template <typename T> struct OpArgs {
   const C2<T>* twz;
   const int* posx;   // frequency kx -> position after the x DIF
   C2<T>* H;          // half spectrum [S][c][nz][ny][hs] (kx < nxh used; y, z positions per kofy / kofz)
-  const T* gtab;     // Gamma^h (internal basis, scaled by 1/V): [ncoef][nz][ny][nxh]
+  const T* gtab;     // Gamma^h (internal basis, scaled by 1/V): [ncoef][nz][ny][ts]
   int ncoef;
   // local term M_beta = (A_beta - A0)^{-1}, diagonal in the internal basis
   const unsigned char* phase;  // [nbatch][V]

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs
   const int nz = a.nz, TZ = a.TZ;
   const long long zstride = (long long)a.ny * a.hs;  // distance between z planes of H
   const long long cstride = zstride * nz;
-  const long long gzs = (long long)a.ny * a.nxh, gcs = gzs * nz;  // the same in the Gamma table
+  const long long gzs = (long long)a.ny * a.ts, gcs = gzs * nz;  // the same in the Gamma table
   C2<T>* __restrict__ Hp = a.H + (long long)s * NC * cstride + (long long)yp * a.hs + kx0;
   const int tot = NC * nz * TZ;
   for (int base = threadIdx.x; base < tot; base += 4 * blockDim.x) {
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs
   __syncthreads();
   if (nz > 1) fft_lines<T, false>(buf, NC * TZ, a.lsz, a.pz, tw);
   // per-frequency product with Gamma^h_k
-  const T* __restrict__ G = a.gtab + (long long)yp * a.nxh + kx0;
+  const T* __restrict__ G = a.gtab + (long long)yp * a.ts + kx0;
   const int ky = (a.onfly || a.fdphase) ? a.kofy[yp] : 0;
   for (int idx = threadIdx.x; idx < nz * TZ; idx += blockDim.x) {
     const int zp = fdiv(idx, TZ), t = idx - zp * TZ;
@@ -795,6 +795,7 @@ __device__ void gamma0_acc(const GammaCtx& g, const double xi[3], double w, doub
 template <typename T>
 __global__ void k_gamma_table(OpArgs<T> a, GammaCtx g, const int* __restrict__ kofy, const int* __restrict__ kofz) {
   const long long nf = (long long)a.nz * a.ny * a.nxh;
+  const long long ntab = (long long)a.nz * a.ny * a.ts;  // per coefficient, rows padded to ts
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
     const int kx = (int)(f % a.nxh);
     const int yp = (int)((f / a.nxh) % a.ny);
@@ -891,7 +892,8 @@ __global__ void k_gamma_table(OpArgs<T> a, GammaCtx g, const int* __restrict__ k
     int coef = 0;
     T* out = const_cast<T*>(a.gtab);
     for (int i = 0; i < c; ++i)
-      for (int j = i; j < c; ++j, ++coef) out[coef * nf + f] = (T)(0.5 * (Gi[i * c + j] + Gi[j * c + i]) * invV);
+      for (int j = i; j < c; ++j, ++coef)
+        out[coef * ntab + ((long long)zp * a.ny + yp) * a.ts + kx] = (T)(0.5 * (Gi[i * c + j] + Gi[j * c + i]) * invV);
   }
 }
 

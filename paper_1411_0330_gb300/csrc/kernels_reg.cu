@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS, ZCfg<T, NC, N, T
   const bool valid = yp >= 0;
   const long long zstride = (long long)a.ny * a.hs;  // z planes of H
   const long long cstride = zstride * N;
-  const long long gzs = (long long)a.ny * a.nxh, gcs = gzs * N;  // the same in the Gamma table
+  const long long gzs = (long long)a.ny * a.ts, gcs = gzs * N;  // the same in the Gamma table
   C2<T>* __restrict__ Hl = a.H + ((long long)s * NC + comp) * cstride + (valid ? (long long)yp * a.hs + kx : 0);
   C2<T>* exl = buf + (comp * TZ + i) * RL::LS;
   C2<T> v[R1];
@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS, ZCfg<T, NC, N, T
     constexpr int NCO = NC * (NC + 1) / 2;
     auto off = [&](int item) {
       const int kz = item / TZ, li = item - kz * TZ;
-      return kz * gzs + (long long)line_yp[li] * a.nxh + line_kx[li];
+      return kz * gzs + (long long)line_yp[li] * a.ts + line_kx[li];
     };
     auto ok = [&](int item) { return item < N * TZ && line_yp[item % TZ] >= 0; };
     T gc[NCO], gn[NCO];

@@ -80,7 +80,7 @@ template <typename T> void twiddles(int n, std::vector<T>& out) {
 
 // ---------------------------------------------------------------- derived problem data
 struct Derived {
-  int dim, c, nx, ny, nz, nxh, hs, ncoef, physics, green, precision, nphase;
+  int dim, c, nx, ny, nz, nxh, hs, ts, ncoef, physics, green, precision, nphase;
   int B;       // microstructures
   int Smax;    // systems per wave
   long long V;
@@ -169,6 +169,7 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
   d->V = (long long)d->nx * d->ny * d->nz;
   d->nxh = d->nx / 2 + 1;
   d->hs = (d->nxh + 3) & ~3;  // 32-byte rows: z-pass column segments start on DRAM sectors
+  d->ts = (d->nxh + 7) & ~7;  // the same for the FP32 Gamma table rows
   d->c = pr->physics == LSH_ELASTIC_ISO ? 6 : pr->dim;
   d->ncoef = d->c * (d->c + 1) / 2;
   d->B = pr->nbatch > 1 ? pr->nbatch : 1;
@@ -379,7 +380,7 @@ Layout make_layout(const Derived& d) {
   };
   const int S = d.Smax;
   const long long n = (long long)d.c * d.V;  // elements per system
-  const long long nf = (long long)d.nz * d.ny * d.nxh;   // Gamma table per coefficient
+  const long long nf = (long long)d.nz * d.ny * d.ts;    // Gamma table per coefficient (padded rows)
   const long long nfh = (long long)d.nz * d.ny * d.hs;  // half spectrum per component
   LaunchCfg Ld = make_cfg<double>(d), Lf = make_cfg<float>(d);
   long long np = std::max<long long>({(long long)S * Ld.grid_x, (long long)S * Lf.grid_x, (long long)S * Ld.ew_per_sys,
@@ -541,6 +542,7 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.nz = d.nz;
   a.nxh = d.nxh;
   a.hs = d.hs;
+  a.ts = d.ts;
   a.c = d.c;
   a.V = d.V;
   a.S = d.Smax;

@@ -264,6 +264,7 @@ extern "C" lsh_status lsh_apply_noalloc(const lsh_problem* pr, const double* x, 
   a.nz = nz;
   a.nxh = nxh;
   a.hs = nxh;
+  a.ts = nxh;
   a.fdphase = pr->green == LSH_GREEN_FD ? 1 : 0;
   a.kofy = (const int*)(base + o_kofy);  // frequency of each y / z position (phase rotations)
   a.kofz = (const int*)(base + o_kofz);
