@@ -66,8 +66,12 @@ enum { LSH_F64 = 0, LSH_F32 = 1 }; /* element type of fields passed to lsh_apply
 /* AUTO: CG when every active phase has A_phase - A0 of one sign (K definite),
  * MINRES (Paige-Saunders, FP64) when the signs differ (K indefinite, e.g. the
  * reference k0 = (k_min + k_max)/2); CG: always CG (with a breakdown check);
- * MINRES: always MINRES (handles of at most 2^22 unknowns, or indefinite). */
-enum { LSH_SOLVER_AUTO = 0, LSH_SOLVER_CG = 1, LSH_SOLVER_MINRES = 2 };
+ * MINRES: always MINRES (handles of at most 2^22 unknowns, or indefinite);
+ * BASIC: the fixed-point scheme of Moulinec and Suquet written on the
+ * polarisation, tau <- tau + (A - A0)(b - K tau) (FP64; converges when A0 lies
+ * between the phases, e.g. the mean of the extreme moduli, at the rate
+ * (A_max - A_min) / (A_max + A_min) for that choice). */
+enum { LSH_SOLVER_AUTO = 0, LSH_SOLVER_CG = 1, LSH_SOLVER_MINRES = 2, LSH_SOLVER_BASIC = 3 };
 
 /* Problem description (Sec. 2.2 and Sec. 3).  All pointers are read during
  * lsh_setup only. */
@@ -98,7 +102,7 @@ typedef struct lsh_problem {
 typedef struct lsh_solve_opts {
   double tol;        /* stop when ||b - K tau||_2 <= tol ||b||_2 (Sec. 5 uses 1e-5)    */
   int maxit;         /* iteration limit (FP64 CG iterations, or inner iterations summed) */
-  int solver;        /* LSH_SOLVER_AUTO, LSH_SOLVER_CG or LSH_SOLVER_MINRES                */
+  int solver;        /* LSH_SOLVER_AUTO, _CG, _MINRES or _BASIC                            */
   double inner_tol;  /* LSH_MIXED: relative residual reduction of each inner solve
                         (<= 0 selects 0.5 sqrt(tol) within [1e-6, 1e-3]: two
                         refinement steps)                                               */

@@ -540,6 +540,30 @@ __global__ void __launch_bounds__(kThreads) k_mr_c(double* __restrict__ x, doubl
   }
 }
 
+// Basic fixed-point scheme (Moulinec-Suquet): with r = b - K tau, the update
+// tau += (A - A0) r equals tau_new = (A - A0)(b - Gamma tau), the classic
+// iteration written on the polarisation.  Grid (G, S); systems whose flag is
+// set (converged) are left alone.
+__global__ void __launch_bounds__(kThreads) k_basic_update(OpArgs<double> a, double* __restrict__ x,
+                                                           const double* __restrict__ r,
+                                                           const unsigned char* __restrict__ flags) {
+  const int s = blockIdx.y;
+  if (flags[s]) return;
+  const long long n = (long long)a.c * a.V;
+  const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V;
+  double* xs = x + s * n;
+  const double* rs = r + s * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int comp = (int)(i / a.V);
+    const long long vox = i - (long long)comp * a.V;
+    const int p = a.phase[pbase + vox];
+    if (!a.act[p]) continue;
+    double mod = a.modtab[p * a.c + comp];
+    if (a.scale) mod *= (double)a.scale[pbase + vox];
+    xs[i] += (mod - a.ref[comp]) * rs[i];
+  }
+}
+
 // Start: beta1 = |r0| (the right-hand side of this MINRES run: b, or b - K x0
 // for a warm start), zero recurrence scalars; the tolerance is relative to |b|.
 __global__ void k_mr_begin(SolverState* __restrict__ st, MinresScalars* __restrict__ ms,
@@ -1101,6 +1125,11 @@ void launch_xinv(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* xin,
     else if (mode == 3) k_xinv<T, 3, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
     else k_xinv<T, 2, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
   }
+}
+
+void launch_basic_update(const OpArgs<double>& a, double* x, const double* r, const unsigned char* flags, int G,
+                         cudaStream_t s) {
+  k_basic_update<<<dim3(G, a.S), kThreads, 0, s>>>(a, x, r, flags);
 }
 
 void launch_minres_begin(SolverState* st, MinresScalars* ms, const double* rhs2, const double* bb, double tol, int S,

@@ -896,6 +896,58 @@ lsh_status minres_run(lsh_handle* h, const OpArgs<double>& a, int maxit, int che
   return LSH_OK;
 }
 
+// The basic scheme on the FP64 operator for the systems of a wave (x holds the
+// initial guesses): per iteration one residual r = b - K x (five passes) and
+// the update x += (A - A0) r; residual norms read every check_every iterations.
+lsh_status basic_run(lsh_handle* h, const OpArgs<double>& a, int maxit, int check_every, double tol,
+                     const std::vector<double>& bb, std::vector<int>& iters, std::vector<double>& relres,
+                     std::vector<int>& done) {
+  PrecBufs<double>& P = h->pd;
+  cudaStream_t s = h->stream;
+  const int S = a.S;
+  SolverState* sres = h->st + 2 * h->d.Smax;
+  std::vector<unsigned char> flags(S, 0);
+  iters.assign(S, 0);
+  relres.assign(S, 0.0);
+  done.assign(S, 0);
+  for (int k = 0; k < S; ++k)
+    if (!(bb[k] > 0.0)) {
+      flags[k] = 1;
+      done[k] = 1;
+    }
+  LSH_CK(cudaMemcpyAsync(h->flags, flags.data(), S, cudaMemcpyHostToDevice, s));
+  lsh_status stt;
+  std::vector<SolverState> rs(S);
+  int it = 0;
+  while (it < maxit) {
+    bool all = true;
+    for (int k = 0; k < S; ++k) all = all && done[k];
+    if (all) break;
+    const int chunk = std::min(check_every, maxit - it);
+    for (int j = 0; j < chunk; ++j) {
+      if ((stt = residual64(h, a, P.x, P.r))) return stt;
+      launch_basic_update(a, P.x, P.r, h->flags, P.L.ew_per_sys, s);
+      h->launches += 1;
+    }
+    it += chunk;
+    // the residual of the last update (one more application, not counted as an iteration)
+    if ((stt = residual64(h, a, P.x, P.r))) return stt;
+    if ((stt = read_states(h, sres, S, rs.data()))) return stt;
+    for (int k = 0; k < S; ++k) {
+      if (done[k]) continue;
+      iters[k] = it;
+      relres[k] = bb[k] > 0 ? std::sqrt(std::max(rs[k].aux[0], 0.0) / bb[k]) : 0.0;
+      if (!std::isfinite(relres[k])) return LSH_ERR_BREAKDOWN;
+      if (relres[k] <= tol) {
+        done[k] = 1;
+        flags[k] = 1;
+      }
+    }
+    LSH_CK(cudaMemcpyAsync(h->flags, flags.data(), S, cudaMemcpyHostToDevice, s));
+  }
+  return LSH_OK;
+}
+
 // A kernel that gave up a bounded wait (TMA copies) set the fault word.
 lsh_status check_fault(lsh_handle* h) {
   int f = 0;
@@ -935,7 +987,23 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
   std::vector<SolverState> st;
   const int solver = o ? o->solver : LSH_SOLVER_AUTO;
   const bool use_minres = solver == LSH_SOLVER_MINRES || (solver == LSH_SOLVER_AUTO && d.definite == 0);
-  if (use_minres) {
+  if (solver == LSH_SOLVER_BASIC) {
+    // Moulinec-Suquet fixed point, FP64 whatever the precision
+    if (!warm) {
+      launch_fill_rhs<double>(ad, Pd.r, Pd.x, G, h->stream);
+      h->launches += 1;
+    }
+    if ((stt = last_launch())) return stt;
+    std::vector<int> its, dn;
+    std::vector<double> rel;
+    if ((stt = basic_run(h, ad, maxit, check, tol, bb, its, rel, dn))) return stt;
+    for (int s = 0; s < S; ++s) {
+      infos[s].iters = its[s];
+      infos[s].applies64 += its[s];
+      infos[s].relres = rel[s];
+      infos[s].status = dn[s] ? LSH_OK : LSH_ERR_NOT_CONVERGED;
+    }
+  } else if (use_minres) {
     // indefinite operator (or asked for): MINRES in FP64 whatever the precision
     if (!h->wa) return LSH_ERR_UNSUPPORTED;
     const double* rhs2 = h->bbdev;

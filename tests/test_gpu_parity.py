@@ -595,3 +595,29 @@ def test_mixed_solve_with_odd_field_lengths(shape):
     A, infos = h.effective(tol=1e-11)
     Ao, _ = oracle.effective(oracle.Problem(ph, mods, physics=0, green=1), tol=1e-13)
     assert rel(A, Ao) < 1e-8 and all(i["status"] == 0 for i in infos)
+
+
+def test_basic_scheme_matches_oracle():
+    """The Moulinec-Suquet fixed point (tau <- tau + (A - A0)(b - K tau)) with the
+    reference between the phases converges to the same A* as the oracle; with the
+    soft default reference it does not converge and says so."""
+    ph = ms.square_inclusion(32)
+    mods = np.array([np.eye(2), 10 * np.eye(2)])
+    ref = 5.5 * np.eye(2)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.TRUNCATED, ref=ref)
+    A, infos = h.effective(tol=1e-10, solver=lsh.SOLVER_BASIC, maxit=2000)
+    Ao, _ = oracle.effective(oracle.Problem(ph, mods, green=0, ref=ref), tol=1e-13)
+    assert rel(A, Ao) < 1e-9, (A, Ao, infos)
+    assert all(i["status"] == 0 and i["relres"] <= 1e-10 for i in infos)
+    # elasticity, mixed handle (runs in FP64), reference at the mean of the phases
+    phs, _, _ = ms.sphere_microstructure(12, 1.5, 0.2, seed=41)
+    refe = 0.5 * (EL[0] + EL[1])
+    he = lsh.Handle(torch.from_numpy(phs).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, ref=refe,
+                    precision=lsh.MIXED)
+    Ae, inf_e = he.effective(tol=1e-10, solver=lsh.SOLVER_BASIC, maxit=3000)
+    Aeo, _ = oracle.effective(oracle.Problem(phs, EL, physics=1, green=1, ref=refe), tol=1e-13)
+    assert rel(Ae, Aeo) < 1e-9, rel(Ae, Aeo)
+    # soft reference: the fixed point diverges
+    hs = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.TRUNCATED)
+    _, inf_s = hs.effective(tol=1e-10, solver=lsh.SOLVER_BASIC, maxit=40, raise_on_fail=False)
+    assert all(i["status"] != 0 for i in inf_s)
