@@ -64,7 +64,8 @@ class _Problem(ctypes.Structure):
                 ("phase_moduli", ctypes.POINTER(ctypes.c_double)),
                 ("ref_moduli", ctypes.POINTER(ctypes.c_double)),
                 ("phase", ctypes.POINTER(ctypes.c_ubyte)),
-                ("scale", ctypes.POINTER(ctypes.c_double))]
+                ("scale", ctypes.POINTER(ctypes.c_double)),
+                ("frac", ctypes.POINTER(ctypes.c_double))]
 
 
 def _load():
@@ -110,9 +111,11 @@ class Problem:
     ref: reference medium in the same format as one phase; None -> the
         oracle's default rule (half the softest phase).
     scale: optional per-voxel factor s with A_beta = s_beta A_phase(beta).
+    frac: optional per-voxel volume fraction of phase 1 (two phases): the local
+        operator becomes the voxel average of (A - A0)^{-1}, Eq. (def_ah).
     """
 
-    def __init__(self, phase, phase_moduli, physics=SCALAR, green=TRUNCATED, ref=None, scale=None):
+    def __init__(self, phase, phase_moduli, physics=SCALAR, green=TRUNCATED, ref=None, scale=None, frac=None):
         phase = np.ascontiguousarray(phase, dtype=np.uint8)
         self.dim = phase.ndim
         if self.dim not in (2, 3):
@@ -128,6 +131,7 @@ class Problem:
             ref = default_reference(self.dim, physics, self.phase_moduli)
         self.ref = np.ascontiguousarray(ref, dtype=np.float64)
         self.scale = None if scale is None else np.ascontiguousarray(scale, dtype=np.float64)
+        self.frac = None if frac is None else np.ascontiguousarray(frac, dtype=np.float64)
         self.c = 6 if physics == ELASTIC else self.dim
         self.V = int(phase.size)
 
@@ -145,11 +149,12 @@ class Problem:
         s.ref_moduli = _dptr(self.ref)
         s.phase = self.phase.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte))
         s.scale = _dptr(self.scale) if self.scale is not None else ctypes.POINTER(ctypes.c_double)()
+        s.frac = _dptr(self.frac) if self.frac is not None else ctypes.POINTER(ctypes.c_double)()
         return s
 
     def with_(self, **kw) -> "Problem":
         args = dict(phase=self.phase, phase_moduli=self.phase_moduli, physics=self.physics,
-                    green=self.green, ref=self.ref, scale=self.scale)
+                    green=self.green, ref=self.ref, scale=self.scale, frac=self.frac)
         args.update(kw)
         return Problem(**args)
 

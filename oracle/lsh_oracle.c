@@ -179,6 +179,22 @@ int or_default_reference(int dim, int physics, int nphase, const double *mod, do
 static int local_M(const or_problem *p, long vox, double *M, int *active) {
   int c = or_ncomp(p);
   double A[36], A0[36], D[36];
+  if (p->frac) {
+    /* Eq. (def_ah): the voxel average of (A(x) - A0)^{-1} over its two phases */
+    if (p->nphase != 2 || p->scale) return OR_ERR_ARG;
+    double M0[36], M1[36];
+    material_matrix(p, p->ref_moduli, A0);
+    for (int ph = 0; ph < 2; ++ph) {
+      material_matrix(p, p->phase_moduli + (long)ph * (p->physics == OR_ELASTIC ? 2 : c * c), A);
+      for (int i = 0; i < c * c; ++i) D[i] = A[i] - A0[i];
+      if (mat_inverse(c, D, ph ? M1 : M0)) return OR_ERR_SINGULAR;
+    }
+    const double f = p->frac[vox];
+    if (!(f >= 0.0 && f <= 1.0)) return OR_ERR_ARG;
+    for (int i = 0; i < c * c; ++i) M[i] = f * M1[i] + (1.0 - f) * M0[i];
+    *active = 1;
+    return OR_OK;
+  }
   int ph = p->phase[vox];
   if (ph >= p->nphase) return OR_ERR_ARG;
   material_matrix(p, p->phase_moduli + (long)ph * (p->physics == OR_ELASTIC ? 2 : c * c), A);
@@ -460,7 +476,7 @@ static int check_problem(const or_problem *p) {
   return OR_OK;
 }
 
-/* Per-phase cache of M (only when there is no per-voxel scale). */
+/* Per-phase cache of M (only when there is no per-voxel scale or fraction). */
 typedef struct {
   double *M;            /* nphase * c * c */
   unsigned char *act;   /* nphase */
@@ -472,7 +488,7 @@ static int mcache_init(const or_problem *p, mcache *mc) {
   mc->M = NULL;
   mc->act = NULL;
   mc->ok = 0;
-  if (p->scale) return OR_OK;
+  if (p->scale || p->frac) return OR_OK;
   mc->M = (double *)calloc((size_t)p->nphase * c * c, sizeof(double));
   mc->act = (unsigned char *)calloc((size_t)p->nphase, 1);
   if (!mc->M || !mc->act) return OR_ERR_NOMEM;
@@ -921,6 +937,7 @@ int or_effective_variational(const or_problem *p, const double *tau_all, double 
 int or_scale_gradient(const or_problem *p, const double *tau_all, const double *W, double *grad) {
   int st = check_problem(p);
   if (st) return st;
+  if (p->frac) return OR_ERR_ARG;  /* the scale derivative needs one material per voxel */
   int c = or_ncomp(p);
   long V = or_nvox(p), N = c * V;
   for (long v = 0; v < V; ++v) {

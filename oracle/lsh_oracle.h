@@ -53,6 +53,10 @@ typedef struct {
   const double *ref_moduli;    /* A0 in the same format as one phase            */
   const unsigned char *phase;  /* phase id per voxel                            */
   const double *scale;         /* optional: A_beta = scale_beta * A_phase, or NULL */
+  const double *frac;          /* optional (two phases, neither equal to A0): volume
+                                  fraction f_beta of phase 1 in voxel beta; the local
+                                  operator is then the voxel average of (A(x) - A0)^{-1},
+                                  Eq. (def_ah): f M_1 + (1 - f) M_0; NULL otherwise   */
 } or_problem;
 
 int or_ncomp(const or_problem *p);
@@ -62,8 +66,8 @@ long or_nvox(const or_problem *p);
 int or_default_reference(int dim, int physics, int nphase, const double *phase_moduli,
                          double *ref_out);
 
-/* Per-voxel local operator M_beta = (A_beta - A0)^{-1} (Eq. (7), (def_ah) with
- * one material per voxel), c*c per voxel, and the I0 indicator. */
+/* Per-voxel local operator M_beta = (A_beta - A0)^{-1} (Eq. (7); with `frac`
+ * the average over the voxel, Eq. (def_ah)), c*c per voxel, and the I0 indicator. */
 int or_local_operator(const or_problem *p, double *M, unsigned char *active);
 
 /* Continuous Green operator at a nonzero frequency xi (Sec. 2.2.1):

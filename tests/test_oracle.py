@@ -415,3 +415,44 @@ def test_default_reference_rule(oracle_mod):
     assert np.isclose(ref[1], mu1 / 2)
     nu0 = (3 * ref[0] - 2 * ref[1]) / (2 * (3 * ref[0] + ref[1]))
     assert np.isclose(nu0, 0.3)
+
+
+# ---------------------------------------------------------------- sub-voxel averaging, Eq. (def_ah)
+def test_fraction_zero_one_reduces_to_phases(oracle_mod):
+    """Volume fractions of exactly 0 or 1 give the one-material-per-voxel operator."""
+    rng = np.random.default_rng(71)
+    ph = (rng.random((6, 7, 8)) < 0.4).astype(np.uint8)
+    mods = np.array([k_mu(1.0, 0.3), k_mu(10.0, 0.2)])
+    P = oracle_mod.Problem(ph, mods, physics=oracle_mod.ELASTIC, green=oracle_mod.FILTERED)
+    Pf = P.with_(frac=ph.astype(np.float64))
+    x = rng.standard_normal(P.field_shape)
+    assert np.allclose(oracle_mod.apply(Pf, x), oracle_mod.apply(P, x), rtol=0, atol=1e-13)
+    A, _ = oracle_mod.effective(P, tol=1e-13)
+    Af, _ = oracle_mod.effective(Pf, tol=1e-13)
+    assert np.allclose(Af, A, rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("physics", [0, 1])
+def test_uniform_fraction_gives_the_averaged_uniform_medium(oracle_mod, physics):
+    """The same fraction f in every voxel is a uniform medium whose local operator
+    is f M1 + (1 - f) M0, so A* = A0 + (f M1 + (1 - f) M0)^{-1} exactly (Gamma^h_0 = 0
+    annihilates the constant polarisation)."""
+    f = 0.3
+    if physics == 1:
+        mods = np.array([k_mu(1.0, 0.3), k_mu(10.0, 0.2)])
+        ref = np.array(k_mu(0.4, 0.3))
+        A0 = iso_mandel(*ref)
+        A1, A2 = iso_mandel(*mods[0]), iso_mandel(*mods[1])
+        shape = (6, 6, 6)
+    else:
+        mods = np.array([np.diag([1.0, 2.0]), np.diag([7.0, 5.0])])
+        ref = 0.5 * np.eye(2)
+        A0, A1, A2 = ref, mods[0], mods[1]
+        shape = (8, 10)
+    M = (1 - f) * np.linalg.inv(A1 - A0) + f * np.linalg.inv(A2 - A0)
+    expected = A0 + np.linalg.inv(M)
+    ph = np.zeros(shape, np.uint8)
+    P = oracle_mod.Problem(ph, mods, physics=physics, green=oracle_mod.FILTERED, ref=ref,
+                           frac=np.full(shape, f))
+    A, _ = oracle_mod.effective(P, tol=1e-14)
+    assert np.allclose(A, expected, rtol=1e-12, atol=1e-12)
