@@ -97,6 +97,12 @@ typedef struct lsh_problem {
   int nbatch;                  /* microstructures sharing grid, phases and A0 (<= 1: one) */
   int max_systems;             /* systems (microstructure x load) solved simultaneously;
                                   bounds the workspace.  <= 0: nbatch * c                 */
+  int scale_kind;              /* what `scale` holds: 0 a factor s of the phase moduli
+                                  (A_beta = s_beta A_phase); 1 the volume fraction f of
+                                  phase 1 in each voxel of a two-phase medium, whose
+                                  local operator is then the voxel average of
+                                  (A(x) - A0)^{-1}, Eq. (def_ah): f M_1 + (1 - f) M_0
+                                  (the phase map is not used; no gradient)               */
 } lsh_problem;
 
 typedef struct lsh_solve_opts {

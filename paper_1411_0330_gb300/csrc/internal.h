@@ -40,6 +40,7 @@ template <typename T> struct OpArgs {
   // local term M_beta = (A_beta - A0)^{-1}, diagonal in the internal basis
   const unsigned char* phase;  // [nbatch][V]
   const float* scale;          // [nbatch][V] or null
+  int frac;                    // 1: scale holds the volume fraction of phase 1 (Eq. (def_ah))
   const unsigned char* act;    // per phase: 1 if A_phase != A0 (voxel in I0)
   int nphase;
   const T* mtab;               // per phase * c: diagonal of M (no scale field)

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xinv(OpArgs<T
     pos[i] = a.posx[i];
   }
   const int ntab = a.nphase * a.c;
-  for (int i = threadIdx.x; i < ntab; i += blockDim.x) mloc[i] = a.scale ? a.modtab[i] : a.mtab[i];
+  for (int i = threadIdx.x; i < ntab; i += blockDim.x) mloc[i] = (a.scale && !a.frac) ? a.modtab[i] : a.mtab[i];
   for (int i = threadIdx.x; i < a.nphase; i += blockDim.x) aloc[i] = a.act[i];
   __syncthreads();
   const int blk = blockIdx.x - s * a.bps;
@@ -388,7 +388,11 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xinv(OpArgs<T
         const int p = ph[h2][u];
         const bool active = aloc[p] != 0;
         T m = mloc[p * a.c + comp[h2]];
-        if (a.scale) m = (T)1 / ((T)a.scale[voxs[h2] + u] * m - a.ref[comp[h2]]);
+        if (a.scale) {
+          const T f = (T)a.scale[voxs[h2] + u];
+          m = a.frac ? f * mloc[a.c + comp[h2]] + ((T)1 - f) * mloc[comp[h2]]  // Eq. (def_ah)
+                     : (T)1 / (f * m - a.ref[comp[h2]]);
+        }
         const T gv = h2 ? zc[u].y : zc[u].x;
         const T xq = xv[h2][u];
         if (MODE == 0) {
@@ -558,9 +562,16 @@ __global__ void __launch_bounds__(kThreads) k_basic_update(OpArgs<double> a, dou
     const long long vox = i - (long long)comp * a.V;
     const int p = a.phase[pbase + vox];
     if (!a.act[p]) continue;
-    double mod = a.modtab[p * a.c + comp];
-    if (a.scale) mod *= (double)a.scale[pbase + vox];
-    xs[i] += (mod - a.ref[comp]) * rs[i];
+    double d;
+    if (a.scale && a.frac) {
+      const double f = (double)a.scale[pbase + vox];
+      d = 1.0 / (f * a.mtab[a.c + comp] + (1.0 - f) * a.mtab[comp]);  // inverse of the averaged M
+    } else {
+      double mod = a.modtab[p * a.c + comp];
+      if (a.scale) mod *= (double)a.scale[pbase + vox];
+      d = mod - a.ref[comp];
+    }
+    xs[i] += d * rs[i];
   }
 }
 

@@ -133,7 +133,11 @@ __device__ __forceinline__ bool xinv_rows(const OpArgs<float>& a, const float* _
       const int p = ph[u];
       const bool active = aloc[p] != 0;
       float m = mloc[p * a.c + comp];
-      if (a.scale) m = 1.f / (a.scale[pbase + vox + u] * m - a.ref[comp]);
+      if (a.scale) {
+        const float f = a.scale[pbase + vox + u];
+        m = a.frac ? f * mloc[a.c + comp] + (1.f - f) * mloc[comp]  // Eq. (def_ah)
+                   : 1.f / (f * m - a.ref[comp]);
+      }
       if (MODE == 0) {
         ov[u] = active ? m * xq[u] + gv[u] : 0.f;
       } else if (MODE == 1) {
@@ -196,7 +200,7 @@ __global__ void __launch_bounds__(TH, TH == 256 ? 2 : 4) k_xinv_reg(OpArgs<float
   float2* tw = ex + XC::LINES * XC::LS;
   for (int u = threadIdx.x; u < N; u += blockDim.x) tw[u] = a.twx[u];
   const int ntab = a.nphase * a.c;
-  for (int u = threadIdx.x; u < ntab; u += blockDim.x) mloc[u] = a.scale ? a.modtab[u] : a.mtab[u];
+  for (int u = threadIdx.x; u < ntab; u += blockDim.x) mloc[u] = (a.scale && !a.frac) ? a.modtab[u] : a.mtab[u];
   for (int u = threadIdx.x; u < a.nphase; u += blockDim.x) aloc[u] = a.act[u];
   const int blk = blockIdx.x - s * bps;
   const int rloc = blk * RY;                            // first row inside the system
@@ -288,7 +292,11 @@ __global__ void __launch_bounds__(TH, TH == 256 ? 2 : 4) k_xinv_reg(OpArgs<float
       const int p = ph[u];
       const bool active = aloc[p] != 0;
       float m = mloc[p * a.c + comp];
-      if (a.scale) m = 1.f / (a.scale[pbase + vox + u] * m - a.ref[comp]);
+      if (a.scale) {
+        const float f = a.scale[pbase + vox + u];
+        m = a.frac ? f * mloc[a.c + comp] + (1.f - f) * mloc[comp]  // Eq. (def_ah)
+                   : 1.f / (f * m - a.ref[comp]);
+      }
       if (MODE == 0) {
         ov[u] = active ? m * xq[u] + gv[u] : 0.f;
       } else if (MODE == 1) {
@@ -343,7 +351,7 @@ __global__ void __launch_bounds__(256, 2) k_xinv_regp(OpArgs<float> a, const flo
   const int ntab = a.nphase * a.c;
   unsigned char* aloc = reinterpret_cast<unsigned char*>(mloc + ntab);
   for (int u = threadIdx.x; u < N; u += blockDim.x) tw[u] = a.twx[u];
-  for (int u = threadIdx.x; u < ntab; u += blockDim.x) mloc[u] = a.scale ? a.modtab[u] : a.mtab[u];
+  for (int u = threadIdx.x; u < ntab; u += blockDim.x) mloc[u] = (a.scale && !a.frac) ? a.modtab[u] : a.mtab[u];
   for (int u = threadIdx.x; u < a.nphase; u += blockDim.x) aloc[u] = a.act[u];
   const uint32_t bytes = (uint32_t)(sizeof(float2) * (size_t)XC::RY * a.hs);
   auto live = [&](long long rb) { return rb < nrb && (MODE != 1 || st[rb / bps].done == 0); };

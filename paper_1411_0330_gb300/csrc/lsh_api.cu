@@ -85,6 +85,7 @@ struct Derived {
   int Smax;    // systems per wave
   long long V;
   bool has_scale;
+  bool frac = false;  // scale holds volume fractions of phase 1 (two phases)
   Plan1D px, py, pz;
   double ref_in[6];      // diagonal of A0 in the internal basis
   double ref_user[6];    // scalar: diagonal of A0; elastic: (K0, mu0)
@@ -177,11 +178,14 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
   if (pr->max_systems > 0) d->Smax = std::min(d->Smax, pr->max_systems);
   if ((long long)d->Smax * d->c * d->nz > 65535LL || (long long)d->B * d->V > (1LL << 40)) return LSH_ERR_UNSUPPORTED_SIZE;
   d->has_scale = pr->scale != nullptr;
+  if (pr->scale_kind != 0 && pr->scale_kind != 1) return LSH_ERR_INVALID_ARG;
+  d->frac = d->has_scale && pr->scale_kind == 1;
+  if (d->frac && pr->nphase != 2) return LSH_ERR_INVALID_ARG;
   if (!make_plan(d->nx, &d->px) || !make_plan(d->ny, &d->py) || !make_plan(d->nz, &d->pz))
     return LSH_ERR_UNSUPPORTED_SIZE;
   const int c = d->c, dim = d->dim;
   // reference medium
-  if (!pr->ref_moduli && d->has_scale) return LSH_ERR_INVALID_ARG;
+  if (!pr->ref_moduli && d->has_scale && !d->frac) return LSH_ERR_INVALID_ARG;
   if (pr->physics == LSH_ELASTIC_ISO) {
     double K0, mu0;
     if (pr->ref_moduli) {
@@ -282,7 +286,7 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
     } else {
       for (int i = 0; i < dim; ++i) md[i] = pr->phase_moduli[ph * dim * dim + i * dim + i];
     }
-    if (d->has_scale) {
+    if (d->has_scale && !d->frac) {
       // with a scale field every voxel is in I0; the sign structure of
       // s A_phase - A0 is the caller's responsibility (A0 softer than all)
       d->act[ph] = 1;
@@ -306,6 +310,10 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
     }
   }
   d->definite = (pos && neg) ? 0 : (neg ? -1 : 1);
+  if (d->frac) {
+    // averaged (A - A0)^{-1} needs both phases away from A0; every voxel is in I0
+    if (!d->act[0] || !d->act[1]) return LSH_ERR_SINGULAR_CONTRAST;
+  }
   return LSH_OK;
 }
 
@@ -568,6 +576,7 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.ncoef = d.ncoef;
   a.phase = h->phase;
   a.scale = h->scale;
+  a.frac = d.frac ? 1 : 0;
   a.act = h->act;
   a.nphase = d.nphase;
   a.mtab = P.mtab;
@@ -1473,6 +1482,7 @@ lsh_status lsh_effective_batch(int nh, lsh_handle* const* hs, const lsh_solve_op
 
 lsh_status lsh_effective_grad(lsh_handle* h, const double* tau_all, const double* W, double* grad) {
   if (!h || !tau_all || !W || !grad) return LSH_ERR_INVALID_ARG;
+  if (h->d.frac) return LSH_ERR_UNSUPPORTED;
   const Derived& d = h->d;
   double wbuf[64] = {0};
   for (int i = 0; i < d.c * d.c; ++i) wbuf[i] = W[i];

@@ -124,6 +124,7 @@ extern "C" lsh_status lsh_apply_noalloc(const lsh_problem* pr, const double* x, 
   if (pr->green != LSH_GREEN_TRUNCATED && pr->green != LSH_GREEN_FILTERED && pr->green != LSH_GREEN_FD)
     return LSH_ERR_INVALID_ARG;
   if (pr->green == LSH_GREEN_FD && pr->physics != LSH_SCALAR) return LSH_ERR_UNSUPPORTED;
+  if (pr->scale && pr->scale_kind != 0) return LSH_ERR_UNSUPPORTED;
   if (pr->nphase < 1 || pr->nphase > 256) return LSH_ERR_INVALID_ARG;
   if (pr->scale && !pr->ref_moduli) return LSH_ERR_INVALID_ARG;
   const int dim = pr->dim, nx = pr->n[0], ny = pr->n[1], nz = dim == 3 ? pr->n[2] : 1;

@@ -45,7 +45,8 @@ class _Problem(ctypes.Structure):
                 ("phase_moduli", ctypes.POINTER(ctypes.c_double)),
                 ("ref_moduli", ctypes.POINTER(ctypes.c_double)),
                 ("phase", ctypes.c_void_p), ("phase_on_host", ctypes.c_int),
-                ("scale", ctypes.c_void_p), ("nbatch", ctypes.c_int), ("max_systems", ctypes.c_int)]
+                ("scale", ctypes.c_void_p), ("nbatch", ctypes.c_int), ("max_systems", ctypes.c_int),
+                ("scale_kind", ctypes.c_int)]
 
 
 class _Opts(ctypes.Structure):
@@ -129,7 +130,7 @@ def _check(status: int, what: str, allow=()):
 
 
 def _problem_struct(phase_ptr, on_host, shape, physics, green, precision, moduli, ref, scale_ptr, nbatch=1,
-                    max_systems=0):
+                    max_systems=0, scale_kind=0):
     s = _Problem()
     dim = len(shape)
     s.dim = dim
@@ -145,6 +146,7 @@ def _problem_struct(phase_ptr, on_host, shape, physics, green, precision, moduli
     s.scale = scale_ptr
     s.nbatch = nbatch
     s.max_systems = max_systems
+    s.scale_kind = scale_kind
     return s
 
 
@@ -196,12 +198,14 @@ class Handle:
     phase_moduli: scalar -> (nphase, d, d) diagonal conductivities; elastic -> (nphase, 2) (K, mu).
     ref: reference medium in the same format as one phase, or None (half the softest phase).
     scale: optional per-voxel float32 factor s (A_beta = s_beta A_phase), shaped like phase.
+    fraction: instead of scale, the per-voxel volume fraction of phase 1 of a two-phase medium
+        (sub-voxel averaging of (A - A0)^{-1}, Eq. (def_ah)); the phase map is then not used.
     max_systems: systems (microstructure x load) solved at once; bounds the workspace.
     tune: run lsh_autotune after setup (times the FP32 y / z pass variants, keeps the fastest).
     """
 
     def __init__(self, phase, phase_moduli, physics=SCALAR, green=TRUNCATED, precision=FP64, ref=None,
-                 scale=None, device=None, stream=None, batch=False, max_systems=0, tune=False):
+                 scale=None, device=None, stream=None, batch=False, max_systems=0, tune=False, fraction=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("liblsh needs a CUDA device; no CPU fallback exists")
@@ -227,6 +231,11 @@ class Handle:
         self.c = 6 if physics == ELASTIC else self.dim
         self.V = int(np.prod(self.shape))
         self.moduli = np.ascontiguousarray(phase_moduli, dtype=np.float64)
+        self.scale_kind = 0
+        if fraction is not None:
+            if scale is not None:
+                raise ValueError("scale and fraction are exclusive")
+            scale, self.scale_kind = fraction, 1
         self.ref = None if ref is None else np.ascontiguousarray(ref, dtype=np.float64)
         on_host = phase_t.device.type == "cpu"
         scale_t = None
@@ -239,7 +248,7 @@ class Handle:
         self.phase_source = phase_t  # kept so the scale field can be replaced alone
         s = _problem_struct(ctypes.c_void_p(phase_t.data_ptr()), on_host, self.shape, physics, green, precision,
                             self.moduli, self.ref, ctypes.c_void_p(scale_t.data_ptr()) if scale_t is not None else None,
-                            self.nbatch, max_systems)
+                            self.nbatch, max_systems, self.scale_kind)
         nbytes = ctypes.c_size_t(0)
         _check(self.lib.lsh_workspace_size(ctypes.byref(s), ctypes.byref(nbytes)), "lsh_workspace_size")
         self.workspace = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)

@@ -142,6 +142,14 @@ def sphere_microstructure(n: int, radius_vox: float, fraction: float, seed: int,
     return voxelize_spheres(n, cen, r), cen, r
 
 
+def sphere_fractions(n, centres: np.ndarray, radius: float, sub: int = 4) -> np.ndarray:
+    """Volume fraction of the union of spheres in each voxel of an n^3 grid,
+    estimated on a regular sub^3 lattice of points per voxel (point in a sphere:
+    periodic minimum-image distance <= radius).  float32, shape (n, n, n)."""
+    fine = voxelize_spheres(n * sub, centres, radius).astype(np.float32)
+    return fine.reshape(n, sub, n, sub, n, sub).mean(axis=(1, 3, 5)).astype(np.float32)
+
+
 def scale_field(shape, seed: int, lo: float = 0.5, hi: float = 2.0) -> np.ndarray:
     """Per-voxel stiffness scale s ~ U(lo, hi), float32."""
     rng = np.random.default_rng(seed)
