@@ -152,8 +152,8 @@ def pass_flops(kind, V, c, nx, ny, nz, nxh):
 # systems of the 128^3 workload, from the ncu captures summarised in
 # profiles/fp32_passes_128cube_six_systems.md (filtered operator); to be
 # retaken whenever one of these kernels changes.
-NCU_TRAFFIC_FP32 = {"x_forward": 1771.1e6, "y_forward": 587.7e6, "z_gamma": 865.8e6, "y_inverse": 587.7e6,
-                    "x_inverse_local": 902.1e6, "cg_update": 862.1e6}
+NCU_TRAFFIC_FP32 = {"x_forward": 1770.9e6, "y_forward": 588.4e6, "z_gamma": 873.5e6, "y_inverse": 587.6e6,
+                    "x_inverse_local": 901.6e6, "cg_update": 862.9e6}
 
 
 def load_peaks():
