@@ -230,6 +230,24 @@ def profile_case(kind):
     return 0
 
 
+# ----------------------------------------------------------------- replicas
+def slowest_rank_ms(ms, world, device):
+    """The timed region's duration on the slowest rank (every rank solves its own
+    copy of the workload; no data-path collective)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t[0])
+
+
+def replica_rate(units_per_rank, world, ms_slowest):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world / (ms_slowest / 1e3)
+
+
 # ----------------------------------------------------------------- other workloads
 def _wall(fn):
     """Wall time of a synchronous call that may use several streams."""
@@ -622,10 +640,7 @@ def main():
         torch.cuda.synchronize()
         clocks = clk.stop()
         ms = e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([ms], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t[0])
+        ms = slowest_rank_ms(ms, world, dev)
         profs = [h.profile_read(reset=True) for h in handles]
         for h in handles:
             h.profile_enable(False)
@@ -639,9 +654,9 @@ def main():
     # comparison: the plain FP64 solver on the same workload
     ms_64, its_64, last_64, prof_64, clocks64 = timed(h64, True, "timed_fp64")
     nrep = world
-    value_64 = its_64 * V * nrep / (ms_64 / 1e3)
-    value_raw = its_mx * V * nrep / (ms_mx / 1e3)
-    value = its_64 * V * nrep / (ms_mx / 1e3)  # FP64-equivalent: the FP64 solver's iterations, mixed time
+    value_64 = replica_rate(its_64 * V, nrep, ms_64)
+    value_raw = replica_rate(its_mx * V, nrep, ms_mx)
+    value = replica_rate(its_64 * V, nrep, ms_mx)  # FP64-equivalent: the FP64 solver's iterations, mixed time
     cerr = max(float(np.abs(a[0] - b[0]).max() / np.abs(b[0]).max()) for a, b in zip(last_mx, last_64))
     launches = sum(p["launches"] for p in prof_mx)
 
