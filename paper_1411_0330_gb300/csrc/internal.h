@@ -121,6 +121,7 @@ void launch_scale_grad(const double* tau_all, const double* W, const unsigned ch
                        const double* modtab, const double* ref, int c, int elastic, long long V, int B,
                        double* grad, cudaStream_t s);
 
+void launch_dot_finalize(SolverState* st, const double* partials, int nb, int S, cudaStream_t s);
 void launch_basic_update(const OpArgs<double>& a, double* x, const double* r, const unsigned char* flags, int G,
                          cudaStream_t s);
 void launch_minres_begin(SolverState* st, MinresScalars* ms, const double* rhs2, const double* bb, double tol, int S,

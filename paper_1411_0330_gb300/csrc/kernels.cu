@@ -434,6 +434,31 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_xinv(OpArgs<T
   }
 }
 
+// ------------------------------------------------------------------ (p, Kp) from per-block partials
+// One block per system sums the partials of its nb blocks in block order and
+// sets alpha = (r, r) / (p, Kp) (or flags a breakdown), as the ticket reduction
+// of the inverse x pass does.
+__global__ void __launch_bounds__(kThreads) k_dot_finalize(SolverState* __restrict__ st,
+                                                           const double* __restrict__ partials, int nb) {
+  const int s = blockIdx.x;
+  SolverState* sst = st + s;
+  if (sst->done) return;
+  const double* part = partials + (long long)s * nb;
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) v += part[i];
+  const double sum = block_sum(v);
+  if (threadIdx.x == 0) {
+    sst->pq = sum;
+    if (!(fabs(sum) > 0.0) || !isfinite(sum) || !isfinite(sst->rr)) {
+      sst->status = 5;  // LSH_ERR_BREAKDOWN
+      sst->alpha = 0.0;
+      sst->done = 1;
+    } else {
+      sst->alpha = sst->rr / sum;
+    }
+  }
+}
+
 // ------------------------------------------------------------------ MINRES vector kernels
 // One MINRES iteration after q = K r2 (r2 = beta v, so K v = q / beta) and
 // pq = (r2, q) from the inverse x pass:
@@ -1136,6 +1161,10 @@ void launch_xinv(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* xin,
     else if (mode == 3) k_xinv<T, 3, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
     else k_xinv<T, 2, 1><<<grid, L.threads, L.smem_x, s>>>(a, xin, out, st, partials);
   }
+}
+
+void launch_dot_finalize(SolverState* st, const double* partials, int nb, int S, cudaStream_t s) {
+  k_dot_finalize<<<S, kThreads, 0, s>>>(st, partials, nb);
 }
 
 void launch_basic_update(const OpArgs<double>& a, double* x, const double* r, const unsigned char* flags, int G,

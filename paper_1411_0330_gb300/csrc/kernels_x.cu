@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(TH, TH == 256 ? 2 : 4) k_xinv_reg(OpArgs<float
   typedef XReg<N, TH> XC;
   constexpr int P = XC::P, R1 = RL::R1, Q = RL::Q, RY = XC::RY, OSTR = XC::OSTR;
   const int s = blockIdx.x / bps;
-  if (MODE == 1 && st[s].done) return;
+  if ((MODE == 1 || MODE == 4) && st[s].done) return;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ float mloc[256 * 6];
   __shared__ unsigned char aloc[256];
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(TH, TH == 256 ? 2 : 4) k_xinv_reg(OpArgs<float
       }
       if (MODE == 0) {
         ov[u] = active ? m * xq[u] + gv[u] : 0.f;
-      } else if (MODE == 1) {
+      } else if (MODE == 1 || MODE == 4) {
         ov[u] = active ? m * xq[u] + gv[u] : 0.f;
         acc.add(xq[u] * ov[u]);
       } else {
@@ -309,7 +309,11 @@ __global__ void __launch_bounds__(TH, TH == 256 ? 2 : 4) k_xinv_reg(OpArgs<float
     }
     *reinterpret_cast<float4*>(out + g) = make_float4(ov[0], ov[1], ov[2], ov[3]);
   }
-  if (MODE != 0) {
+  if (MODE == 4) {
+    // (p, Kp) partial of this block only; k_dot_finalize sums them (no fence, no ticket)
+    const double tot = block_reduce(acc);
+    if (threadIdx.x == 0) partials[(long long)s * bps + blk] = tot;
+  } else if (MODE != 0) {
     const double tot = block_reduce(acc);
     double* part = partials + (long long)s * bps;
     SolverState* sst = st + s;
@@ -586,8 +590,11 @@ template <int N, int TH = 256> bool launch_xinv_reg_n(const OpArgs<float>& a, in
   if (smem > 200 * 1024) return false;
   const int grid = a.S * bps;
   if (mode == 0) k_xinv_reg<0, N, TH><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
-  else if (mode == 1) k_xinv_reg<1, N, TH><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
-  else k_xinv_reg<2, N, TH><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
+  else if (mode == 1) {
+    // CG: partials per block, then one small kernel per system turns them into alpha
+    k_xinv_reg<4, N, TH><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
+    launch_dot_finalize(st, partials, bps, a.S, s);
+  } else k_xinv_reg<2, N, TH><<<grid, XC::THREADS, smem, s>>>(a, xin, out, st, partials, bps, rows16);
   return true;
 }
 
@@ -632,6 +639,8 @@ template <int N> bool launch_xinv_regp_n(const OpArgs<float>& a, int mode, const
 
 template <int N> void xreg_attrs() {
   const int mx = 200 * 1024;
+  cudaFuncSetAttribute(k_xinv_reg<4, N, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  cudaFuncSetAttribute(k_xinv_reg<4, N, 256>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xinv_reg<0, N, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xinv_reg<1, N, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
   cudaFuncSetAttribute(k_xinv_reg<2, N, 128>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);

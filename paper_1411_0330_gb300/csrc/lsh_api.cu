@@ -754,7 +754,8 @@ template <typename T> void enqueue_cg_iteration(lsh_handle* h, PrecBufs<T>& P, c
     cudaEventRecordWithFlags(e[6], s, rf);
     h->ev_used += 7;
   }
-  h->launches += 6;
+  // the FP32 register inverse x pass adds one small reduction kernel
+  h->launches += 6 + ((sizeof(T) == 4 && (a.xreg == 1 || a.xreg == 3)) ? 1 : 0);
 }
 
 // The graph replaying `chunk` CG iterations of this wave, captured on first use.
