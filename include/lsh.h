@@ -141,11 +141,13 @@ typedef struct lsh_tune_report {
   int z_variant;  /* FP32 z pass (with Gamma) in use: 0 register FFT; TMA tiles of
                      1: 4 columns double-buffered, 2: 8 columns, 3: 8 columns double-
                      buffered, 4: 16 columns with the FFT exchange in the tile, 5: the
-                     same with two components per thread                             */
+                     same with two components per thread; 6 register FFT in blocks
+                     of 4 columns; 7 register FFT in a persistent kernel that stages
+                     the next tile's columns by asynchronous copies               */
   float xf_ms[2]; /* measured time of one launch per candidate (-1: not available)   */
   float x_ms[4];
   float y_ms[2];
-  float z_ms[7];
+  float z_ms[8];
 } lsh_tune_report;
 
 /* Bytes of device workspace lsh_setup needs for this problem. */

@@ -111,39 +111,48 @@ __device__ __forceinline__ void fd_rotate(const OpArgs<T>& a, int kx, int ky, in
   }
 }
 
-// c x c symmetric Gamma^h_k (packed upper triangle, coefficient stride cstride)
-// times the c components of one frequency, in place.
-template <typename T, int NC>
-__device__ __forceinline__ void gamma_table_apply(const T* __restrict__ G, long long cstride, long long off, C2<T>* v) {
-  C2<T> y[NC];
-#pragma unroll
-  for (int i = 0; i < NC; ++i) y[i] = mkc<T>(0, 0);
-  int coef = 0;
-#pragma unroll
-  for (int i = 0; i < NC; ++i)
-#pragma unroll
-    for (int j = i; j < NC; ++j, ++coef) {
-      const T g = G[coef * cstride + off];
-      y[i].x += g * v[j].x;
-      y[i].y += g * v[j].y;
-      if (j != i) {
-        y[j].x += g * v[i].x;
-        y[j].y += g * v[i].y;
-      }
-    }
-#pragma unroll
-  for (int i = 0; i < NC; ++i) v[i] = y[i];
+// The Gamma^h table holds, per frequency f = (z position * ny + y position) *
+// ts + kx (ts a multiple of 8), the c(c+1)/2 coefficients of the symmetric
+// c x c matrix (packed upper triangle) padded to NCOP, a multiple of 4.  It is
+// cut in blocks of 8 consecutive frequencies (f & ~7): inside a block, 16-byte
+// vector q of frequency f & 7 sits at vector q * 8 + (f & 7).  Eight threads on
+// consecutive kx then read one whole 128-byte line per vector load.
+template <int NC> struct GammaPack {
+  static constexpr int NCO = NC * (NC + 1) / 2;
+  static constexpr int NCOP = (NCO + 3) & ~3;
+};
+
+// element index of coefficient `coef` of frequency f (ncop the padded count)
+template <typename T> __host__ __device__ __forceinline__ long long gamma_elem(long long f, int coef, int ncop) {
+  constexpr int VEC = 16 / (int)sizeof(T);
+  return (f & ~7ll) * ncop + (long long)(coef / VEC) * (8 * VEC) + (f & 7) * VEC + coef % VEC;
 }
 
-// The same product split in two: the coefficients of one frequency loaded into
-// registers (so that the loads of the next frequency can be in flight while
-// this one is applied), then applied.
 template <typename T, int NC>
-__device__ __forceinline__ void gamma_coef_load(const T* __restrict__ G, long long cstride, long long off,
-                                                T* gc) {
+__device__ __forceinline__ void gamma_coef_load(const T* __restrict__ G, long long f, T* gc) {
+  constexpr int NCO = GammaPack<NC>::NCO, NCOP = GammaPack<NC>::NCOP;
+  if constexpr (sizeof(T) == 4) {
+    const float4* p = reinterpret_cast<const float4*>(G + (f & ~7ll) * NCOP) + (f & 7);
 #pragma unroll
-  for (int c = 0; c < NC * (NC + 1) / 2; ++c) gc[c] = G[c * cstride + off];
+    for (int j = 0; j < NCOP / 4; ++j) {
+      const float4 v = p[8 * j];
+      if (4 * j + 0 < NCO) gc[4 * j + 0] = v.x;
+      if (4 * j + 1 < NCO) gc[4 * j + 1] = v.y;
+      if (4 * j + 2 < NCO) gc[4 * j + 2] = v.z;
+      if (4 * j + 3 < NCO) gc[4 * j + 3] = v.w;
+    }
+  } else {
+    const double2* p = reinterpret_cast<const double2*>(G + (f & ~7ll) * NCOP) + (f & 7);
+#pragma unroll
+    for (int j = 0; j < NCOP / 2; ++j) {
+      const double2 v = p[8 * j];
+      if (2 * j + 0 < NCO) gc[2 * j + 0] = v.x;
+      if (2 * j + 1 < NCO) gc[2 * j + 1] = v.y;
+    }
+  }
 }
+
+// c x c symmetric product with coefficients already in registers, in place.
 template <typename T, int NC> __device__ __forceinline__ void gamma_coef_apply(const T* gc, C2<T>* v) {
   C2<T> y[NC];
 #pragma unroll
@@ -163,6 +172,14 @@ template <typename T, int NC> __device__ __forceinline__ void gamma_coef_apply(c
     }
 #pragma unroll
   for (int i = 0; i < NC; ++i) v[i] = y[i];
+}
+
+// Gamma^h of frequency f applied to the c components of that frequency, in place.
+template <typename T, int NC>
+__device__ __forceinline__ void gamma_table_apply(const T* __restrict__ G, long long f, C2<T>* v) {
+  T gc[GammaPack<NC>::NCO];
+  gamma_coef_load<T, NC>(G, f, gc);
+  gamma_coef_apply<T, NC>(gc, v);
 }
 
 }  // namespace lsh

@@ -35,7 +35,7 @@ template <typename T> struct OpArgs {
   const C2<T>* twz;
   const int* posx;   // frequency kx -> position after the x DIF
   C2<T>* H;          // half spectrum [S][c][nz][ny][hs] (kx < nxh used; y, z positions per kofy / kofz)
-  const T* gtab;     // Gamma^h (internal basis, scaled by 1/V): [ncoef][nz][ny][ts]
+  const T* gtab;     // Gamma^h (internal basis, scaled by 1/V): blocks of 8 frequencies, see gamma_elem
   int ncoef;
   // local term M_beta = (A_beta - A0)^{-1}, diagonal in the internal basis
   const unsigned char* phase;  // [nbatch][V]
@@ -62,7 +62,8 @@ template <typename T> struct OpArgs {
   // FP32 y and z passes through the Tensor Memory Accelerator (host pointers
   // to the maps)
   int ytma;           // 1: TMA y pass
-  int ztma;           // 0: register z pass; 1..5: the variant of launch_zgamma_tma; 6: register, 4 columns
+  int ztma;           // 0: register z pass; 1..5: the variant of launch_zgamma_tma; 6: register, 4 columns;
+                      // 7: persistent register z pass with staged prefetch
   const CUtensorMap* tmy;
   const CUtensorMap* tmz;   // z boxes of 4 columns
   const CUtensorMap* tmz8;  // z boxes of 8 columns
@@ -137,6 +138,7 @@ void launch_yfft_tma(const OpArgs<float>& a, bool inv, const SolverState* st, cu
 bool encode_y_map(CUtensorMap* out, void* H, int hs, int ny, long long planes);
 bool launch_zgamma_tma(const OpArgs<float>& a, int var, const SolverState* st, cudaStream_t s);
 bool tma_z_variant_fits(const OpArgs<float>& a, int var);
+bool launch_zgamma_regp(const OpArgs<float>& a, const SolverState* st, cudaStream_t s);
 bool encode_z_map(CUtensorMap* out, void* H, int hs, int ny, int nz, int c, long long nsys, int tz);
 void tma_prepare();
 bool launch_xinv_reg(const OpArgs<float>& a, int mode, const float* xin, float* out, SolverState* st,

@@ -216,7 +216,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs
   const int nz = a.nz, TZ = a.TZ;
   const long long zstride = (long long)a.ny * a.hs;  // distance between z planes of H
   const long long cstride = zstride * nz;
-  const long long gzs = (long long)a.ny * a.ts, gcs = gzs * nz;  // the same in the Gamma table
   C2<T>* __restrict__ Hp = a.H + (long long)s * NC * cstride + (long long)yp * a.hs + kx0;
   const int tot = NC * nz * TZ;
   for (int base = threadIdx.x; base < tot; base += 4 * blockDim.x) {
@@ -240,7 +239,6 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs
   __syncthreads();
   if (nz > 1) fft_lines<T, false>(buf, NC * TZ, a.lsz, a.pz, tw);
   // per-frequency product with Gamma^h_k
-  const T* __restrict__ G = a.gtab + (long long)yp * a.ts + kx0;
   const int ky = (a.onfly || a.fdphase) ? a.kofy[yp] : 0;
   for (int idx = threadIdx.x; idx < nz * TZ; idx += blockDim.x) {
     const int zp = fdiv(idx, TZ), t = idx - zp * TZ;
@@ -252,25 +250,7 @@ __global__ void __launch_bounds__(kThreads, MinBlocks<T>::value) k_zgamma(OpArgs
       gamma_trunc_onfly<T, NC>(a, kx0 + t, ky, a.kofz[zp], v);
     } else {
       if (a.fdphase) fd_rotate<T, NC>(a, kx0 + t, ky, a.kofz[zp], v, (T)-1);
-      // symmetric c x c table, packed upper triangle
-      C2<T> y[NC];
-#pragma unroll
-      for (int i = 0; i < NC; ++i) y[i] = mkc<T>(0, 0);
-      int coef = 0;
-#pragma unroll
-      for (int i = 0; i < NC; ++i)
-#pragma unroll
-        for (int j = i; j < NC; ++j, ++coef) {
-          const T g = G[coef * gcs + zp * gzs + t];
-          y[i].x += g * v[j].x;
-          y[i].y += g * v[j].y;
-          if (j != i) {
-            y[j].x += g * v[i].x;
-            y[j].y += g * v[i].y;
-          }
-        }
-#pragma unroll
-      for (int i = 0; i < NC; ++i) v[i] = y[i];
+      gamma_table_apply<T, NC>(a.gtab, ((long long)zp * a.ny + yp) * a.ts + kx0 + t, v);
       if (a.fdphase) fd_rotate<T, NC>(a, kx0 + t, ky, a.kofz[zp], v, (T)1);
     }
 #pragma unroll
@@ -855,7 +835,7 @@ __device__ void gamma0_acc(const GammaCtx& g, const double xi[3], double w, doub
 template <typename T>
 __global__ void k_gamma_table(OpArgs<T> a, GammaCtx g, const int* __restrict__ kofy, const int* __restrict__ kofz) {
   const long long nf = (long long)a.nz * a.ny * a.nxh;
-  const long long ntab = (long long)a.nz * a.ny * a.ts;  // per coefficient, rows padded to ts
+  const int ncop = ((g.c * (g.c + 1) / 2) + 3) & ~3;  // coefficients per frequency, padded
   for (long long f = blockIdx.x * (long long)blockDim.x + threadIdx.x; f < nf; f += (long long)gridDim.x * blockDim.x) {
     const int kx = (int)(f % a.nxh);
     const int yp = (int)((f / a.nxh) % a.ny);
@@ -951,9 +931,11 @@ __global__ void k_gamma_table(OpArgs<T> a, GammaCtx g, const int* __restrict__ k
     const double invV = 1.0 / (double)a.V;
     int coef = 0;
     T* out = const_cast<T*>(a.gtab);
+    const long long fi = ((long long)zp * a.ny + yp) * a.ts + kx;
     for (int i = 0; i < c; ++i)
       for (int j = i; j < c; ++j, ++coef)
-        out[coef * ntab + ((long long)zp * a.ny + yp) * a.ts + kx] = (T)(0.5 * (Gi[i * c + j] + Gi[j * c + i]) * invV);
+        out[gamma_elem<T>(fi, coef, ncop)] = (T)(0.5 * (Gi[i * c + j] + Gi[j * c + i]) * invV);
+    for (; coef < ncop; ++coef) out[gamma_elem<T>(fi, coef, ncop)] = (T)0;
   }
 }
 
@@ -1131,6 +1113,7 @@ template <typename T>
 void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
     if (a.ztma >= 1 && a.ztma <= 5 && launch_zgamma_tma(a, a.ztma, st, s)) return;
+    if (a.ztma == 7 && launch_zgamma_regp(a, st, s)) return;
   }
   if (a.zreg) {
     launch_zgamma_reg<T>(a, st, s, (sizeof(T) == 4 && a.ztma == 6) ? 4 : 0);

@@ -14,6 +14,7 @@
 #include "internal.h"
 #include "regfft.cuh"
 #include "gamma_onfly.cuh"
+#include "tma.cuh"
 
 namespace lsh {
 
@@ -84,6 +85,75 @@ template <typename T, int NC, int N, int TZV = 0> struct ZCfg {
   static constexpr int BUF = EXN > GBN ? EXN : GBN;
 };
 
+// Gamma^h_k on the NC components of the N x TZ frequencies of a block's tile,
+// in place in buf[kz KS + comp TZ + li]; line_yp/line_kx give each line's y
+// position (-1: no line) and kx.  PIPE: a thread loads the table coefficients
+// of its next frequency while it applies the current ones.
+template <typename T, int NC, int N, int TZ, int KS, bool PIPE = true>
+__device__ __forceinline__ void z_gamma_block(const OpArgs<T>& a, C2<T>* buf, const int* line_yp,
+                                              const int* line_kx) {
+  if (a.onfly) {
+    for (int item = threadIdx.x; item < N * TZ; item += blockDim.x) {
+      const int kz = item / TZ, li = item - kz * TZ;
+      const int lyp = line_yp[li];
+      if (lyp < 0) continue;
+      C2<T> g[NC];
+#pragma unroll
+      for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
+      gamma_trunc_onfly<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g);
+#pragma unroll
+      for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
+    }
+  } else if constexpr (!PIPE) {
+    for (int item = threadIdx.x; item < N * TZ; item += blockDim.x) {
+      const int kz = item / TZ, li = item - kz * TZ;
+      const int lyp = line_yp[li];
+      if (lyp < 0) continue;
+      C2<T> g[NC];
+#pragma unroll
+      for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
+      if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g, (T)-1);
+      gamma_table_apply<T, NC>(a.gtab, ((long long)kz * a.ny + lyp) * a.ts + line_kx[li], g);
+      if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g, (T)1);
+#pragma unroll
+      for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
+    }
+  } else {
+    // tabulated Gamma^h_k: the coefficients of a thread's next frequency are
+    // loaded while the current one is applied
+    constexpr int NCO = NC * (NC + 1) / 2;
+    auto off = [&](int item) {  // frequency index in the table
+      const int kz = item / TZ, li = item - kz * TZ;
+      return ((long long)kz * a.ny + line_yp[li]) * a.ts + line_kx[li];
+    };
+    auto ok = [&](int item) { return item < N * TZ && line_yp[item % TZ] >= 0; };
+    T gc[NCO], gn[NCO];
+    int item = threadIdx.x;
+    bool have = ok(item);
+    if (have) gamma_coef_load<T, NC>(a.gtab, off(item), gc);
+#pragma unroll 1
+    for (; item < N * TZ; item += blockDim.x) {
+      const int nxt = item + blockDim.x;
+      const bool hn = ok(nxt);
+      if (hn) gamma_coef_load<T, NC>(a.gtab, off(nxt), gn);
+      if (have) {
+        const int kz = item / TZ, li = item - kz * TZ;
+        C2<T> g[NC];
+#pragma unroll
+        for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
+        if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[line_yp[li]], kz, g, (T)-1);
+        gamma_coef_apply<T, NC>(gc, g);
+        if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[line_yp[li]], kz, g, (T)1);
+#pragma unroll
+        for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
+      }
+#pragma unroll
+      for (int c = 0; c < NCO; ++c) gc[c] = gn[c];
+      have = hn;
+    }
+  }
+}
+
 template <typename T, int NC, int N, int TZV>
 __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS, ZCfg<T, NC, N, TZV>::THREADS <= 192 ? 4 : 2)
     k_zgamma_reg(OpArgs<T> a, const SolverState* __restrict__ st, int nrt, int nreg) {
@@ -121,7 +191,6 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS, ZCfg<T, NC, N, T
   const bool valid = yp >= 0;
   const long long zstride = (long long)a.ny * a.hs;  // z planes of H
   const long long cstride = zstride * N;
-  const long long gzs = (long long)a.ny * a.ts, gcs = gzs * N;  // the same in the Gamma table
   C2<T>* __restrict__ Hl = a.H + ((long long)s * NC + comp) * cstride + (valid ? (long long)yp * a.hs + kx : 0);
   C2<T>* exl = buf + (comp * TZ + i) * RL::LS;
   C2<T> v[R1];
@@ -135,52 +204,7 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS, ZCfg<T, NC, N, T
 #pragma unroll
   for (int m = 0; m < R1; ++m) buf[RL::freq(t, m) * KS + comp * TZ + i] = v[m];
   __syncthreads();
-  if (a.onfly) {
-    for (int item = threadIdx.x; item < N * TZ; item += blockDim.x) {
-      const int kz = item / TZ, li = item - kz * TZ;
-      const int lyp = line_yp[li];
-      if (lyp < 0) continue;
-      C2<T> g[NC];
-#pragma unroll
-      for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
-      gamma_trunc_onfly<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g);
-#pragma unroll
-      for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
-    }
-  } else {
-    // tabulated Gamma^h_k: the coefficients of a thread's next frequency are
-    // loaded while the current one is applied
-    constexpr int NCO = NC * (NC + 1) / 2;
-    auto off = [&](int item) {
-      const int kz = item / TZ, li = item - kz * TZ;
-      return kz * gzs + (long long)line_yp[li] * a.ts + line_kx[li];
-    };
-    auto ok = [&](int item) { return item < N * TZ && line_yp[item % TZ] >= 0; };
-    T gc[NCO], gn[NCO];
-    int item = threadIdx.x;
-    bool have = ok(item);
-    if (have) gamma_coef_load<T, NC>(a.gtab, gcs, off(item), gc);
-#pragma unroll 1
-    for (; item < N * TZ; item += blockDim.x) {
-      const int nxt = item + blockDim.x;
-      const bool hn = ok(nxt);
-      if (hn) gamma_coef_load<T, NC>(a.gtab, gcs, off(nxt), gn);
-      if (have) {
-        const int kz = item / TZ, li = item - kz * TZ;
-        C2<T> g[NC];
-#pragma unroll
-        for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
-        if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[line_yp[li]], kz, g, (T)-1);
-        gamma_coef_apply<T, NC>(gc, g);
-        if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[line_yp[li]], kz, g, (T)1);
-#pragma unroll
-        for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
-      }
-#pragma unroll
-      for (int c = 0; c < NCO; ++c) gc[c] = gn[c];
-      have = hn;
-    }
-  }
+  z_gamma_block<T, NC, N, TZ, KS>(a, buf, line_yp, line_kx);
   __syncthreads();
 #pragma unroll
   for (int m = 0; m < R1; ++m) v[m] = buf[RL::freq(t, m) * KS + comp * TZ + i];
@@ -192,6 +216,131 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS, ZCfg<T, NC, N, T
 #pragma unroll
     for (int j = 0; j < R1; ++j) Hl[(t + P * j) * zstride] = v[j];
   }
+}
+
+// ------------------------------------------------------------------ z pass + Gamma, persistent
+// FP32 variant of k_zgamma_reg whose blocks stay resident and walk the tiles
+// (system s, TZ lines) with the grid's stride.  The columns of the next tile
+// are copied into a staging area of shared memory by per-thread asynchronous
+// copies issued right after the current tile has left it, so the strided reads
+// along z run under the FFTs and the Gamma^h product of the current tile.
+template <int NC, int N> struct ZPCfg {
+  typedef ZCfg<float, NC, N, 0> ZC;
+  static constexpr int TZ = ZC::TZ, THREADS = ZC::THREADS;
+  static constexpr int STAGE = N * NC * TZ;  // complex values of one tile
+  static constexpr size_t SMEM = sizeof(float2) * (STAGE + N + ZC::BUF);
+  static constexpr bool FITS = SMEM <= 226 * 1024;
+};
+
+template <int NC, int N>
+__global__ void __launch_bounds__(ZPCfg<NC, N>::THREADS, ZPCfg<NC, N>::THREADS <= 192 ? 4 : 2)
+    k_zgamma_regp(OpArgs<float> a, const SolverState* __restrict__ st, int nrt, int nreg, int ntiles) {
+  typedef RegLine<float, N> RL;
+  typedef ZCfg<float, NC, N, 0> ZC;
+  constexpr int TZ = ZC::TZ, P = RL::P, R1 = RL::R1, KS = ZC::KS, THREADS = ZC::THREADS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* stage = reinterpret_cast<float2*>(smem_raw);  // [z][comp][li]
+  float2* tw = stage + ZPCfg<NC, N>::STAGE;
+  float2* buf = tw + N;
+  __shared__ int line_yp[TZ], line_kx[TZ];
+  for (int u = threadIdx.x; u < N; u += THREADS) tw[u] = a.twz[u];
+  const int S = a.S, nleft = a.nxh - nreg, nregt = a.ny * nrt;
+  const int total = S * ntiles;  // below 2^31 (checked by the launcher)
+  const int zstride = a.ny * a.hs, cstride = zstride * N;
+  // line li of tile `tile`: y position (-1: past the last column) and kx
+  auto line = [&](int tile, int li, int& yp, int& kx) {
+    if (tile < nregt) {
+      yp = tile / nrt;
+      kx = (tile - yp * nrt) * TZ + li;
+    } else {
+      const int l = (tile - nregt) * TZ + li;
+      yp = -1;
+      kx = 0;
+      if (l < a.ny * nleft) {
+        yp = l / nleft;
+        kx = nreg + (l - yp * nleft);
+      }
+    }
+  };
+  auto next_live = [&](int tl) {
+    while (tl < total && st != nullptr && st[tl % S].done) tl += gridDim.x;
+    return tl;
+  };
+  // stage the columns of tile tl; its Gamma^h rows go to L2 meanwhile
+  auto prefetch = [&](int tl) {
+    const int s = tl % S, tile = tl / S;
+    const float2* Hs = a.H + (long long)s * NC * cstride;
+    if (tile < nregt) {
+      // TZ consecutive columns: rows of TZ / 2 aligned 16-byte pieces
+      constexpr int CH = TZ / 2, NCOP = GammaPack<NC>::NCOP;
+      const int yp = tile / nrt, kx0 = (tile - yp * nrt) * TZ;
+      const float2* src = Hs + (long long)yp * a.hs + kx0;
+      for (int q = threadIdx.x; q < N * NC * CH; q += THREADS) {
+        const int row = q / CH, piece = q - row * CH;  // row = z NC + comp
+        const int z = row / NC, comp = row - z * NC;
+        cp_async16(stage + row * TZ + 2 * piece, src + (long long)comp * cstride + (long long)z * zstride + 2 * piece);
+      }
+      if (!a.onfly)
+        for (int kz = threadIdx.x; kz < N; kz += THREADS)
+          bulk_prefetch_l2(a.gtab + (((long long)kz * a.ny + yp) * a.ts + kx0) * NCOP,
+                           (uint32_t)(sizeof(float) * TZ * NCOP));
+    } else {
+      for (int q = threadIdx.x; q < N * NC * TZ; q += THREADS) {
+        const int row = q / TZ, li = q - row * TZ;
+        const int z = row / NC, comp = row - z * NC;
+        int yp, kx;
+        line(tile, li, yp, kx);
+        if (yp >= 0)
+          cp_async8(stage + q, Hs + (long long)comp * cstride + (long long)z * zstride + (long long)yp * a.hs + kx);
+      }
+    }
+    cp_async_commit();
+  };
+  const int i = threadIdx.x % TZ, comp = (threadIdx.x / TZ) % NC, t = threadIdx.x / (TZ * NC);
+  float2* exl = buf + (comp * TZ + i) * RL::LS;
+  int cur = next_live(blockIdx.x);
+  if (cur < total) prefetch(cur);
+  while (cur < total) {
+    const int nxt = next_live(cur + gridDim.x);
+    const int s = cur % S, tile = cur / S;
+    cp_async_wait_all();
+    __syncthreads();  // the tile is staged; the previous tile is done with buf and the line table
+    if (threadIdx.x < TZ) {
+      int yp, kx;
+      line(tile, threadIdx.x, yp, kx);
+      line_yp[threadIdx.x] = yp;
+      line_kx[threadIdx.x] = kx;
+    }
+    int yp, kx;
+    line(tile, i, yp, kx);
+    const bool valid = yp >= 0;
+    float2 v[R1];
+#pragma unroll
+    for (int j = 0; j < R1; ++j) v[j] = valid ? stage[((t + P * j) * NC + comp) * TZ + i] : mkc<float>(0, 0);
+    RL::fwd_a(v, t, tw, exl);
+    __syncthreads();  // every thread has read the staging area
+    if (nxt < total) prefetch(nxt);
+    RL::fwd_b(v, t, tw, exl);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < R1; ++m) buf[RL::freq(t, m) * KS + comp * TZ + i] = v[m];
+    __syncthreads();
+    z_gamma_block<float, NC, N, TZ, KS, false>(a, buf, line_yp, line_kx);
+    __syncthreads();
+#pragma unroll
+    for (int m = 0; m < R1; ++m) v[m] = buf[RL::freq(t, m) * KS + comp * TZ + i];
+    __syncthreads();
+    RL::inv_a(v, t, tw, exl);
+    __syncthreads();
+    RL::inv_b(v, t, tw, exl);
+    if (valid) {
+      float2* Hl = a.H + ((long long)s * NC + comp) * cstride + (long long)yp * a.hs + kx;
+#pragma unroll
+      for (int j = 0; j < R1; ++j) Hl[(long long)(t + P * j) * zstride] = v[j];
+    }
+    cur = nxt;
+  }
+  cp_async_wait_all();
 }
 
 // ------------------------------------------------------------------ launchers
@@ -252,6 +401,83 @@ template <typename T> void launch_zgamma_reg(const OpArgs<T>& a, const SolverSta
   else launch_z_tz<T, 0>(a, st, s);
 }
 
+int multiprocessors() {
+  static int n = []() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      v = 1;
+    }
+    return v;
+  }();
+  return n;
+}
+
+template <int NC, int N> int zp_blocks_per_sm() {
+  typedef ZPCfg<NC, N> ZP;
+  static int n = []() {
+    int v = 0;
+    if constexpr (ZP::FITS) {
+      cudaFuncSetAttribute(k_zgamma_regp<NC, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZP::SMEM);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_zgamma_regp<NC, N>, ZP::THREADS, ZP::SMEM) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        v = 0;
+      }
+    }
+    return v;
+  }();
+  return n;
+}
+
+template <int NC, int N> bool launch_zp_n(const OpArgs<float>& a, const SolverState* st, cudaStream_t s) {
+  typedef ZPCfg<NC, N> ZP;
+  if constexpr (!ZP::FITS) {
+    return false;
+  } else {
+    const int bpsm = zp_blocks_per_sm<NC, N>();
+    if (bpsm < 1 || a.S < 1) return bpsm >= 1;
+    const int nrt = a.nxh / ZP::TZ, nreg = nrt * ZP::TZ;
+    const int ntiles = a.ny * nrt + (a.ny * (a.nxh - nreg) + ZP::TZ - 1) / ZP::TZ;
+    const long long total = (long long)a.S * ntiles;
+    const long long cstride = (long long)a.ny * a.hs * N;
+    if (total + (long long)multiprocessors() * bpsm >= (1ll << 31) || cstride >= (1ll << 31)) return false;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(total, (long long)multiprocessors() * bpsm));
+    k_zgamma_regp<NC, N><<<grid, ZP::THREADS, ZP::SMEM, s>>>(a, st, nrt, nreg, ntiles);
+    return true;
+  }
+}
+
+template <int NC> bool launch_zp_nc(const OpArgs<float>& a, const SolverState* st, cudaStream_t s) {
+  switch (a.nz) {
+    case 16: return launch_zp_n<NC, 16>(a, st, s);
+    case 32: return launch_zp_n<NC, 32>(a, st, s);
+    case 64: return launch_zp_n<NC, 64>(a, st, s);
+    case 128: return launch_zp_n<NC, 128>(a, st, s);
+    case 256: return launch_zp_n<NC, 256>(a, st, s);
+    default: return false;
+  }
+}
+
+// Persistent FP32 z pass with staged prefetch; false (nothing launched) when
+// the length has no register plan or the kernel does not fit.  With a.S = 0
+// it only answers whether it would launch.
+bool launch_zgamma_regp(const OpArgs<float>& a, const SolverState* st, cudaStream_t s) {
+  if (a.c == 6) return launch_zp_nc<6>(a, st, s);
+  if (a.c == 3) return launch_zp_nc<3>(a, st, s);
+  if (a.c == 2) return launch_zp_nc<2>(a, st, s);
+  return false;
+}
+
+template <int NC> void zp_prepare() {
+  zp_blocks_per_sm<NC, 16>();
+  zp_blocks_per_sm<NC, 32>();
+  zp_blocks_per_sm<NC, 64>();
+  zp_blocks_per_sm<NC, 128>();
+  zp_blocks_per_sm<NC, 256>();
+}
+
 // dynamic shared memory of one instantiation (static shared memory comes on top
 // of it, so the attribute is set to exactly what the launch asks for)
 template <typename T, int NC, int N> void attr_z_n() {
@@ -286,6 +512,11 @@ template <typename T> void set_smem_attrs_reg() {
   attr_z_nc<T, 2>();
   attr_z_nc<T, 3>();
   attr_z_nc<T, 6>();
+  if constexpr (sizeof(T) == 4) {
+    zp_prepare<2>();
+    zp_prepare<3>();
+    zp_prepare<6>();
+  }
 }
 template void set_smem_attrs_reg<double>();
 template void set_smem_attrs_reg<float>();

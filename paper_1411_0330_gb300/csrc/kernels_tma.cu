@@ -179,7 +179,6 @@ __global__ void __launch_bounds__(ZTma<NC, N, TZ, NB>::THREADS, ZTma<NC, N, TZ, 
   const int i = threadIdx.x % TZ, t = (threadIdx.x / TZ) % P, comp = threadIdx.x / (TZ * P);
   float2* exl = ex + (comp * TZ + i) * ZC::LS;
   const int S = a.S;
-  const long long gzs = (long long)a.ny * a.ts, gcs = gzs * N;  // Gamma table strides
   auto live = [&](long long tl) {
     if (tl >= ntiles) return false;
     if (st == nullptr) return true;
@@ -243,7 +242,7 @@ __global__ void __launch_bounds__(ZTma<NC, N, TZ, NB>::THREADS, ZTma<NC, N, TZ, 
           gamma_trunc_onfly<float, NC>(a, kx, ky, kz, g);
         } else {
           if (a.fdphase) fd_rotate<float, NC>(a, kx, ky, kz, g, -1.f);
-          gamma_table_apply<float, NC>(a.gtab, gcs, kz * gzs + (long long)yp * a.ts + kx, g);
+          gamma_table_apply<float, NC>(a.gtab, ((long long)kz * a.ny + yp) * a.ts + kx, g);
           if (a.fdphase) fd_rotate<float, NC>(a, kx, ky, kz, g, 1.f);
         }
 #pragma unroll
@@ -323,7 +322,6 @@ __global__ void __launch_bounds__(ZTma16<NC, N, CPT>::THREADS, 1)
   __syncthreads();
   const int i = threadIdx.x % TZ, t = (threadIdx.x / TZ) % P, cg = threadIdx.x / (TZ * P);
   const int S = a.S;
-  const long long gzs = (long long)a.ny * a.ts, gcs = gzs * N;
   auto live = [&](long long tl) {
     if (tl >= ntiles) return false;
     if (st == nullptr) return true;
@@ -390,7 +388,7 @@ __global__ void __launch_bounds__(ZTma16<NC, N, CPT>::THREADS, 1)
           gamma_trunc_onfly<float, NC>(a, kx, ky, kz, g);
         } else {
           if (a.fdphase) fd_rotate<float, NC>(a, kx, ky, kz, g, -1.f);
-          gamma_table_apply<float, NC>(a.gtab, gcs, kz * gzs + (long long)yp * a.ts + kx, g);
+          gamma_table_apply<float, NC>(a.gtab, ((long long)kz * a.ny + yp) * a.ts + kx, g);
           if (a.fdphase) fd_rotate<float, NC>(a, kx, ky, kz, g, 1.f);
         }
 #pragma unroll

@@ -388,7 +388,7 @@ Layout make_layout(const Derived& d) {
   };
   const int S = d.Smax;
   const long long n = (long long)d.c * d.V;  // elements per system
-  const long long nf = (long long)d.nz * d.ny * d.ts;    // Gamma table per coefficient (padded rows)
+  const long long nf = (long long)d.nz * d.ny * d.ts;    // Gamma table frequencies (rows padded to ts)
   const long long nfh = (long long)d.nz * d.ny * d.hs;  // half spectrum per component
   LaunchCfg Ld = make_cfg<double>(d), Lf = make_cfg<float>(d);
   long long np = std::max<long long>({(long long)S * Ld.grid_x, (long long)S * Lf.grid_x, (long long)S * Ld.ew_per_sys,
@@ -428,11 +428,12 @@ Layout make_layout(const Derived& d) {
   l.off_wb = take(l.minres ? sizeof(double) * (size_t)(S * n) : 0);
   l.off_ms = take(sizeof(MinresScalars) * (size_t)S);
   l.off_Hd = take(sizeof(double2) * (size_t)(S * d.c * nfh));
-  l.off_gd = take(sizeof(double) * (size_t)(d.ncoef * nf));
+  const int ncop = (d.ncoef + 3) & ~3;  // Gamma coefficients per frequency, padded
+  l.off_gd = take(sizeof(double) * (size_t)(ncop * nf));
   if (mixed) {
     for (int i = 0; i < 4; ++i) l.off_ff[i] = take(sizeof(float) * (size_t)(S * n));
     l.off_Hf = take(sizeof(float2) * (size_t)(S * d.c * nfh));
-    l.off_gf = take(sizeof(float) * (size_t)(d.ncoef * nf));
+    l.off_gf = take(sizeof(float) * (size_t)(ncop * nf));
   }
   l.total = o;
   return l;
@@ -1508,7 +1509,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   r.z_variant = h->pf.a.ztma;
   for (int k = 0; k < 4; ++k) r.x_ms[k] = -1.f;
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
-  for (int k = 0; k < 7; ++k) r.z_ms[k] = -1.f;
+  for (int k = 0; k < 8; ++k) r.z_ms[k] = -1.f;
   const Derived& d = h->d;
   if (d.precision == LSH_MIXED) {
     PrecBufs<float>& P = h->pf;
@@ -1585,15 +1586,17 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       r.y_variant = (r.y_ms[1] > 0.f && (r.y_ms[0] < 0.f || r.y_ms[1] < r.y_ms[0])) ? 1 : 0;
       a.ytma = r.y_variant;
     }
-    if (a.zreg && P.ztma_ok) {
+    if (a.zreg) {
       int best = 0;
-      for (int v = 0; v < 7; ++v) {
+      for (int v = 0; v < 8; ++v) {
+        if (v >= 1 && v <= 5 && !P.ztma_ok) continue;  // TMA tiles need the tensor map
         a.ztma = v;
         r.z_ms[v] = timeit([&]() {
           if (v == 0 || v == 6) {
             launch_zgamma<float>(a, P.L, nullptr, s);
             return true;
           }
+          if (v == 7) return launch_zgamma_regp(a, nullptr, s);
           return launch_zgamma_tma(a, v, nullptr, s);
         });
         if (r.z_ms[v] > 0.f && (r.z_ms[best] < 0.f || r.z_ms[v] < r.z_ms[best])) best = v;
@@ -1619,7 +1622,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
 lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
   if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 3 || y_variant < 0 || y_variant > 1 ||
-      z_variant < 0 || z_variant > 6)
+      z_variant < 0 || z_variant > 7)
     return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;
   if (h->d.precision != LSH_MIXED)
@@ -1627,7 +1630,12 @@ lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_
   if (x_variant >= 1 && !xinv_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (xf_variant == 1 && !xfwd_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;
-  if (z_variant == 6 && !P.a.zreg) return LSH_ERR_UNSUPPORTED;
+  if ((z_variant == 6 || z_variant == 7) && !P.a.zreg) return LSH_ERR_UNSUPPORTED;
+  if (z_variant == 7) {
+    OpArgs<float> a = P.a;
+    a.S = 0;
+    if (!launch_zgamma_regp(a, nullptr, 0)) return LSH_ERR_UNSUPPORTED;
+  }
   if (z_variant >= 1 && z_variant <= 5 && !P.ztma_ok) return LSH_ERR_UNSUPPORTED;
   if (z_variant >= 1 && z_variant <= 5) {
     // the variant must have a kernel for this length and component count

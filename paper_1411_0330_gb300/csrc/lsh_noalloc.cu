@@ -250,7 +250,8 @@ extern "C" lsh_status lsh_apply_noalloc(const lsh_problem* pr, const double* x, 
   const size_t o_p = o; o = up(o + (el ? sizeof(double) * (size_t)(c * V) : 0));
   const size_t o_q = o; o = up(o + (el ? sizeof(double) * (size_t)(c * V) : 0));
   const size_t o_H = o; o = up(o + sizeof(double2) * (size_t)(c * nf));
-  const size_t o_g = o; o = up(o + sizeof(double) * (size_t)(ncoef * nf));
+  const long long ntf = (long long)nz * ny * ((nxh + 7) & ~7);  // Gamma table rows padded to 8
+  const size_t o_g = o; o = up(o + sizeof(double) * (size_t)(((ncoef + 3) & ~3) * ntf));
   if (o > LSH_NOALLOC_SCRATCH_BYTES) return LSH_ERR_UNSUPPORTED_SIZE;
 
   void* base_v = nullptr;
@@ -265,7 +266,7 @@ extern "C" lsh_status lsh_apply_noalloc(const lsh_problem* pr, const double* x, 
   a.nz = nz;
   a.nxh = nxh;
   a.hs = nxh;
-  a.ts = nxh;
+  a.ts = (nxh + 7) & ~7;
   a.fdphase = pr->green == LSH_GREEN_FD ? 1 : 0;
   a.kofy = (const int*)(base + o_kofy);  // frequency of each y / z position (phase rotations)
   a.kofz = (const int*)(base + o_kofz);

@@ -442,7 +442,7 @@ def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkey
     h_reg = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=1, precision=lsh.MIXED)
     y_reg = h_reg.apply(xt)
     assert rel(y_reg.cpu().numpy(), oracle.apply(P, x)) < 2e-5
-    for zv in range(7):
+    for zv in range(8):
         try:
             h_tma.set_variants(0, 0, 1, zv)
         except lsh.LSHError as e:
@@ -460,12 +460,13 @@ def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkey
         y_x = h_tma.apply(xt)
         assert rel(y_x.cpu().numpy(), oracle.apply(P, x)) < 2e-5, (xf, xv)
     rep = h_tma.autotune()
-    assert rep["z_variant"] in range(7) and rep["y_variant"] in (0, 1) and rep["x_variant"] in (0, 1, 2, 3)
+    assert rep["z_variant"] in range(8) and rep["y_variant"] in (0, 1) and rep["x_variant"] in (0, 1, 2, 3)
     assert rep["xf_variant"] in (0, 1)
     assert rel(h_tma.apply(xt).cpu().numpy(), oracle.apply(P, x)) < 2e-5
 
 
-@pytest.mark.parametrize("variants", [(0, 0, 0, 0), (1, 1, 1, 0), (1, 1, 1, 4), (0, 1, 0, 1), (1, 2, 1, 0)])
+@pytest.mark.parametrize("variants", [(0, 0, 0, 0), (1, 1, 1, 0), (1, 1, 1, 4), (0, 1, 0, 1), (1, 2, 1, 0),
+                                      (1, 3, 1, 7)])
 def test_mixed_solver_with_each_kernel_variant(variants):
     """The mixed-precision solver (FP32 CG on the forced x / y / z kernel variants,
     FP64 refinement) reaches the oracle's C* to the mixed tolerance whichever
@@ -481,6 +482,35 @@ def test_mixed_solver_with_each_kernel_variant(variants):
     Ao, _ = oracle.effective(oracle.Problem(ph, EL, physics=1, green=1), tol=1e-13)
     assert rel(A, Ao) < 1e-8, rel(A, Ao)
     assert all(i["status"] == 0 for i in infos)
+
+
+@pytest.mark.parametrize("shape,physics,green", [((16, 12, 10), 1, 1), ((64, 12, 18), 1, 0), ((128, 8, 30), 1, 1),
+                                                 ((16, 20, 14), 0, 1), ((256, 6, 32), 0, 2), ((32, 4, 40), 0, 0),
+                                                 ((64, 10, 6), 0, 2)])
+def test_persistent_z_pass_matches_register_z_pass(shape, physics, green):
+    """The persistent FP32 z pass (tiles walked with the grid's stride, the next
+    tile's columns staged by asynchronous copies, Gamma^h rows prefetched to L2)
+    equals the one-tile-per-block register pass bit for bit: truncated (on the fly),
+    filtered and (conductivity) finite-difference Gamma^h, three microstructures
+    (systems) per launch, ragged last tiles."""
+    rng = np.random.default_rng(sum(shape) + 7 * green)
+    if physics == 1:
+        ph = (rng.random((3,) + shape) < 0.35).astype(np.uint8)
+        mods = EL
+    else:
+        ph = rng.integers(0, 3, (3,) + shape).astype(np.uint8)
+        mods = _scalar_mods(3, 4)
+    Ps = [oracle.Problem(ph[k], mods, physics=physics, green=green) for k in range(3)]
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=green, precision=lsh.MIXED, batch=True)
+    x = rng.standard_normal((3,) + Ps[0].field_shape)
+    xt = torch.from_numpy(x).float().cuda()
+    h.set_variants(0, 0, 0, 0)
+    y0 = h.apply(xt)
+    h.set_variants(0, 0, 0, 7)
+    y7 = h.apply(xt)
+    assert torch.equal(y7, y0)
+    for k in range(3):
+        assert rel(y7[k].cpu().numpy(), oracle.apply(Ps[k], x[k])) < 2e-5
 
 
 @pytest.mark.parametrize("shape,physics", [((16, 256, 32), 1), ((256, 16, 16), 1), ((8, 256, 256), 0)])
