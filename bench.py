@@ -152,8 +152,8 @@ def pass_flops(kind, V, c, nx, ny, nz, nxh):
 # systems of the 128^3 workload, from the ncu captures summarised in
 # profiles/fp32_passes_128cube_six_systems.md (filtered operator); to be
 # retaken whenever one of these kernels changes.
-NCU_TRAFFIC_FP32 = {"x_forward": 1770.9e6, "y_forward": 588.4e6, "z_gamma": 873.5e6, "y_inverse": 587.6e6,
-                    "x_inverse_local": 901.6e6, "cg_update": 862.9e6}
+NCU_TRAFFIC_FP32 = {"x_forward": 1770.9e6, "y_forward": 588.4e6, "z_gamma": 829.8e6, "y_inverse": 587.6e6,
+                    "x_inverse_local": 902.0e6, "cg_update": 862.9e6}
 
 
 def load_peaks():
@@ -223,7 +223,7 @@ def profile_case(kind):
     h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.ELASTIC, green=lsh.FILTERED,
                    precision=lsh.MIXED if kind == "mixed" else lsh.FP64)
     if kind == "mixed":
-        h.set_variants(1, 1, 1, 0)
+        h.set_variants(1, 3, 1, 0)
     _, infos = h.effective(tol=1e-30, maxit=4, raise_on_fail=False)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": kind, "info": infos[0]}))
@@ -548,6 +548,63 @@ def run_convergence(args, grids=(16, 32, 64, 128, 256), fine=512):
 
 
 # ----------------------------------------------------------------- main arm
+def run_cufft(args, reps=20):
+    """Timed comparison with the vendor FFT: cuFFT (through torch.fft) forward R2C
+    and inverse C2R of the 6 load systems x 6 components of the 128^3 FP32 field
+    (the transforms alone: no Gamma^h, local term, projection or CG vector work),
+    against this library's five FP32 operator passes at the same size, which do
+    all of that, as the inner CG of the mixed solver runs them."""
+    import torch
+    from paper_1411_0330_gb300 import lsh
+    torch.cuda.set_device(0)
+    ph, mods, _ = workload()
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
+    tune = h.autotune()
+    h.effective(tol=1e-30, maxit=8, raise_on_fail=False)  # warm-up, graph capture
+    h.profile_read(reset=True)
+    h.profile_enable(True)
+    h.effective(tol=1e-30, maxit=40, raise_on_fail=False)
+    pf = h.profile_read(reset=True)
+    h.profile_enable(False)
+    ours = {k: pf["pass_ms"][k] / max(pf["pass_launches"][k], 1) for k in lsh.PASS_NAMES}
+    h.close()
+    del h
+    torch.cuda.empty_cache()
+    x = torch.randn(6, 6, N, N, N, device="cuda", dtype=torch.float32)
+    dims = (-3, -2, -1)
+    X = torch.fft.rfftn(x, dim=dims)
+    y = torch.fft.irfftn(X, s=(N, N, N), dim=dims)
+    err = float((y - x).abs().max() / x.abs().max())
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    for _ in range(3):
+        torch.fft.rfftn(x, dim=dims, out=X)
+        torch.fft.irfftn(X, s=(N, N, N), dim=dims, out=y)
+    torch.cuda.synchronize()
+    fwd = inv = 0.0
+    for _ in range(reps):  # 302 MB field and 307 MB spectrum: larger than L2
+        e[0].record()
+        torch.fft.rfftn(x, dim=dims, out=X)
+        e[1].record()
+        torch.fft.irfftn(X, s=(N, N, N), dim=dims, out=y)
+        e[2].record()
+        torch.cuda.synchronize()
+        fwd += e[0].elapsed_time(e[1])
+        inv += e[1].elapsed_time(e[2])
+    fwd /= reps
+    inv /= reps
+    fft_passes = ["x_forward", "y_forward", "z_gamma", "y_inverse", "x_inverse_local"]
+    ours_fft = sum(ours[k] for k in fft_passes)
+    line = {"workload": "cufft_comparison",
+            "config": {"grid": [N, N, N], "fields": "6 load systems x 6 components, FP32",
+                       "variants": {k: tune[k] for k in ("xf_variant", "x_variant", "y_variant", "z_variant")}},
+            "cufft_ms": {"rfftn": fwd, "irfftn": inv, "sum": fwd + inv, "round_trip_max_rel_err": err},
+            "lsh_ms": {"passes": ours, "five_operator_passes": ours_fft,
+                       "with_cg_update": ours_fft + ours["cg_update"]},
+            "ratio_cufft_over_lsh_operator": (fwd + inv) / ours_fft}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -559,11 +616,12 @@ def main():
     ap.add_argument("--concurrent", action="store_true",
                     help="solve the filtered and truncated handles together, one stream each")
     ap.add_argument("--workload", default="spheres128",
-                    choices=["spheres128", "batch64", "contrast256", "gradient128", "convergence"],
+                    choices=["spheres128", "batch64", "contrast256", "gradient128", "convergence", "cufft"],
                     help="spheres128: the 128^3 sphere packing (default); batch64: 64 microstructures "
                          "of uneven grids solved together; contrast256: 256^3 mixed vs FP64 at contrasts "
                          "10/100/1000; gradient128: adjoint gradient of C* and its finite-difference check; "
-                         "convergence: C* against the grid, centre rule vs sub-voxel averaging")
+                         "convergence: C* against the grid, centre rule vs sub-voxel averaging; cufft: "
+                         "the FP32 operator passes against cuFFT R2C + C2R alone at 128^3")
     ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
                     help="small case for ncu: 4 CG iterations of one 128^3 filtered solve, then exit")
     args = ap.parse_args()
@@ -583,6 +641,8 @@ def main():
         return run_gradient128(args)
     if args.workload == "convergence":
         return run_convergence(args)
+    if args.workload == "cufft":
+        return run_cufft(args)
 
     import torch
     import torch.distributed as dist
