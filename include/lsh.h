@@ -62,7 +62,12 @@ enum { LSH_GREEN_TRUNCATED = 0, LSH_GREEN_FILTERED = 1, LSH_GREEN_FD = 2 };
  * products and CG scalars in double, wrapped in iterative refinement whose
  * residual b - K x is computed with the double-precision operator. */
 enum { LSH_FP64 = 0, LSH_MIXED = 1 };
-enum { LSH_F64 = 0, LSH_F32 = 1 }; /* element type of fields passed to lsh_apply */
+/* element type of fields passed to lsh_apply.  LSH_F64_DF: FP64 fields, the
+ * operator evaluated in double-float arithmetic (pairs of FP32 values, 48
+ * significant bits) on the FP32 pipes -- the arithmetic of the mixed solver's
+ * refinement residual; LSH_MIXED handles on 3D grids of lengths 16..256
+ * (powers of two), truncated or filtered operator, 3 or 6 components. */
+enum { LSH_F64 = 0, LSH_F32 = 1, LSH_F64_DF = 2 };
 /* AUTO: CG when every active phase has A_phase - A0 of one sign (K definite),
  * MINRES (Paige-Saunders, FP64) when the signs differ (K indefinite, e.g. the
  * reference k0 = (k_min + k_max)/2); CG: always CG (with a breakdown check);

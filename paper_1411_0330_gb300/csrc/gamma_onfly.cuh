@@ -4,6 +4,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "df.cuh"
 #include "internal.h"
 
 namespace lsh {
@@ -131,7 +132,16 @@ template <typename T> __host__ __device__ __forceinline__ long long gamma_elem(l
 template <typename T, int NC>
 __device__ __forceinline__ void gamma_coef_load(const T* __restrict__ G, long long f, T* gc) {
   constexpr int NCO = GammaPack<NC>::NCO, NCOP = GammaPack<NC>::NCOP;
-  if constexpr (sizeof(T) == 4) {
+  if constexpr (is_df<T>::value) {
+    // two double-float coefficients per 16-byte vector
+    const float4* p = reinterpret_cast<const float4*>(G + (f & ~7ll) * NCOP) + (f & 7);
+#pragma unroll
+    for (int j = 0; j < NCOP / 2; ++j) {
+      const float4 v = p[8 * j];
+      if (2 * j + 0 < NCO) gc[2 * j + 0] = DF(v.x, v.y);
+      if (2 * j + 1 < NCO) gc[2 * j + 1] = DF(v.z, v.w);
+    }
+  } else if constexpr (sizeof(T) == 4) {
     const float4* p = reinterpret_cast<const float4*>(G + (f & ~7ll) * NCOP) + (f & 7);
 #pragma unroll
     for (int j = 0; j < NCOP / 4; ++j) {

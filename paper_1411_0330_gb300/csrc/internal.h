@@ -139,6 +139,14 @@ bool encode_y_map(CUtensorMap* out, void* H, int hs, int ny, long long planes);
 bool launch_zgamma_tma(const OpArgs<float>& a, int var, const SolverState* st, cudaStream_t s);
 bool tma_z_variant_fits(const OpArgs<float>& a, int var);
 bool launch_zgamma_regp(const OpArgs<float>& a, const SolverState* st, cudaStream_t s);
+// double-float passes (kernels_df.cu); DF and DF2 come from df.cuh
+struct DF;
+struct DF2;
+bool df_supported(const OpArgs<double>& a);
+void launch_d2df(const double* in, DF* out, long long n, cudaStream_t s);
+void launch_df_x(const OpArgs<double>& a, const DF2* twx, int mode, const double* in, double* out, SolverState* st,
+                 double* partials, cudaStream_t s);
+void df_prepare();
 bool encode_z_map(CUtensorMap* out, void* H, int hs, int ny, int nz, int c, long long nsys, int tz);
 void tma_prepare();
 bool launch_xinv_reg(const OpArgs<float>& a, int mode, const float* xin, float* out, SolverState* st,

@@ -1,0 +1,263 @@
+// kernels_df.cu -- the operator of Eq. (13) in double-float arithmetic (df.cuh):
+// FP64 fields in HBM, every step of the five passes on the FP32 pipes with 48
+// significant bits.  It serves the iterative-refinement residual of the mixed
+// solver (r = b - K x, which must resolve about 1e-11 of ||b||) and the
+// emulated-FP64 apply; on GB300 it runs several times faster than the same
+// passes in native FP64, whose pipe issues 1/64 of the FP32 rate.
+//
+// The y and z passes are the register-FFT kernels of kernels_reg.cu
+// instantiated for DF (the Gamma^h table converted once to double-float).
+// The x passes below read and write FP64: a block owns RY consecutive rows of
+// one system, two real rows form one complex line of N points held by P
+// threads (two-level register FFT, regfft.cuh).
+//   forward (apply):  projection on I0, FFT, split into the two Hermitian half
+//                     rows, store of the half spectrum (double-float pairs);
+//   inverse:          gather of each line's frequencies (X(N - k) = conj X(k)
+//                     beyond the half), inverse FFT, local term M x,
+//                     projection, and for the residual (r, r).
+#include <algorithm>
+
+#include "common.cuh"
+#include "df.cuh"
+#include "fft.cuh"
+#include "internal.h"
+#include "regfft.cuh"
+
+namespace lsh {
+
+template <int N> struct XDf {
+  static constexpr int P = RegPlan<N>::P;
+  static constexpr int THREADS = 128;
+  static constexpr int LINES = THREADS / P;  // packed lines (row pairs) per block
+  static constexpr int RY = 2 * LINES;       // rows per block
+  static constexpr int LS = RegLine<DF, N>::LS;
+  static constexpr int ZS = N + 1;           // shared row stride of the packed spectra
+  static constexpr int EXN = LINES * (LS > ZS ? LS : ZS);
+  static constexpr size_t SMEM = sizeof(DF2) * (size_t)(EXN + N);
+};
+
+__global__ void k_d2df(const double* __restrict__ in, DF* __restrict__ out, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = df_from(in[i]);
+}
+
+// The half spectrum of P x (apply), x FP64 [S][c][nz][ny][nx].
+template <int N>
+__global__ void __launch_bounds__(128) k_df_xfwd(OpArgs<double> a, const DF2* __restrict__ twx,
+                                                 const double* __restrict__ in, int bps) {
+  typedef RegLine<DF, N> RL;
+  typedef XDf<N> XC;
+  constexpr int P = XC::P, R1 = RL::R1, RY = XC::RY, LINES = XC::LINES, ZS = XC::ZS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DF2* ex = reinterpret_cast<DF2*>(smem_raw);
+  DF2* tw = ex + XC::EXN;
+  __shared__ unsigned char aloc[256];
+  for (int u = threadIdx.x; u < N; u += XC::THREADS) tw[u] = twx[u];
+  for (int u = threadIdx.x; u < a.nphase; u += XC::THREADS) aloc[u] = a.act[u];
+  const int s = blockIdx.x / bps, blk = blockIdx.x - s * bps;
+  const int rloc = blk * RY;
+  const long long row0 = (long long)s * a.rps + rloc;
+  const int rows_per_comp = a.nz * a.ny;
+  const int comp = rloc / rows_per_comp;  // the block's rows lie in one component plane
+  const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V;
+  const long long vox0 = (long long)(rloc - comp * rows_per_comp) * N;
+  __syncthreads();
+  const int t = threadIdx.x % P, l = threadIdx.x / P;
+  const double* xa = in + (row0 + 2 * l) * N;
+  const unsigned char* pa = a.phase + pbase + vox0 + (long long)(2 * l) * N;
+  DF2 v[R1];
+#pragma unroll
+  for (int j = 0; j < R1; ++j) {
+    const int x = t + P * j;
+    v[j].x = aloc[pa[x]] ? df_from(xa[x]) : DF(0.f, 0.f);
+    v[j].y = aloc[pa[N + x]] ? df_from(xa[N + x]) : DF(0.f, 0.f);
+  }
+  DF2* exl = ex + l * XC::LS;
+  RL::fwd_a(v, t, tw, exl);
+  __syncthreads();
+  RL::fwd_b(v, t, tw, exl);
+  __syncthreads();  // the exchange area becomes the packed spectra
+  DF2* Zs = ex;
+#pragma unroll
+  for (int m = 0; m < R1; ++m) Zs[l * ZS + RL::freq(t, m)] = v[m];
+  __syncthreads();
+  // split Z = X_a + i X_b into the two Hermitian half rows (zero padding columns)
+  const int hs = a.hs, nxh = a.nxh;
+  DF2* H = reinterpret_cast<DF2*>(a.H);
+  for (int item = threadIdx.x; item < LINES * hs; item += XC::THREADS) {
+    const int ln = item / hs, kx = item - ln * hs;
+    DF2 ya, yb;
+    ya.x = ya.y = yb.x = yb.y = DF(0.f, 0.f);
+    if (kx < nxh) {
+      const DF2 z1 = Zs[ln * ZS + kx];
+      const DF2 z2 = Zs[ln * ZS + ((N - kx) & (N - 1))];
+      ya.x = df_scale2(z1.x + z2.x, 0.5f);
+      ya.y = df_scale2(z1.y - z2.y, 0.5f);
+      yb.x = df_scale2(z1.y + z2.y, 0.5f);
+      yb.y = df_scale2(z2.x - z1.x, 0.5f);
+    }
+    H[(row0 + 2 * ln) * hs + kx] = ya;
+    H[(row0 + 2 * ln + 1) * hs + kx] = yb;
+  }
+}
+
+// MODE 0: out = P (M xin + g).  MODE 2 (residual): out = P (load - M xin - g),
+// (out, out) -> st[s].aux[0].  g = the inverse transform of the spectrum.
+template <int MODE, int N>
+__global__ void __launch_bounds__(128) k_df_xinv(OpArgs<double> a, const DF2* __restrict__ twx,
+                                                 const double* __restrict__ xin, double* __restrict__ out,
+                                                 SolverState* __restrict__ st, double* __restrict__ partials,
+                                                 int bps) {
+  typedef RegLine<DF, N> RL;
+  typedef XDf<N> XC;
+  constexpr int P = XC::P, R1 = RL::R1, Q = RL::Q, RY = XC::RY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DF2* ex = reinterpret_cast<DF2*>(smem_raw);
+  DF2* tw = ex + XC::EXN;
+  __shared__ double mloc[256 * 6];
+  __shared__ unsigned char aloc[256];
+  for (int u = threadIdx.x; u < N; u += XC::THREADS) tw[u] = twx[u];
+  const int ntab = a.nphase * a.c;
+  for (int u = threadIdx.x; u < ntab; u += XC::THREADS) mloc[u] = (a.scale && !a.frac) ? a.modtab[u] : a.mtab[u];
+  for (int u = threadIdx.x; u < a.nphase; u += XC::THREADS) aloc[u] = a.act[u];
+  const int s = blockIdx.x / bps, blk = blockIdx.x - s * bps;
+  const int rloc = blk * RY;
+  const long long row0 = (long long)s * a.rps + rloc;
+  const int rows_per_comp = a.nz * a.ny;
+  const int comp = rloc / rows_per_comp;
+  const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V;
+  const long long vox0 = (long long)(rloc - comp * rows_per_comp) * N;
+  const int t = threadIdx.x % P, l = threadIdx.x / P;
+  const int hs = a.hs;
+  const DF2* Ha = reinterpret_cast<const DF2*>(a.H) + (row0 + 2 * l) * hs;
+  const DF2* Hb = Ha + hs;
+  DF2 v[R1];
+#pragma unroll
+  for (int q = 0; q < Q; ++q)
+#pragma unroll
+    for (int u = 0; u < P; ++u) {
+      const int f = t * Q + q + R1 * u;
+      const bool lo = f <= N / 2;
+      const int k = lo ? f : N - f;
+      const DF2 ya = Ha[k], yb = Hb[k];
+      // Z(f) = X_a(f) + i X_b(f), X(N - k) = conj X(k)
+      DF2 z;
+      if (lo) {
+        z.x = ya.x - yb.y;
+        z.y = ya.y + yb.x;
+      } else {
+        z.x = ya.x + yb.y;
+        z.y = yb.x - ya.y;
+      }
+      v[q * P + u] = z;
+    }
+  __syncthreads();  // tw, mloc, aloc in place
+  DF2* exl = ex + l * XC::LS;
+  RL::inv_a(v, t, tw, exl);
+  __syncthreads();
+  RL::inv_b(v, t, tw, exl);
+  // v[j] = (g of row 2l, g of row 2l + 1) at x = t + P j
+  const double load = MODE == 2 ? a.loads[s * 6 + comp] : 0.0;
+  const DF loaddf = df_from(load);
+  float acc_s = 0.f, acc_c = 0.f;  // compensated (r, r) of this thread
+#pragma unroll
+  for (int j = 0; j < R1; ++j) {
+    const int x = t + P * j;
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) {
+      const long long rowl = 2 * l + h2;
+      const long long vox = vox0 + rowl * N + x;
+      const int p = a.phase[pbase + vox];
+      double o = 0.0;
+      if (aloc[p]) {
+        double m = mloc[p * a.c + comp];
+        if (a.scale) {
+          const double fr = (double)a.scale[pbase + vox];
+          m = a.frac ? fr * mloc[a.c + comp] + (1.0 - fr) * mloc[comp]  // Eq. (def_ah)
+                     : 1.0 / (fr * m - a.ref[comp]);
+        }
+        const DF g = h2 == 0 ? v[j].x : v[j].y;
+        const DF mx = df_from(m) * df_from(xin[(row0 + rowl) * N + x]) + g;
+        if (MODE == 0) {
+          o = df_to(mx);
+        } else {
+          const DF r = loaddf - mx;
+          o = df_to(r);
+          const float y = __fsub_rn(__fmul_rn(r.h, r.h), acc_c);
+          const float tt = __fadd_rn(acc_s, y);
+          acc_c = __fsub_rn(__fsub_rn(tt, acc_s), y);
+          acc_s = tt;
+        }
+      }
+      out[(row0 + rowl) * N + x] = o;
+    }
+  }
+  if (MODE == 2) {
+    Acc<float> acc;
+    acc.s = acc_s;
+    acc.c = acc_c;
+    const double tot = block_reduce(acc);
+    double* part = partials + (long long)s * bps;
+    SolverState* sst = st + s;
+    if (publish_partial_sys(part, blk, bps, tot, &sst->counter[0])) {
+      const double sum = gather_partials_sys(part, bps, &sst->counter[0]);
+      if (threadIdx.x == 0) sst->aux[0] = sum;
+    }
+  }
+}
+
+bool df_length(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+
+// The double-float passes cover 3D grids whose three lengths have register
+// plans and operators without finite-difference phases.
+bool df_supported(const OpArgs<double>& a) {
+  return df_length(a.nx) && df_length(a.ny) && df_length(a.nz) && !a.fdphase && (a.c == 6 || a.c == 3);
+}
+
+void launch_d2df(const double* in, DF* out, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  const long long g = std::min<long long>((n + 255) / 256, 4096);
+  k_d2df<<<(unsigned)g, 256, 0, s>>>(in, out, n);
+}
+
+template <int N> void launch_df_x_n(const OpArgs<double>& a, const DF2* twx, int mode, const double* in, double* out,
+                                    SolverState* st, double* partials, cudaStream_t s) {
+  typedef XDf<N> XC;
+  const int bps = a.rps / XC::RY;
+  const unsigned grid = (unsigned)(a.S * bps);
+  if (mode < 0) k_df_xfwd<N><<<grid, XC::THREADS, XC::SMEM, s>>>(a, twx, in, bps);
+  else if (mode == 0) k_df_xinv<0, N><<<grid, XC::THREADS, XC::SMEM, s>>>(a, twx, in, out, st, partials, bps);
+  else k_df_xinv<2, N><<<grid, XC::THREADS, XC::SMEM, s>>>(a, twx, in, out, st, partials, bps);
+}
+
+// mode -1: forward x pass of P in; 0: inverse x pass, out = P (M in + g);
+// 2: inverse x pass, out = P (load - M in - g) with (out, out) -> st[s].aux[0].
+void launch_df_x(const OpArgs<double>& a, const DF2* twx, int mode, const double* in, double* out, SolverState* st,
+                 double* partials, cudaStream_t s) {
+  switch (a.nx) {
+    case 16: launch_df_x_n<16>(a, twx, mode, in, out, st, partials, s); break;
+    case 32: launch_df_x_n<32>(a, twx, mode, in, out, st, partials, s); break;
+    case 64: launch_df_x_n<64>(a, twx, mode, in, out, st, partials, s); break;
+    case 128: launch_df_x_n<128>(a, twx, mode, in, out, st, partials, s); break;
+    default: launch_df_x_n<256>(a, twx, mode, in, out, st, partials, s); break;
+  }
+}
+
+template <int N> void df_attrs_n() {
+  const int bytes = (int)XDf<N>::SMEM;
+  cudaFuncSetAttribute(k_df_xfwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_df_xinv<0, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  cudaFuncSetAttribute(k_df_xinv<2, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+// launch attributes, set once outside any stream capture
+void df_prepare() {
+  df_attrs_n<16>();
+  df_attrs_n<32>();
+  df_attrs_n<64>();
+  df_attrs_n<128>();
+  df_attrs_n<256>();
+  set_smem_attrs_reg<DF>();
+}
+
+}  // namespace lsh

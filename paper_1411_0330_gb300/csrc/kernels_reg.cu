@@ -92,17 +92,21 @@ template <typename T, int NC, int N, int TZV = 0> struct ZCfg {
 template <typename T, int NC, int N, int TZ, int KS, bool PIPE = true>
 __device__ __forceinline__ void z_gamma_block(const OpArgs<T>& a, C2<T>* buf, const int* line_yp,
                                               const int* line_kx) {
-  if (a.onfly) {
-    for (int item = threadIdx.x; item < N * TZ; item += blockDim.x) {
-      const int kz = item / TZ, li = item - kz * TZ;
-      const int lyp = line_yp[li];
-      if (lyp < 0) continue;
-      C2<T> g[NC];
+  // double-float (T = DF): tabulated coefficients only, no finite-difference phases
+  constexpr bool FLY = !is_df<T>::value;
+  if (FLY && a.onfly) {
+    if constexpr (FLY) {
+      for (int item = threadIdx.x; item < N * TZ; item += blockDim.x) {
+        const int kz = item / TZ, li = item - kz * TZ;
+        const int lyp = line_yp[li];
+        if (lyp < 0) continue;
+        C2<T> g[NC];
 #pragma unroll
-      for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
-      gamma_trunc_onfly<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g);
+        for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
+        gamma_trunc_onfly<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g);
 #pragma unroll
-      for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
+        for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
+      }
     }
   } else if constexpr (!PIPE) {
     for (int item = threadIdx.x; item < N * TZ; item += blockDim.x) {
@@ -112,9 +116,11 @@ __device__ __forceinline__ void z_gamma_block(const OpArgs<T>& a, C2<T>* buf, co
       C2<T> g[NC];
 #pragma unroll
       for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
-      if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g, (T)-1);
+      if constexpr (FLY)
+        if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g, (T)-1);
       gamma_table_apply<T, NC>(a.gtab, ((long long)kz * a.ny + lyp) * a.ts + line_kx[li], g);
-      if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g, (T)1);
+      if constexpr (FLY)
+        if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[lyp], kz, g, (T)1);
 #pragma unroll
       for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
     }
@@ -141,9 +147,11 @@ __device__ __forceinline__ void z_gamma_block(const OpArgs<T>& a, C2<T>* buf, co
         C2<T> g[NC];
 #pragma unroll
         for (int c2 = 0; c2 < NC; ++c2) g[c2] = buf[kz * KS + c2 * TZ + li];
-        if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[line_yp[li]], kz, g, (T)-1);
+        if constexpr (FLY)
+          if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[line_yp[li]], kz, g, (T)-1);
         gamma_coef_apply<T, NC>(gc, g);
-        if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[line_yp[li]], kz, g, (T)1);
+        if constexpr (FLY)
+          if (a.fdphase) fd_rotate<T, NC>(a, line_kx[li], a.kofy[line_yp[li]], kz, g, (T)1);
 #pragma unroll
         for (int c2 = 0; c2 < NC; ++c2) buf[kz * KS + c2 * TZ + li] = g[c2];
       }
@@ -155,7 +163,8 @@ __device__ __forceinline__ void z_gamma_block(const OpArgs<T>& a, C2<T>* buf, co
 }
 
 template <typename T, int NC, int N, int TZV>
-__global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS, ZCfg<T, NC, N, TZV>::THREADS <= 192 ? 4 : 2)
+__global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS,
+                                  (ZCfg<T, NC, N, TZV>::THREADS <= 192 && !is_df<T>::value) ? 4 : 2)
     k_zgamma_reg(OpArgs<T> a, const SolverState* __restrict__ st, int nrt, int nreg) {
   typedef RegLine<T, N> RL;
   typedef ZCfg<T, NC, N, TZV> ZC;
@@ -397,8 +406,13 @@ template <typename T, int TZV> void launch_z_tz(const OpArgs<T>& a, const Solver
 
 // tz = 4: blocks of 4 columns (FP32 autotuner candidate); otherwise the default width
 template <typename T> void launch_zgamma_reg(const OpArgs<T>& a, const SolverState* st, cudaStream_t s, int tz) {
-  if (sizeof(T) == 4 && tz == 4) launch_z_tz<T, 4>(a, st, s);
-  else launch_z_tz<T, 0>(a, st, s);
+  if constexpr (sizeof(T) == 4) {
+    if (tz == 4) {
+      launch_z_tz<T, 4>(a, st, s);
+      return;
+    }
+  }
+  launch_z_tz<T, 0>(a, st, s);
 }
 
 int multiprocessors() {
@@ -483,7 +497,7 @@ template <int NC> void zp_prepare() {
 template <typename T, int NC, int N> void attr_z_n() {
   const int bytes = (int)(sizeof(C2<T>) * (N + ZCfg<T, NC, N, 0>::BUF));
   cudaFuncSetAttribute(k_zgamma_reg<T, NC, N, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (sizeof(T) == 4) {
+  if constexpr (sizeof(T) == 4) {
     const int b4 = (int)(sizeof(C2<T>) * (N + ZCfg<T, NC, N, 4>::BUF));
     cudaFuncSetAttribute(k_zgamma_reg<T, NC, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b4);
   }
@@ -520,10 +534,13 @@ template <typename T> void set_smem_attrs_reg() {
 }
 template void set_smem_attrs_reg<double>();
 template void set_smem_attrs_reg<float>();
+template void set_smem_attrs_reg<DF>();
 
 template void launch_yfft_reg<double>(const OpArgs<double>&, bool, const SolverState*, cudaStream_t);
 template void launch_yfft_reg<float>(const OpArgs<float>&, bool, const SolverState*, cudaStream_t);
 template void launch_zgamma_reg<double>(const OpArgs<double>&, const SolverState*, cudaStream_t, int);
 template void launch_zgamma_reg<float>(const OpArgs<float>&, const SolverState*, cudaStream_t, int);
+template void launch_yfft_reg<DF>(const OpArgs<DF>&, bool, const SolverState*, cudaStream_t);
+template void launch_zgamma_reg<DF>(const OpArgs<DF>&, const SolverState*, cudaStream_t, int);
 
 }  // namespace lsh

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
@@ -19,6 +20,7 @@
 #include <type_traits>
 #include <vector>
 
+#include "df.cuh"
 #include "internal.h"
 #include "lsh.h"
 
@@ -373,10 +375,22 @@ struct Layout {
   size_t off_fd[4], off_Hd, off_gd;
   size_t off_ff[4], off_Hf, off_gf;
   size_t off_wa, off_wb, off_ms;  // MINRES: two direction fields (FP64) and per-system scalars
+  size_t off_gdf, off_twdf;       // double-float Gamma table and twiddles (mixed handles)
+  bool df;                        // double-float residual passes available
   bool minres;                    // MINRES buffers present
   size_t total;
   long long nparts;
 };
+
+bool reg_len(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+
+// The mixed solver's iterative-refinement residual runs in double-float
+// arithmetic (kernels_df.cu) on 3D grids whose lengths have register-FFT
+// plans, for tabulated operators without finite-difference phases.
+bool df_eligible(const Derived& d) {
+  return d.precision == LSH_MIXED && d.dim == 3 && reg_len(d.nx) && reg_len(d.ny) && reg_len(d.nz) &&
+         d.green != LSH_GREEN_FD && (d.c == 3 || d.c == 6);
+}
 
 Layout make_layout(const Derived& d) {
   Layout l{};
@@ -435,6 +449,9 @@ Layout make_layout(const Derived& d) {
     l.off_Hf = take(sizeof(float2) * (size_t)(S * d.c * nfh));
     l.off_gf = take(sizeof(float) * (size_t)(ncop * nf));
   }
+  l.df = df_eligible(d);
+  l.off_gdf = take(l.df ? sizeof(DF) * (size_t)(ncop * nf) : 0);
+  l.off_twdf = take(l.df ? sizeof(DF2) * (size_t)(d.nx + d.ny + d.nz) : 0);
   l.total = o;
   return l;
 }
@@ -476,6 +493,9 @@ struct lsh_handle {
   double *sums, *Wdev, *tabd, *bbdev;
   PrecBufs<double> pd;
   PrecBufs<float> pf;
+  bool dfres = false;  // refinement residual in double-float (else native FP64)
+  DF* gdf = nullptr;   // double-float Gamma table (the FP64 one converted)
+  DF2* twdf = nullptr; // double-float twiddles, x then y then z
   std::vector<long long> n_active;  // voxels in I0 per microstructure
   // diagnostics
   long long launches = 0;
@@ -719,11 +739,62 @@ template <typename T> lsh_status apply_internal(lsh_handle* h, const OpArgs<T>& 
   return last_launch();
 }
 
-// r = b - K x in FP64 for the wave, (r, r) -> residual states' aux[0]
+// The arguments of the double-float y and z passes: those of the FP64 wave
+// with the spectrum read as double-float pairs and the double-float tables.
+OpArgs<DF> df_args(lsh_handle* h, const OpArgs<double>& a) {
+  static_assert(sizeof(OpArgs<DF>) == sizeof(OpArgs<double>) && alignof(OpArgs<DF>) == alignof(OpArgs<double>),
+                "same layout");
+  static_assert(offsetof(OpArgs<DF>, invV) == offsetof(OpArgs<double>, invV) &&
+                    offsetof(OpArgs<DF>, xfreg) == offsetof(OpArgs<double>, xfreg),
+                "same layout");
+  OpArgs<DF> b;
+  std::memcpy(static_cast<void*>(&b), &a, sizeof(b));  // every member but the typed ones below
+  const Derived& d = h->d;
+  b.twx = h->twdf;
+  b.twy = h->twdf + d.nx;
+  b.twz = h->twdf + d.nx + d.ny;
+  b.H = reinterpret_cast<DF2*>(a.H);
+  b.gtab = h->gdf;
+  b.mtab = b.modtab = b.loads = nullptr;
+  for (int i = 0; i < 6; ++i) {
+    b.ref[i] = DF(a.ref[i]);
+    b.g0[i] = DF(a.g0[i]);
+  }
+  b.invV = DF(a.invV);
+  b.onfly = 0;
+  b.fdphase = 0;
+  return b;
+}
+
+// y = K x in double-float arithmetic (FP64 in and out)
+lsh_status apply_df(lsh_handle* h, const OpArgs<double>& a, const double* in, double* out) {
+  cudaStream_t s = h->stream;
+  const OpArgs<DF> b = df_args(h, a);
+  launch_df_x(a, b.twx, -1, in, nullptr, nullptr, nullptr, s);
+  launch_yfft_reg<DF>(b, false, nullptr, s);
+  launch_zgamma_reg<DF>(b, nullptr, s, 0);
+  launch_yfft_reg<DF>(b, true, nullptr, s);
+  launch_df_x(a, b.twx, 0, in, out, nullptr, nullptr, s);
+  h->launches += 5;
+  return last_launch();
+}
+
+// r = b - K x in FP64 for the wave, (r, r) -> residual states' aux[0]; in
+// double-float arithmetic where the handle has those passes
 lsh_status residual64(lsh_handle* h, const OpArgs<double>& a, const double* x, double* r) {
   PrecBufs<double>& P = h->pd;
   cudaStream_t s = h->stream;
   SolverState* sres = h->st + 2 * h->d.Smax;
+  if (h->dfres) {
+    const OpArgs<DF> b = df_args(h, a);
+    launch_df_x(a, b.twx, -1, x, nullptr, nullptr, nullptr, s);
+    launch_yfft_reg<DF>(b, false, nullptr, s);
+    launch_zgamma_reg<DF>(b, nullptr, s, 0);
+    launch_yfft_reg<DF>(b, true, nullptr, s);
+    launch_df_x(a, b.twx, 2, x, r, sres, h->partials, s);
+    h->launches += 5;
+    return last_launch();
+  }
   launch_xfwd<double>(a, P.L, 0, x, nullptr, nullptr, nullptr, nullptr, s);
   launch_yfft<double>(a, P.L, false, nullptr, s);
   launch_zgamma<double>(a, P.L, nullptr, s);
@@ -1254,6 +1325,12 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   {
     const char* e = getenv("LSH_NO_TMA");
     h->no_tma = e && e[0] == '1';
+    const char* f = getenv("LSH_NO_DF");
+    h->dfres = l.df && !(f && f[0] == '1');
+    if (l.df) {
+      h->gdf = (DF*)(h->base + l.off_gdf);
+      h->twdf = (DF2*)(h->base + l.off_twdf);
+    }
   }
   init_prec<double>(h, h->pd, l.off_fd, l.off_Hd, l.off_gd, l.off_tw_d, l.off_tabd, l.off_loads_d, h->st);
   if (d.precision == LSH_MIXED)
@@ -1297,11 +1374,17 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   set_smem_attrs<float>();
   tma_prepare();
   xreg_prepare();
+  if (l.df) df_prepare();
   launch_gamma_table<double>(h->pd.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st,
                              d.rotated ? d.A0full : nullptr, d.rotated ? d.R : nullptr);
   if (d.precision == LSH_MIXED)
     launch_gamma_table<float>(h->pf.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st,
                               d.rotated ? d.A0full : nullptr, d.rotated ? d.R : nullptr);
+  if (l.df) {
+    const long long nf = (long long)d.nz * d.ny * d.ts, ncop = (d.ncoef + 3) & ~3;
+    launch_d2df(h->pd.gtab, h->gdf, ncop * nf, st);
+    launch_d2df((const double*)(h->base + l.off_tw_d), reinterpret_cast<DF*>(h->twdf), 2ll * (d.nx + d.ny + d.nz), st);
+  }
   if (last_launch() != LSH_OK) { delete h; return LSH_ERR_CUDA; }
   s = scan_microstructure(h);  // synchronises the stream (host vectors may go)
   if (s) { delete h; return s; }
@@ -1323,11 +1406,12 @@ lsh_status lsh_apply(lsh_handle* h, int dtype, const void* x, void* y) {
   const Derived& d = h->d;
   const bool el = d.physics == LSH_ELASTIC_ISO;
   const long long n = (long long)d.c * d.V;
-  if (dtype != LSH_F64 && dtype != LSH_F32) return LSH_ERR_INVALID_ARG;
+  if (dtype != LSH_F64 && dtype != LSH_F32 && dtype != LSH_F64_DF) return LSH_ERR_INVALID_ARG;
   if (dtype == LSH_F32 && d.precision != LSH_MIXED) return LSH_ERR_UNSUPPORTED;
+  if (dtype == LSH_F64_DF && !h->lay.df) return LSH_ERR_UNSUPPORTED;
   // one system per microstructure; in waves when the handle holds fewer systems
   // (FP64 on a mixed handle: one system at a time through the p, q scratch)
-  const int per_wave = (dtype == LSH_F64 && d.precision == LSH_MIXED) ? 1 : std::min(d.Smax, d.B);
+  const int per_wave = (dtype != LSH_F32 && d.precision == LSH_MIXED) ? 1 : std::min(d.Smax, d.B);
   for (int b0 = 0; b0 < d.B; b0 += per_wave) {
     const int S = std::min(per_wave, d.B - b0);
     std::vector<double> zl(6 * (size_t)S, 0.0);
@@ -1339,7 +1423,7 @@ lsh_status lsh_apply(lsh_handle* h, int dtype, const void* x, void* y) {
       if (el) launch_rotate<TT>(in, out, d.V, S, to_internal, h->stream);
       else launch_rotate_scalar<TT>(in, out, d.V, S, d.c, d.R, to_internal, h->stream);
     };
-    if (dtype == LSH_F64) {
+    if (dtype != LSH_F32) {
       PrecBufs<double>& P = h->pd;
       const double* in = (const double*)x + b0 * n;
       double* o = (double*)y + b0 * n;
@@ -1347,7 +1431,8 @@ lsh_status lsh_apply(lsh_handle* h, int dtype, const void* x, void* y) {
         rotate(in, P.p, 1);
         in = P.p;
       }
-      lsh_status s = apply_internal<double>(h, wave_args<double>(h, w), in, rot ? P.q : o);
+      lsh_status s = dtype == LSH_F64_DF ? apply_df(h, wave_args<double>(h, w), in, rot ? P.q : o)
+                                         : apply_internal<double>(h, wave_args<double>(h, w), in, rot ? P.q : o);
       if (s) return s;
       if (rot) rotate((const double*)P.q, o, 0);
     } else {

@@ -22,7 +22,7 @@ from . import build as _build
 SCALAR, ELASTIC = 0, 1
 TRUNCATED, FILTERED, FD = 0, 1, 2
 FP64, MIXED = 0, 1
-F64, F32 = 0, 1
+F64, F32, F64_DF = 0, 1, 2
 SOLVER_AUTO, SOLVER_CG, SOLVER_MINRES, SOLVER_BASIC = 0, 1, 2, 3
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_REFERENCE_INDEFINITE, ERR_SINGULAR_CONTRAST, \
@@ -315,14 +315,17 @@ class Handle:
         _check(self.lib.lsh_set_microstructure(self._h, ctypes.c_void_p(phase.data_ptr()), sp, 1 if on_host else 0),
                "lsh_set_microstructure")
 
-    def apply(self, x, out=None, dtype=None):
-        """y = K x, the operator of Eq. (13) with the projection on I0."""
+    def apply(self, x, out=None, dtype=None, double_float=False):
+        """y = K x, the operator of Eq. (13) with the projection on I0.
+        double_float=True (FP64 fields, mixed handles): evaluated in double-float
+        arithmetic on the FP32 pipes, as the mixed solver's refinement residual is."""
         t = self._torch
         dtype = dtype or (x.dtype if isinstance(x, t.Tensor) and x.dtype in (t.float32, t.float64) else t.float64)
         x = self._field(x, dtype)
         y = out if out is not None else t.empty_like(x)
         self._wait_inputs()
-        _check(self.lib.lsh_apply(self._h, F64 if dtype == t.float64 else F32, ctypes.c_void_p(x.data_ptr()),
+        code = F32 if dtype != t.float64 else (F64_DF if double_float else F64)
+        _check(self.lib.lsh_apply(self._h, code, ctypes.c_void_p(x.data_ptr()),
                                   ctypes.c_void_p(y.data_ptr())), "lsh_apply")
         self._release_outputs()
         return y

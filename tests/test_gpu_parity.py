@@ -513,6 +513,48 @@ def test_persistent_z_pass_matches_register_z_pass(shape, physics, green):
         assert rel(y7[k].cpu().numpy(), oracle.apply(Ps[k], x[k])) < 2e-5
 
 
+@pytest.mark.parametrize("shape,physics,green", [((32, 32, 32), 1, 1), ((16, 64, 32), 1, 0), ((64, 16, 128), 1, 1),
+                                                 ((32, 16, 64), 0, 1), ((16, 32, 16), 0, 0), ((16, 16, 256), 1, 0)])
+def test_double_float_apply_matches_fp64(shape, physics, green):
+    """K x in double-float arithmetic (FP64 fields, every pass on the FP32 pipes
+    with 48-bit significands) against the native FP64 passes and the oracle: the
+    difference stays at the level of 2^-48 times log N, far below what the
+    refinement residual must resolve (1e-11 of ||b||)."""
+    rng = np.random.default_rng(sum(shape) + 11 * green + physics)
+    if physics == 1:
+        ph = (rng.random(shape) < 0.35).astype(np.uint8)
+        mods = EL
+    else:
+        ph = rng.integers(0, 3, shape).astype(np.uint8)
+        mods = _scalar_mods(3, 4)
+    P = oracle.Problem(ph, mods, physics=physics, green=green)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=green, precision=lsh.MIXED)
+    x = rng.standard_normal(P.field_shape)
+    xt = torch.from_numpy(x).cuda()
+    y64 = h.apply(xt).cpu().numpy()
+    ydf = h.apply(xt, double_float=True).cpu().numpy()
+    yo = oracle.apply(P, x)
+    assert rel(ydf, y64) < 1e-13, rel(ydf, y64)
+    assert rel(ydf, yo) < 1e-13, rel(ydf, yo)
+
+
+def test_double_float_residual_solve_matches_native_fp64_residual(monkeypatch):
+    """The mixed solver with its refinement residual in double-float (the default
+    on such grids) and with the native FP64 residual reach the same C* to the
+    solve tolerance, and both the oracle's."""
+    ph, _, _ = ms.sphere_microstructure(32, 4.0, 0.25, seed=78)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
+    A_df, inf_df = h.effective(tol=1e-10)
+    monkeypatch.setenv("LSH_NO_DF", "1")
+    h64 = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
+    A_64, inf_64 = h64.effective(tol=1e-10)
+    Ao, _ = oracle.effective(oracle.Problem(ph, EL, physics=1, green=1), tol=1e-13)
+    assert rel(A_df, A_64) < 1e-9, rel(A_df, A_64)
+    assert rel(A_df, Ao) < 1e-8 and rel(A_64, Ao) < 1e-8
+    assert all(i["status"] == 0 and i["relres"] <= 1e-10 for i in inf_df)
+    assert sum(i["outer"] for i in inf_df) == sum(i["outer"] for i in inf_64)
+
+
 @pytest.mark.parametrize("shape,physics", [((16, 256, 32), 1), ((256, 16, 16), 1), ((8, 256, 256), 0)])
 def test_length_256_passes_fp64_and_fp32(shape, physics):
     """Lines of 256 points (the largest register-FFT length: 16 x 16 split) along each
