@@ -61,7 +61,25 @@ __device__ __forceinline__ DF& operator*=(DF& a, DF b) { return a = a * b; }
 // exact scalings by powers of two
 __device__ __forceinline__ DF df_scale2(DF a, float p2) { return DF(__fmul_rn(a.h, p2), __fmul_rn(a.l, p2)); }
 
-// conversions (one FP64 operation each)
+// double -> double-float with integer operations only (the FP64 pipe is the
+// scarce unit): h = d with its significand cut to 24 bits, l = the remaining
+// 29 bits rounded to FP32 (together within 2^-48 |d|).  |d| < 2^-126 maps to
+// 0, the low part of |d| < 2^-74 to 0 (below 2^-98 in absolute terms).
+__device__ __forceinline__ DF df_split(double d) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(d);
+  const unsigned hi = (unsigned)(u >> 32), lo = (unsigned)u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const int ef = e - 896;  // FP32 exponent field: e - 1023 + 127
+  const unsigned sign = hi & 0x80000000u;
+  if (ef <= 0) return DF(0.f, 0.f);
+  if (ef >= 255) return DF(__uint_as_float(sign | 0x7f800000u), 0.f);
+  const float h = __uint_as_float(sign | ((unsigned)ef << 23) | ((hi & 0xfffffu) << 3) | (lo >> 29));
+  float l = 0.f;
+  if (e >= 949) l = __fmul_rn(__uint2float_rn(lo & 0x1fffffffu), __uint_as_float((unsigned)(e - 948) << 23));
+  return DF(h, sign ? -l : l);
+}
+
+// conversions through the FP64 pipe (one FP64 operation each)
 __device__ __forceinline__ DF df_from(double d) {
   const float h = __double2float_rn(d);
   return DF(h, __double2float_rn(d - (double)h));

@@ -113,7 +113,7 @@ void launch_gamma_table(const OpArgs<T>& a, int dim, int physics, int green, con
 template <typename T>
 void launch_rotate_scalar(const T* in, T* out, long long V, int nsys, int d, const double* R, int to_internal,
                           cudaStream_t s);
-void launch_d2f_begin(const double* r64, float* r32, float* x32, long long n, int S, SolverState* st,
+void launch_d2f_begin(const double* r64, bool df_pairs, float* r32, float* x32, long long n, int S, SolverState* st,
                       double* partials, double tol, const unsigned char* active, int G, cudaStream_t s);
 void launch_f2d_axpy(double* x64, const float* x32, long long n, cudaStream_t s);
 void launch_scan_phase(const unsigned char* phase, long long V, int B, const unsigned char* act, int nphase,

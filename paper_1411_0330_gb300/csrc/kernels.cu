@@ -942,6 +942,8 @@ __global__ void k_gamma_table(OpArgs<T> a, GammaCtx g, const int* __restrict__ k
 // ------------------------------------------------------------------ mixed precision helpers
 // r32 = (float) r64, x32 = 0, inner CG state begun with tolerance tol relative
 // to the new right-hand side; systems with active[s] == 0 start done.
+// DFIN: r64's elements hold double-float pairs (h, l); the FP32 residual is h
+template <bool DFIN>
 __global__ void __launch_bounds__(kThreads) k_d2f_begin(const double* __restrict__ r64, float* __restrict__ r32,
                                                         float* __restrict__ x32, long long n,
                                                         SolverState* __restrict__ st, double* __restrict__ partials,
@@ -952,7 +954,7 @@ __global__ void __launch_bounds__(kThreads) k_d2f_begin(const double* __restrict
   float* x32s = x32 + s * n;
   Acc<float> acc;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const float v = (float)r64s[i];
+    const float v = DFIN ? reinterpret_cast<const float2*>(r64s)[i].x : (float)r64s[i];
     r32s[i] = v;
     x32s[i] = 0.0f;
     acc.add(v * v);
@@ -1223,9 +1225,10 @@ void launch_gamma_table(const OpArgs<T>& a, int dim, int physics, int green, con
   const int grid = (int)std::min<long long>((nf + 127) / 128, 152LL * 16);
   k_gamma_table<T><<<grid, 128, 0, s>>>(a, g, kofy, kofz);
 }
-void launch_d2f_begin(const double* r64, float* r32, float* x32, long long n, int S, SolverState* st,
+void launch_d2f_begin(const double* r64, bool df_pairs, float* r32, float* x32, long long n, int S, SolverState* st,
                       double* partials, double tol, const unsigned char* active, int G, cudaStream_t s) {
-  k_d2f_begin<<<dim3(G, S), kThreads, 0, s>>>(r64, r32, x32, n, st, partials, tol, active);
+  if (df_pairs) k_d2f_begin<true><<<dim3(G, S), kThreads, 0, s>>>(r64, r32, x32, n, st, partials, tol, active);
+  else k_d2f_begin<false><<<dim3(G, S), kThreads, 0, s>>>(r64, r32, x32, n, st, partials, tol, active);
 }
 void launch_f2d_axpy(double* x64, const float* x32, long long n, cudaStream_t s) {
   const int grid = (int)std::max(1LL, std::min((n + kThreads - 1) / kThreads, 152LL * 16));

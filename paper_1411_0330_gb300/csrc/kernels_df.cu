@@ -69,6 +69,7 @@ __global__ void __launch_bounds__(128) k_df_xfwd(OpArgs<double> a, const DF2* __
 #pragma unroll
   for (int j = 0; j < R1; ++j) {
     const int x = t + P * j;
+    // the FP64 pipe has room here (measured faster than the integer split)
     v[j].x = aloc[pa[x]] ? df_from(xa[x]) : DF(0.f, 0.f);
     v[j].y = aloc[pa[N + x]] ? df_from(xa[N + x]) : DF(0.f, 0.f);
   }
@@ -101,8 +102,9 @@ __global__ void __launch_bounds__(128) k_df_xfwd(OpArgs<double> a, const DF2* __
   }
 }
 
-// MODE 0: out = P (M xin + g).  MODE 2 (residual): out = P (load - M xin - g),
-// (out, out) -> st[s].aux[0].  g = the inverse transform of the spectrum.
+// MODE 0: out = P (M xin + g) (FP64).  MODE 2 (residual): out = P (load - M xin
+// - g) as double-float pairs (h, l) in the 8 bytes of each element, (out, out)
+// -> st[s].aux[0].  g = the inverse transform of the spectrum.
 template <int MODE, int N>
 __global__ void __launch_bounds__(128) k_df_xinv(OpArgs<double> a, const DF2* __restrict__ twx,
                                                  const double* __restrict__ xin, double* __restrict__ out,
@@ -114,11 +116,11 @@ __global__ void __launch_bounds__(128) k_df_xinv(OpArgs<double> a, const DF2* __
   extern __shared__ __align__(16) unsigned char smem_raw[];
   DF2* ex = reinterpret_cast<DF2*>(smem_raw);
   DF2* tw = ex + XC::EXN;
-  __shared__ double mloc[256 * 6];
+  __shared__ DF mloc[256 * 6];
   __shared__ unsigned char aloc[256];
   for (int u = threadIdx.x; u < N; u += XC::THREADS) tw[u] = twx[u];
   const int ntab = a.nphase * a.c;
-  for (int u = threadIdx.x; u < ntab; u += XC::THREADS) mloc[u] = (a.scale && !a.frac) ? a.modtab[u] : a.mtab[u];
+  for (int u = threadIdx.x; u < ntab; u += XC::THREADS) mloc[u] = df_from(a.mtab[u]);
   for (int u = threadIdx.x; u < a.nphase; u += XC::THREADS) aloc[u] = a.act[u];
   const int s = blockIdx.x / bps, blk = blockIdx.x - s * bps;
   const int rloc = blk * RY;
@@ -157,8 +159,7 @@ __global__ void __launch_bounds__(128) k_df_xinv(OpArgs<double> a, const DF2* __
   __syncthreads();
   RL::inv_b(v, t, tw, exl);
   // v[j] = (g of row 2l, g of row 2l + 1) at x = t + P j
-  const double load = MODE == 2 ? a.loads[s * 6 + comp] : 0.0;
-  const DF loaddf = df_from(load);
+  const DF loaddf = MODE == 2 ? df_from(a.loads[s * 6 + comp]) : DF(0.f, 0.f);
   float acc_s = 0.f, acc_c = 0.f;  // compensated (r, r) of this thread
 #pragma unroll
   for (int j = 0; j < R1; ++j) {
@@ -167,29 +168,29 @@ __global__ void __launch_bounds__(128) k_df_xinv(OpArgs<double> a, const DF2* __
     for (int h2 = 0; h2 < 2; ++h2) {
       const long long rowl = 2 * l + h2;
       const long long vox = vox0 + rowl * N + x;
+      const long long gi = (row0 + rowl) * N + x;
       const int p = a.phase[pbase + vox];
-      double o = 0.0;
+      DF o(0.f, 0.f);
       if (aloc[p]) {
-        double m = mloc[p * a.c + comp];
-        if (a.scale) {
+        DF m = mloc[p * a.c + comp];
+        if (a.scale) {  // per-voxel moduli: M in FP64, then split
           const double fr = (double)a.scale[pbase + vox];
-          m = a.frac ? fr * mloc[a.c + comp] + (1.0 - fr) * mloc[comp]  // Eq. (def_ah)
-                     : 1.0 / (fr * m - a.ref[comp]);
+          const double m0 = a.mtab[comp], m1 = a.mtab[a.c + comp], mp = a.modtab[p * a.c + comp];
+          m = df_from(a.frac ? fr * m1 + (1.0 - fr) * m0  // Eq. (def_ah)
+                             : 1.0 / (fr * mp - a.ref[comp]));
         }
         const DF g = h2 == 0 ? v[j].x : v[j].y;
-        const DF mx = df_from(m) * df_from(xin[(row0 + rowl) * N + x]) + g;
-        if (MODE == 0) {
-          o = df_to(mx);
-        } else {
-          const DF r = loaddf - mx;
-          o = df_to(r);
-          const float y = __fsub_rn(__fmul_rn(r.h, r.h), acc_c);
+        o = m * df_split(xin[gi]) + g;
+        if (MODE == 2) {
+          o = loaddf - o;
+          const float y = __fsub_rn(__fmul_rn(o.h, o.h), acc_c);
           const float tt = __fadd_rn(acc_s, y);
           acc_c = __fsub_rn(__fsub_rn(tt, acc_s), y);
           acc_s = tt;
         }
       }
-      out[(row0 + rowl) * N + x] = o;
+      if (MODE == 0) out[gi] = df_to(o);
+      else reinterpret_cast<float2*>(out)[gi] = make_float2(o.h, o.l);
     }
   }
   if (MODE == 2) {
@@ -231,7 +232,8 @@ template <int N> void launch_df_x_n(const OpArgs<double>& a, const DF2* twx, int
 }
 
 // mode -1: forward x pass of P in; 0: inverse x pass, out = P (M in + g);
-// 2: inverse x pass, out = P (load - M in - g) with (out, out) -> st[s].aux[0].
+// 2: inverse x pass, out = P (load - M in - g) as double-float pairs, with
+// (out, out) -> st[s].aux[0].
 void launch_df_x(const OpArgs<double>& a, const DF2* twx, int mode, const double* in, double* out, SolverState* st,
                  double* partials, cudaStream_t s) {
   switch (a.nx) {

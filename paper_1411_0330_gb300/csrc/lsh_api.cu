@@ -779,13 +779,14 @@ lsh_status apply_df(lsh_handle* h, const OpArgs<double>& a, const double* in, do
   return last_launch();
 }
 
-// r = b - K x in FP64 for the wave, (r, r) -> residual states' aux[0]; in
-// double-float arithmetic where the handle has those passes
-lsh_status residual64(lsh_handle* h, const OpArgs<double>& a, const double* x, double* r) {
+// r = b - K x for the wave, (r, r) -> residual states' aux[0].  df (handles
+// with the double-float passes): computed in double-float arithmetic and
+// stored as (h, l) FP32 pairs in r's 8-byte elements; otherwise native FP64.
+lsh_status residual64(lsh_handle* h, const OpArgs<double>& a, const double* x, double* r, bool df = false) {
   PrecBufs<double>& P = h->pd;
   cudaStream_t s = h->stream;
   SolverState* sres = h->st + 2 * h->d.Smax;
-  if (h->dfres) {
+  if (df) {
     const OpArgs<DF> b = df_args(h, a);
     launch_df_x(a, b.twx, -1, x, nullptr, nullptr, nullptr, s);
     launch_yfft_reg<DF>(b, false, nullptr, s);
@@ -1141,12 +1142,14 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
     const int max_outer = o && o->max_outer > 0 ? o->max_outer : 30;
     std::vector<double> rr(S);
     SolverState* sres = h->st + 2 * d.Smax;
+    bool rdf = false;  // Pd.r holds double-float pairs (else FP64)
     if (!warm) {
       launch_fill_rhs<double>(ad, Pd.r, Pd.x, G, h->stream);
       h->launches += 1;
       rr = bb;
     } else {
-      if ((stt = residual64(h, ad, Pd.x, Pd.r))) return stt;
+      if ((stt = residual64(h, ad, Pd.x, Pd.r, h->dfres))) return stt;
+      rdf = h->dfres;
       for (int s = 0; s < S; ++s) infos[s].applies64 += 1;
       std::vector<SolverState> s2(S);
       if ((stt = read_states(h, sres, S, s2.data()))) return stt;
@@ -1172,12 +1175,14 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
         break;
       }
       LSH_CK(cudaMemcpyAsync(h->flags, active.data(), S, cudaMemcpyHostToDevice, h->stream));
-      launch_d2f_begin(Pd.r, Pf.r, Pf.x, n, S, Pf.st, h->partials, itol, h->flags, Pf.L.ew_per_sys, h->stream);
+      launch_d2f_begin(Pd.r, rdf, Pf.r, Pf.x, n, S, Pf.st, h->partials, itol, h->flags, Pf.L.ew_per_sys,
+                       h->stream);
       h->launches += 1;
       if ((stt = cg_run<float>(h, Pf, af, maxit - total_max, check, graphs, st))) return stt;
       launch_f2d_axpy(Pd.x, Pf.x, n * S, h->stream);
       h->launches += 1;
-      if ((stt = residual64(h, ad, Pd.x, Pd.r))) return stt;
+      if ((stt = residual64(h, ad, Pd.x, Pd.r, h->dfres))) return stt;
+      rdf = h->dfres;
       std::vector<SolverState> s2(S);
       if ((stt = read_states(h, sres, S, s2.data()))) return stt;
       ++outer;
