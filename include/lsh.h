@@ -60,7 +60,10 @@ enum { LSH_GREEN_TRUNCATED = 0, LSH_GREEN_FILTERED = 1, LSH_GREEN_FD = 2 };
 /* Arithmetic of the solve.  LSH_FP64: every step in double precision.
  * LSH_MIXED: FFTs, Gamma apply and CG vectors in single precision, inner
  * products and CG scalars in double, wrapped in iterative refinement whose
- * residual b - K x is computed with the double-precision operator. */
+ * residual b - K x is computed to double-precision accuracy: in double-float
+ * arithmetic (see LSH_F64_DF) where the grid allows it, else with the FP64
+ * operator.  The environment variable LSH_NO_DF=1 at lsh_setup forces the
+ * FP64 operator. */
 enum { LSH_FP64 = 0, LSH_MIXED = 1 };
 /* element type of fields passed to lsh_apply.  LSH_F64_DF: FP64 fields, the
  * operator evaluated in double-float arithmetic (pairs of FP32 values, 48
