@@ -152,6 +152,8 @@ def pass_flops(kind, V, c, nx, ny, nz, nxh):
 # systems of the 128^3 workload, from the ncu captures summarised in
 # profiles/fp32_passes_128cube_six_systems.md (filtered operator); to be
 # retaken whenever one of these kernels changes.
+PROF_EVERY = 8  # per-pass events in one CG chunk of this many
+
 NCU_TRAFFIC_FP32 = {"x_forward": 1770.9e6, "y_forward": 588.4e6, "z_gamma": 829.8e6, "y_inverse": 587.6e6,
                     "x_inverse_local": 902.0e6, "cg_update": 862.9e6}
 
@@ -678,10 +680,11 @@ def main():
             res.append((A, infos))
         return its, res
 
-    def timed(handles, profile, name):
+    def timed(handles, profile, name, steps=None):
+        steps = steps or args.steps
         for h in handles:
             h.profile_read(reset=True)
-            h.profile_enable(profile)
+            h.profile_enable(bool(profile), every=int(profile))
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -692,7 +695,7 @@ def main():
         torch.cuda.nvtx.range_push(name)  # lets a profiler select the timed region
         e0.record(stream)
         tot_its, last = 0, None
-        for _ in range(args.steps):
+        for _ in range(steps):
             its, last = step(handles)
             tot_its += its
         e1.record(stream)
@@ -709,10 +712,12 @@ def main():
     for _ in range(args.warmup):
         step(hmx)
         step(h64)
-    # headline: the mixed-precision solver, all 6 loads of a handle batched in one launch sequence
-    ms_mx, its_mx, last_mx, prof_mx, clocks = timed(hmx, True, "timed_mixed")
+    # headline: the mixed-precision solver, all 6 loads of a handle batched in one launch sequence.
+    # Per-pass CUDA events are recorded in one CG chunk of PROF_EVERY (event nodes in every
+    # graph would add gaps between the kernels: 3.4% on the step)
+    ms_mx, its_mx, last_mx, prof_mx, clocks = timed(hmx, PROF_EVERY, "timed_mixed")
     # comparison: the plain FP64 solver on the same workload
-    ms_64, its_64, last_64, prof_64, clocks64 = timed(h64, True, "timed_fp64")
+    ms_64, its_64, last_64, prof_64, clocks64 = timed(h64, PROF_EVERY, "timed_fp64")
     nrep = world
     value_64 = replica_rate(its_64 * V, nrep, ms_64)
     value_raw = replica_rate(its_mx * V, nrep, ms_mx)
@@ -792,6 +797,7 @@ def main():
                 "config": cfg, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clocks,
                 "mixed": {"value_raw": value_raw, "inner_iterations_per_step": its_mx / args.steps,
+                          "pass_events": f"one CG chunk in {PROF_EVERY}",
                           "c_star_max_rel_err_vs_fp64": cerr,
                           "speedup_vs_fp64": ms_64 / ms_mx,
                           "outer_steps_per_step": sum(i["outer"] for r in last_mx for i in r[1]),

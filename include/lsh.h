@@ -271,7 +271,10 @@ typedef struct lsh_profile {
   long long pass_launches[6];  /* launches that did work, per pass kind           */
 } lsh_profile;
 
-/* Enable (nonzero) or disable per-pass event timing.  Host memory only. */
+/* Per-pass event timing of the CG iterations: 0 off, 1 every iteration, k > 1
+ * the iterations of every k-th chunk of check_every iterations (the other
+ * chunks replay graphs without event nodes, which add gaps between kernels).
+ * Host memory only. */
 lsh_status lsh_profile_enable(lsh_handle *h, int enable);
 
 /* Copy the counters into `out` (host); reset them when `reset` is nonzero. */

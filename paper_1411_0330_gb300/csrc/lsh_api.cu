@@ -500,6 +500,9 @@ struct lsh_handle {
   // diagnostics
   long long launches = 0;
   bool prof = false;
+  int prof_every = 1;           // events in every prof_every-th CG chunk
+  long long prof_chunk = 0;
+  bool prof_now = false;        // the chunk being enqueued records events
   std::vector<cudaEvent_t> ev;  // 7 per timed iteration
   int ev_used = 0;
   double pass_ms[6] = {0, 0, 0, 0, 0, 0};
@@ -807,7 +810,7 @@ lsh_status residual64(lsh_handle* h, const OpArgs<double>& a, const double* x, d
 
 template <typename T> void enqueue_cg_iteration(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a) {
   cudaStream_t s = h->stream;
-  const bool timed = h->prof && h->ev_used + 7 <= (int)h->ev.size();
+  const bool timed = h->prof_now && h->ev_used + 7 <= (int)h->ev.size();
   cudaEvent_t* e = timed ? &h->ev[h->ev_used] : nullptr;
   // inside a capture the records become graph nodes that record at replay
   const unsigned rf = h->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -839,7 +842,7 @@ lsh_status chunk_graph(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int ch
   const int prec = (int)sizeof(T);
   for (auto& g : h->graphs)
     if (g.prec == prec && g.sys0 == a.sys0 && g.S == a.S && g.sys_per_ms == a.sys_per_ms && g.chunk == chunk &&
-        g.prof == h->prof) {
+        g.prof == h->prof_now) {
       *out = &g;
       return LSH_OK;
     }
@@ -858,7 +861,7 @@ lsh_status chunk_graph(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int ch
   }
   h->capturing = false;
   h->stream = user;
-  lsh_handle::Graph g{prec, a.sys0, a.S, a.sys_per_ms, chunk, h->prof, nullptr, h->launches - l0};
+  lsh_handle::Graph g{prec, a.sys0, a.S, a.sys_per_ms, chunk, h->prof_now, nullptr, h->launches - l0};
   h->launches = l0;
   h->ev_used = ev0;
   if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, graph, 0);
@@ -914,20 +917,22 @@ lsh_status cg_run(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int maxit, 
   while (!all_done() && it < maxit) {
     const int chunk = std::min(check_every, maxit - it);
     const int before = max_iter();
+    h->prof_now = h->prof && (h->prof_chunk++ % h->prof_every) == 0;
     if (graphs && chunk == check_every) {
       lsh_handle::Graph* g = nullptr;
       if ((stt = chunk_graph<T>(h, P, a, chunk, &g))) return stt;
-      if (h->prof) h->ev_used = 0;
+      if (h->prof_now) h->ev_used = 0;
       LSH_CK(cudaGraphLaunch(g->exec, h->stream));
       h->launches += g->launches;
-      if (h->prof) h->ev_used = (int)std::min<size_t>(7 * (size_t)chunk, h->ev.size() / 7 * 7);
+      if (h->prof_now) h->ev_used = (int)std::min<size_t>(7 * (size_t)chunk, h->ev.size() / 7 * 7);
     } else {
       for (int j = 0; j < chunk; ++j) enqueue_cg_iteration<T>(h, P, a);
     }
     if ((stt = last_launch())) return stt;
     it += chunk;
     if ((stt = read_states(h, P.st, S, out.data()))) return stt;
-    if (h->prof) harvest_profile(h, max_iter() - before);
+    if (h->prof_now) harvest_profile(h, max_iter() - before);
+    h->prof_now = false;
   }
   launch_cg_finalize<T>(P.x, P.p, (long long)a.c * a.V, S, P.st, P.L.ew_per_sys, h->stream);
   h->launches += 1;
@@ -1752,6 +1757,8 @@ lsh_status lsh_profile_enable(lsh_handle* h, int enable) {
       }
   }
   h->prof = enable != 0;
+  h->prof_every = enable > 1 ? enable : 1;
+  h->prof_chunk = 0;
   h->ev_used = 0;
   return LSH_OK;
 }

@@ -382,8 +382,10 @@ class Handle:
         _check(self.lib.lsh_set_variants(self._h, int(xf_variant), int(x_variant), int(y_variant), int(z_variant)),
                "lsh_set_variants")
 
-    def profile_enable(self, enable=True):
-        _check(self.lib.lsh_profile_enable(self._h, 1 if enable else 0), "lsh_profile_enable")
+    def profile_enable(self, enable=True, every=1):
+        """Per-pass CUDA-event timing of the CG iterations; every=k times one
+        chunk of iterations in k (the others run without event nodes)."""
+        _check(self.lib.lsh_profile_enable(self._h, max(int(every), 1) if enable else 0), "lsh_profile_enable")
 
     def profile_read(self, reset=False):
         p = _Profile()

@@ -369,7 +369,8 @@ def test_apply_fp32_scalar(shape, green):
 def test_cuda_graphs_equal_direct_launches(precision):
     """Replaying the captured graphs of check_every CG iterations gives the same
     results bit for bit as launching the kernels one by one, with and without
-    per-pass profiling, and the graphs follow a microstructure change."""
+    per-pass profiling (every chunk or one in three), and the graphs follow a
+    microstructure change."""
     phs = _batch(12, [0.2, 0.3], 80)
     h = lsh.Handle(torch.from_numpy(phs).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=precision,
                    batch=True)
@@ -384,6 +385,13 @@ def test_cuda_graphs_equal_direct_launches(precision):
     h.profile_enable(False)
     assert np.array_equal(A_p, A_g) and i_p == i_g
     assert prof["timed_iters"] > 0 and all(v > 0 for v in prof["pass_ms"].values())
+    # events in one chunk of three: the same results, fewer timed iterations
+    h.profile_enable(True, every=3)
+    A_s, i_s = h.effective(tol=1e-11, check_every=4)
+    prof_s = h.profile_read(reset=True)
+    h.profile_enable(False)
+    assert np.array_equal(A_s, A_g) and i_s == i_g
+    assert 0 < prof_s["timed_iters"] < prof["timed_iters"]
     # new microstructures in the same handle: the cached graphs are re-captured
     phs2 = _batch(12, [0.25, 0.1], 81)
     h.set_microstructure(phs2)
