@@ -151,11 +151,13 @@ typedef struct lsh_tune_report {
                      buffered, 4: 16 columns with the FFT exchange in the tile, 5: the
                      same with two components per thread; 6 register FFT in blocks
                      of 4 columns; 7 register FFT in a persistent kernel that stages
-                     the next tile's columns by asynchronous copies               */
+                     the next tile's columns by asynchronous copies; 8 register FFT
+                     in blocks of 16 columns; 9 the default register kernel loading
+                     each frequency's Gamma coefficients when it applies them      */
   float xf_ms[2]; /* measured time of one launch per candidate (-1: not available)   */
   float x_ms[4];
   float y_ms[2];
-  float z_ms[8];
+  float z_ms[10];
 } lsh_tune_report;
 
 /* Bytes of device workspace lsh_setup needs for this problem. */

@@ -63,7 +63,8 @@ template <typename T> struct OpArgs {
   // to the maps)
   int ytma;           // 1: TMA y pass
   int ztma;           // 0: register z pass; 1..5: the variant of launch_zgamma_tma; 6: register, 4 columns;
-                      // 7: persistent register z pass with staged prefetch
+                      // 7: persistent register z pass with staged prefetch; 8: register, 16 columns;
+                      // 9: register, coefficients loaded when used
   const CUtensorMap* tmy;
   const CUtensorMap* tmz;   // z boxes of 4 columns
   const CUtensorMap* tmz8;  // z boxes of 8 columns

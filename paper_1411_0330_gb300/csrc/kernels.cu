@@ -1118,7 +1118,9 @@ void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st
     if (a.ztma == 7 && launch_zgamma_regp(a, st, s)) return;
   }
   if (a.zreg) {
-    launch_zgamma_reg<T>(a, st, s, (sizeof(T) == 4 && a.ztma == 6) ? 4 : 0);
+    int tz = 0;
+    if (sizeof(T) == 4) tz = a.ztma == 6 ? 4 : a.ztma == 8 ? 16 : a.ztma == 9 ? -1 : 0;
+    launch_zgamma_reg<T>(a, st, s, tz);
     return;
   }
   dim3 g(a.S, L.grid_zx, L.grid_zy);

@@ -74,7 +74,8 @@ __global__ void __launch_bounds__(16 * RegPlan<N>::P) k_yfft_reg(OpArgs<T> a, co
 
 // ------------------------------------------------------------------ z pass + Gamma
 template <typename T, int NC, int N, int TZV = 0> struct ZCfg {
-  // TZV = 0: 8 columns per block (4 in FP64 or for length 256); else TZV columns
+  // TZV <= 0: 8 columns per block (4 in FP64 or for length 256); else TZV columns.
+  // TZV < 0: the Gamma coefficients are loaded when used, not one frequency ahead.
   static constexpr int TZ = TZV > 0 ? TZV : ((sizeof(T) == 8 || N >= 256) ? 4 : 8);
   static constexpr int W = 128 / (int)sizeof(C2<T>);  // complex values per shared wavefront
   static constexpr int KS0 = NC * TZ;
@@ -164,7 +165,9 @@ __device__ __forceinline__ void z_gamma_block(const OpArgs<T>& a, C2<T>* buf, co
 
 template <typename T, int NC, int N, int TZV>
 __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS,
-                                  (ZCfg<T, NC, N, TZV>::THREADS <= 192 && !is_df<T>::value) ? 4 : 2)
+                                  ZCfg<T, NC, N, TZV>::THREADS > 384
+                                      ? 1
+                                      : ((ZCfg<T, NC, N, TZV>::THREADS <= 192 && !is_df<T>::value) ? 4 : 2))
     k_zgamma_reg(OpArgs<T> a, const SolverState* __restrict__ st, int nrt, int nreg) {
   typedef RegLine<T, N> RL;
   typedef ZCfg<T, NC, N, TZV> ZC;
@@ -195,6 +198,16 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS,
     line_kx[i] = kx;
   }
   __syncthreads();
+  if constexpr (sizeof(T) == 4 && TZV >= 0) {
+    // the tile's Gamma rows (contiguous per z frequency) go to L2 while the
+    // forward transform runs; the first system's block asks for all systems
+    if (!a.onfly && s == 0 && tile < a.ny * nrt) {
+      constexpr int NCOP = GammaPack<NC>::NCOP;
+      for (int kz = threadIdx.x; kz < N; kz += blockDim.x)
+        bulk_prefetch_l2(a.gtab + (((long long)kz * a.ny + line_yp[0]) * a.ts + line_kx[0]) * NCOP,
+                         (uint32_t)(sizeof(T) * TZ * NCOP));
+    }
+  }
   const int i = threadIdx.x % TZ, comp = (threadIdx.x / TZ) % NC, t = threadIdx.x / (TZ * NC);
   const int yp = line_yp[i], kx = line_kx[i];
   const bool valid = yp >= 0;
@@ -213,7 +226,7 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS,
 #pragma unroll
   for (int m = 0; m < R1; ++m) buf[RL::freq(t, m) * KS + comp * TZ + i] = v[m];
   __syncthreads();
-  z_gamma_block<T, NC, N, TZ, KS>(a, buf, line_yp, line_kx);
+  z_gamma_block<T, NC, N, TZ, KS, (TZV >= 0)>(a, buf, line_yp, line_kx);
   __syncthreads();
 #pragma unroll
   for (int m = 0; m < R1; ++m) v[m] = buf[RL::freq(t, m) * KS + comp * TZ + i];
@@ -382,6 +395,10 @@ template <typename T> void launch_yfft_reg(const OpArgs<T>& a, bool inv, const S
 
 template <typename T, int NC, int N, int TZV> void launch_z_n(const OpArgs<T>& a, const SolverState* st, cudaStream_t s) {
   typedef ZCfg<T, NC, N, TZV> ZC;
+  if constexpr (ZC::THREADS > 1024 || sizeof(C2<T>) * (N + ZC::BUF) > 227 * 1024) {
+    launch_z_n<T, NC, N, 0>(a, st, s);  // too wide for one block: the default width
+    return;
+  }
   const int nrt = a.nxh / ZC::TZ, nreg = nrt * ZC::TZ;
   const int ntiles = a.ny * nrt + (a.ny * (a.nxh - nreg) + ZC::TZ - 1) / ZC::TZ;
   const size_t smem = sizeof(C2<T>) * (N + ZC::BUF);
@@ -404,11 +421,20 @@ template <typename T, int TZV> void launch_z_tz(const OpArgs<T>& a, const Solver
   else launch_z_nc<T, 2, TZV>(a, st, s);
 }
 
-// tz = 4: blocks of 4 columns (FP32 autotuner candidate); otherwise the default width
+// FP32 autotuner candidates: tz = 4 or 16 columns per block, tz < 0 the default
+// width without loading the Gamma coefficients ahead; otherwise the default width
 template <typename T> void launch_zgamma_reg(const OpArgs<T>& a, const SolverState* st, cudaStream_t s, int tz) {
   if constexpr (sizeof(T) == 4) {
     if (tz == 4) {
       launch_z_tz<T, 4>(a, st, s);
+      return;
+    }
+    if (tz == 16) {
+      launch_z_tz<T, 16>(a, st, s);
+      return;
+    }
+    if (tz < 0) {
+      launch_z_tz<T, -1>(a, st, s);
       return;
     }
   }
@@ -500,6 +526,13 @@ template <typename T, int NC, int N> void attr_z_n() {
   if constexpr (sizeof(T) == 4) {
     const int b4 = (int)(sizeof(C2<T>) * (N + ZCfg<T, NC, N, 4>::BUF));
     cudaFuncSetAttribute(k_zgamma_reg<T, NC, N, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, b4);
+    const int bn = (int)(sizeof(C2<T>) * (N + ZCfg<T, NC, N, -1>::BUF));
+    cudaFuncSetAttribute(k_zgamma_reg<T, NC, N, -1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bn);
+    typedef ZCfg<T, NC, N, 16> Z16;
+    if constexpr (Z16::THREADS <= 1024 && sizeof(C2<T>) * (N + Z16::BUF) <= 227 * 1024) {
+      const int b16 = (int)(sizeof(C2<T>) * (N + Z16::BUF));
+      cudaFuncSetAttribute(k_zgamma_reg<T, NC, N, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, b16);
+    }
   }
 }
 template <typename T, bool INV, int N> void attr_y_n() {

@@ -1604,7 +1604,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   r.z_variant = h->pf.a.ztma;
   for (int k = 0; k < 4; ++k) r.x_ms[k] = -1.f;
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
-  for (int k = 0; k < 8; ++k) r.z_ms[k] = -1.f;
+  for (int k = 0; k < 10; ++k) r.z_ms[k] = -1.f;
   const Derived& d = h->d;
   if (d.precision == LSH_MIXED) {
     PrecBufs<float>& P = h->pf;
@@ -1683,11 +1683,11 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
     }
     if (a.zreg) {
       int best = 0;
-      for (int v = 0; v < 8; ++v) {
+      for (int v = 0; v < 10; ++v) {
         if (v >= 1 && v <= 5 && !P.ztma_ok) continue;  // TMA tiles need the tensor map
         a.ztma = v;
         r.z_ms[v] = timeit([&]() {
-          if (v == 0 || v == 6) {
+          if (v == 0 || v == 6 || v == 8 || v == 9) {
             launch_zgamma<float>(a, P.L, nullptr, s);
             return true;
           }
@@ -1717,7 +1717,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
 lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
   if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 3 || y_variant < 0 || y_variant > 1 ||
-      z_variant < 0 || z_variant > 7)
+      z_variant < 0 || z_variant > 9)
     return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;
   if (h->d.precision != LSH_MIXED)
@@ -1725,7 +1725,7 @@ lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_
   if (x_variant >= 1 && !xinv_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (xf_variant == 1 && !xfwd_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;
-  if ((z_variant == 6 || z_variant == 7) && !P.a.zreg) return LSH_ERR_UNSUPPORTED;
+  if (z_variant >= 6 && !P.a.zreg) return LSH_ERR_UNSUPPORTED;
   if (z_variant == 7) {
     OpArgs<float> a = P.a;
     a.S = 0;

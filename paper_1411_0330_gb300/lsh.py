@@ -58,7 +58,7 @@ class _Opts(ctypes.Structure):
 class _TuneReport(ctypes.Structure):
     _fields_ = [("xf_variant", ctypes.c_int), ("x_variant", ctypes.c_int), ("y_variant", ctypes.c_int),
                 ("z_variant", ctypes.c_int), ("xf_ms", ctypes.c_float * 2), ("x_ms", ctypes.c_float * 4),
-                ("y_ms", ctypes.c_float * 2), ("z_ms", ctypes.c_float * 8)]
+                ("y_ms", ctypes.c_float * 2), ("z_ms", ctypes.c_float * 10)]
 
 
 class _Info(ctypes.Structure):

@@ -450,7 +450,7 @@ def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkey
     h_reg = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=1, precision=lsh.MIXED)
     y_reg = h_reg.apply(xt)
     assert rel(y_reg.cpu().numpy(), oracle.apply(P, x)) < 2e-5
-    for zv in range(8):
+    for zv in range(10):
         try:
             h_tma.set_variants(0, 0, 1, zv)
         except lsh.LSHError as e:
@@ -468,7 +468,7 @@ def test_fp32_tma_passes_match_register_passes_and_oracle(shape, physics, monkey
         y_x = h_tma.apply(xt)
         assert rel(y_x.cpu().numpy(), oracle.apply(P, x)) < 2e-5, (xf, xv)
     rep = h_tma.autotune()
-    assert rep["z_variant"] in range(8) and rep["y_variant"] in (0, 1) and rep["x_variant"] in (0, 1, 2, 3)
+    assert rep["z_variant"] in range(10) and rep["y_variant"] in (0, 1) and rep["x_variant"] in (0, 1, 2, 3)
     assert rep["xf_variant"] in (0, 1)
     assert rel(h_tma.apply(xt).cpu().numpy(), oracle.apply(P, x)) < 2e-5
 
