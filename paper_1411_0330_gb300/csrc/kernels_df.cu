@@ -158,40 +158,55 @@ __global__ void __launch_bounds__(128) k_df_xinv(OpArgs<double> a, const DF2* __
   RL::inv_a(v, t, tw, exl);
   __syncthreads();
   RL::inv_b(v, t, tw, exl);
-  // v[j] = (g of row 2l, g of row 2l + 1) at x = t + P j
-  const DF loaddf = MODE == 2 ? df_from(a.loads[s * 6 + comp]) : DF(0.f, 0.f);
-  float acc_s = 0.f, acc_c = 0.f;  // compensated (r, r) of this thread
+  // v[j] = (g of row 2l, g of row 2l + 1) at x = t + P j; through shared memory
+  // (rows padded by 4 values: conflict-free) to an epilogue whose global
+  // accesses run along the rows
+  constexpr int GS = N + 4;
+  static_assert(RY * GS <= XC::EXN * 2, "g rows fit in the exchange area");
+  DF* G = reinterpret_cast<DF*>(ex);
+  __syncthreads();  // every thread has read the exchange area
 #pragma unroll
   for (int j = 0; j < R1; ++j) {
-    const int x = t + P * j;
+    G[(2 * l) * GS + t + P * j] = v[j].x;
+    G[(2 * l + 1) * GS + t + P * j] = v[j].y;
+  }
+  __syncthreads();
+  const DF loaddf = MODE == 2 ? df_from(a.loads[s * 6 + comp]) : DF(0.f, 0.f);
+  float acc_s = 0.f, acc_c = 0.f;  // compensated (r, r) of this thread
+  constexpr int NP = N / 2;         // element pairs per row
+  for (int e = threadIdx.x; e < RY * NP; e += XC::THREADS) {
+    const int rowl = e / NP, x = 2 * (e - rowl * NP);
+    const long long vox = vox0 + (long long)rowl * N + x;
+    const long long gi = (row0 + rowl) * N + x;
+    const double2 xv = *reinterpret_cast<const double2*>(xin + gi);
+    const uchar2 ph = *reinterpret_cast<const uchar2*>(a.phase + pbase + vox);
+    DF o[2];
 #pragma unroll
     for (int h2 = 0; h2 < 2; ++h2) {
-      const long long rowl = 2 * l + h2;
-      const long long vox = vox0 + rowl * N + x;
-      const long long gi = (row0 + rowl) * N + x;
-      const int p = a.phase[pbase + vox];
-      DF o(0.f, 0.f);
+      const int p = h2 == 0 ? ph.x : ph.y;
+      o[h2] = DF(0.f, 0.f);
       if (aloc[p]) {
         DF m = mloc[p * a.c + comp];
         if (a.scale) {  // per-voxel moduli: M in FP64, then split
-          const double fr = (double)a.scale[pbase + vox];
+          const double fr = (double)a.scale[pbase + vox + h2];
           const double m0 = a.mtab[comp], m1 = a.mtab[a.c + comp], mp = a.modtab[p * a.c + comp];
           m = df_from(a.frac ? fr * m1 + (1.0 - fr) * m0  // Eq. (def_ah)
                              : 1.0 / (fr * mp - a.ref[comp]));
         }
-        const DF g = h2 == 0 ? v[j].x : v[j].y;
-        o = m * df_split(xin[gi]) + g;
-        if (MODE == 2) {
-          o = loaddf - o;
-          const float y = __fsub_rn(__fmul_rn(o.h, o.h), acc_c);
+        const DF mx = m * df_split(h2 == 0 ? xv.x : xv.y) + G[rowl * GS + x + h2];
+        if (MODE == 0) {
+          o[h2] = mx;
+        } else {
+          o[h2] = loaddf - mx;
+          const float y = __fsub_rn(__fmul_rn(o[h2].h, o[h2].h), acc_c);
           const float tt = __fadd_rn(acc_s, y);
           acc_c = __fsub_rn(__fsub_rn(tt, acc_s), y);
           acc_s = tt;
         }
       }
-      if (MODE == 0) out[gi] = df_to(o);
-      else reinterpret_cast<float2*>(out)[gi] = make_float2(o.h, o.l);
     }
+    if (MODE == 0) *reinterpret_cast<double2*>(out + gi) = make_double2(df_to(o[0]), df_to(o[1]));
+    else *reinterpret_cast<float4*>(out + gi) = make_float4(o[0].h, o[0].l, o[1].h, o[1].l);
   }
   if (MODE == 2) {
     Acc<float> acc;
