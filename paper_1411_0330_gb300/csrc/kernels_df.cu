@@ -62,17 +62,27 @@ __global__ void __launch_bounds__(128) k_df_xfwd(OpArgs<double> a, const DF2* __
   const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V;
   const long long vox0 = (long long)(rloc - comp * rows_per_comp) * N;
   __syncthreads();
+  // P x into padded shared rows with row-contiguous 16-byte loads (the FP64
+  // pipe converts: it has room in this pass)
+  constexpr int GS = N + 4, NP = N / 2;
+  static_assert(RY * GS <= XC::EXN * 2, "rows fit in the exchange area");
+  DF* G = reinterpret_cast<DF*>(ex);
+  for (int e = threadIdx.x; e < RY * NP; e += XC::THREADS) {
+    const int rowl = e / NP, x = 2 * (e - rowl * NP);
+    const double2 xv = *reinterpret_cast<const double2*>(in + (row0 + rowl) * N + x);
+    const uchar2 ph = *reinterpret_cast<const uchar2*>(a.phase + pbase + vox0 + (long long)rowl * N + x);
+    G[rowl * GS + x] = aloc[ph.x] ? df_from(xv.x) : DF(0.f, 0.f);
+    G[rowl * GS + x + 1] = aloc[ph.y] ? df_from(xv.y) : DF(0.f, 0.f);
+  }
+  __syncthreads();
   const int t = threadIdx.x % P, l = threadIdx.x / P;
-  const double* xa = in + (row0 + 2 * l) * N;
-  const unsigned char* pa = a.phase + pbase + vox0 + (long long)(2 * l) * N;
   DF2 v[R1];
 #pragma unroll
   for (int j = 0; j < R1; ++j) {
-    const int x = t + P * j;
-    // the FP64 pipe has room here (measured faster than the integer split)
-    v[j].x = aloc[pa[x]] ? df_from(xa[x]) : DF(0.f, 0.f);
-    v[j].y = aloc[pa[N + x]] ? df_from(xa[N + x]) : DF(0.f, 0.f);
+    v[j].x = G[(2 * l) * GS + t + P * j];
+    v[j].y = G[(2 * l + 1) * GS + t + P * j];
   }
+  __syncthreads();  // the rows become the exchange area
   DF2* exl = ex + l * XC::LS;
   RL::fwd_a(v, t, tw, exl);
   __syncthreads();
