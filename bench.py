@@ -781,7 +781,7 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = oracle_sample(ph, mods, iters=2)
+        cpu = oracle_sample(ph, mods, iters=20)  # about 10 s on 16 host cores
 
     if rank == 0:
         cfg = config(nsph, float(ph.mean()))
