@@ -180,8 +180,10 @@ lsh_status lsh_set_microstructure(lsh_handle *h, const unsigned char *phase, con
 /* y = K x with K = P (M + Gamma) P the operator of Eq. (13) (M_beta =
  * (A_beta - A0)^{-1} of Eq. (7), P the projection on I0: values of x off I0
  * are ignored and y is zero there), for every microstructure of the batch.
- * x, y: device, nbatch*c*V elements of `dtype` (LSH_F64, or LSH_F32 for
- * LSH_MIXED handles), layout [nbatch][c][n2][n1][n0].  Asynchronous. */
+ * x, y: device, nbatch*c*V elements of `dtype` (LSH_F64; LSH_F32 for
+ * LSH_MIXED handles; LSH_F64_DF, FP64 fields evaluated in double-float, for
+ * LSH_MIXED handles of the grids listed at LSH_F64_DF -- else
+ * LSH_ERR_UNSUPPORTED), layout [nbatch][c][n2][n1][n0].  Asynchronous. */
 lsh_status lsh_apply(lsh_handle *h, int dtype, const void *x, void *y);
 
 /* Solve Eq. (13) for one macroscopic load p (host, c doubles; Mandel
