@@ -147,6 +147,7 @@ bool df_supported(const OpArgs<double>& a);
 void launch_d2df(const double* in, DF* out, long long n, cudaStream_t s);
 void launch_df_x(const OpArgs<double>& a, const DF2* twx, int mode, const double* in, double* out, SolverState* st,
                  double* partials, cudaStream_t s);
+void launch_df_z(const OpArgs<DF>& a, cudaStream_t s);
 void df_prepare();
 bool encode_z_map(CUtensorMap* out, void* H, int hs, int ny, int nz, int c, long long nsys, int tz);
 void tma_prepare();

@@ -5,8 +5,13 @@
 // emulated-FP64 apply; on GB300 it runs several times faster than the same
 // passes in native FP64, whose pipe issues 1/64 of the FP32 rate.
 //
-// The y and z passes are the register-FFT kernels of kernels_reg.cu
-// instantiated for DF (the Gamma^h table converted once to double-float).
+// The y pass is the register-FFT kernel of kernels_reg.cu instantiated for DF.
+// The z pass runs as three launches: the z transform, the Gamma^h product
+// (one thread per frequency, its coefficients read once for all systems),
+// the inverse z transform: one fused kernel holding the double-float 6 x 6
+// product and both transforms needed 168 registers and missed the
+// instruction cache (1.64 ms against 0.39 + 0.42 + 0.40 ms for the three at
+// 128^3 with 6 systems).
 // The x passes below read and write FP64: a block owns RY consecutive rows of
 // one system, two real rows form one complex line of N points held by P
 // threads (two-level register FFT, regfft.cuh).
@@ -20,6 +25,7 @@
 #include "common.cuh"
 #include "df.cuh"
 #include "fft.cuh"
+#include "gamma_onfly.cuh"
 #include "internal.h"
 #include "regfft.cuh"
 
@@ -232,6 +238,112 @@ __global__ void __launch_bounds__(128) k_df_xinv(OpArgs<double> a, const DF2* __
   }
 }
 
+// z transform (INV: inverse) of the double-float half spectrum: a block owns
+// 16 consecutive kx columns at one (system, component, y); the columns left
+// over when nx/2+1 is not a multiple of 16 are gathered 16 at a time.
+template <bool INV, int N>
+__global__ void __launch_bounds__(16 * RegPlan<N>::P) k_df_zfft(OpArgs<DF> a, int nrt, int nreg) {
+  typedef RegLine<DF, N> RL;
+  constexpr int TZ = 16, P = RL::P, R1 = RL::R1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DF2* tw = reinterpret_cast<DF2*>(smem_raw);
+  DF2* ex = tw + N;
+  for (int u = threadIdx.x; u < N; u += blockDim.x) tw[u] = a.twz[u];
+  const int i = threadIdx.x % TZ, t = threadIdx.x / TZ;
+  const long long nplanes = (long long)a.S * a.c * a.ny;  // (system, component, y)
+  const int nleft = a.nxh - nreg;
+  long long plane;
+  int kx;
+  bool valid = true;
+  if ((long long)blockIdx.x < nplanes * nrt) {
+    plane = blockIdx.x / nrt;
+    kx = (int)(blockIdx.x - plane * nrt) * TZ + i;
+  } else {
+    const long long l = (blockIdx.x - nplanes * nrt) * (long long)TZ + i;
+    valid = l < nplanes * nleft;
+    plane = valid ? l / nleft : 0;
+    kx = valid ? nreg + (int)(l - plane * nleft) : 0;
+  }
+  const long long sc = plane / a.ny, yp = plane - sc * a.ny;
+  DF2* __restrict__ Hl = a.H + (sc * a.nz * a.ny + yp) * a.hs + kx;
+  const long long rs = (long long)a.ny * a.hs;  // z stride
+  DF2 v[R1];
+  __syncthreads();
+  if (!INV) {
+#pragma unroll
+    for (int j = 0; j < R1; ++j) v[j] = valid ? Hl[(t + P * j) * rs] : DF2{DF(0.f, 0.f), DF(0.f, 0.f)};
+    RL::fwd_a(v, t, tw, ex + i * RL::LS);
+    __syncthreads();
+    RL::fwd_b(v, t, tw, ex + i * RL::LS);
+    if (valid) {
+#pragma unroll
+      for (int m = 0; m < R1; ++m) Hl[RL::freq(t, m) * rs] = v[m];
+    }
+  } else {
+#pragma unroll
+    for (int m = 0; m < R1; ++m) v[m] = valid ? Hl[RL::freq(t, m) * rs] : DF2{DF(0.f, 0.f), DF(0.f, 0.f)};
+    RL::inv_a(v, t, tw, ex + i * RL::LS);
+    __syncthreads();
+    RL::inv_b(v, t, tw, ex + i * RL::LS);
+    if (valid) {
+#pragma unroll
+      for (int j = 0; j < R1; ++j) Hl[(t + P * j) * rs] = v[j];
+    }
+  }
+}
+
+// Gamma^h_k applied to the NC components of every system at each frequency
+// (natural z and y order); a thread reads its frequency's coefficients once.
+template <int NC> __global__ void __launch_bounds__(256) k_df_gamma(OpArgs<DF> a) {
+  const long long nfr = (long long)a.nz * a.ny * a.nxh;
+  const long long cstride = (long long)a.nz * a.ny * a.hs;  // one component plane
+  for (long long f = blockIdx.x * 256ll + threadIdx.x; f < nfr; f += (long long)gridDim.x * 256) {
+    const long long r = f / a.nxh;  // z position * ny + y position
+    const int kx = (int)(f - r * a.nxh);
+    DF gc[GammaPack<NC>::NCO];
+    gamma_coef_load<DF, NC>(a.gtab, r * a.ts + kx, gc);
+    for (int s = 0; s < a.S; ++s) {
+      DF2* h = a.H + (long long)s * NC * cstride + r * a.hs + kx;
+      DF2 v[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) v[c] = h[c * cstride];
+      gamma_coef_apply<DF, NC>(gc, v);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) h[c * cstride] = v[c];
+    }
+  }
+}
+
+template <int N> size_t df_z_smem() { return sizeof(DF2) * (size_t)(N + 16 * RegLine<DF, N>::LS); }
+
+template <bool INV, int N> void launch_df_zfft_n(const OpArgs<DF>& a, cudaStream_t s) {
+  constexpr int TZ = 16;
+  const int nrt = a.nxh / TZ, nreg = nrt * TZ;
+  const long long nplanes = (long long)a.S * a.c * a.ny;
+  const long long grid = nplanes * nrt + (nplanes * (a.nxh - nreg) + TZ - 1) / TZ;
+  k_df_zfft<INV, N><<<(unsigned)grid, TZ * RegPlan<N>::P, df_z_smem<N>(), s>>>(a, nrt, nreg);
+}
+
+template <bool INV> void launch_df_zfft(const OpArgs<DF>& a, cudaStream_t s) {
+  switch (a.nz) {
+    case 16: launch_df_zfft_n<INV, 16>(a, s); break;
+    case 32: launch_df_zfft_n<INV, 32>(a, s); break;
+    case 64: launch_df_zfft_n<INV, 64>(a, s); break;
+    case 128: launch_df_zfft_n<INV, 128>(a, s); break;
+    default: launch_df_zfft_n<INV, 256>(a, s); break;
+  }
+}
+
+// the z pass with Gamma^h in double-float: three launches
+void launch_df_z(const OpArgs<DF>& a, cudaStream_t s) {
+  launch_df_zfft<false>(a, s);
+  const long long nfr = (long long)a.nz * a.ny * a.nxh;
+  const unsigned g = (unsigned)std::min<long long>((nfr + 255) / 256, 152ll * 8);
+  if (a.c == 6) k_df_gamma<6><<<g, 256, 0, s>>>(a);
+  else k_df_gamma<3><<<g, 256, 0, s>>>(a);
+  launch_df_zfft<true>(a, s);
+}
+
 bool df_length(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
 
 // The double-float passes cover 3D grids whose three lengths have register
@@ -271,6 +383,9 @@ void launch_df_x(const OpArgs<double>& a, const DF2* twx, int mode, const double
 }
 
 template <int N> void df_attrs_n() {
+  const int zb = (int)df_z_smem<N>();
+  cudaFuncSetAttribute(k_df_zfft<false, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, zb);
+  cudaFuncSetAttribute(k_df_zfft<true, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, zb);
   const int bytes = (int)XDf<N>::SMEM;
   cudaFuncSetAttribute(k_df_xfwd<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   cudaFuncSetAttribute(k_df_xinv<0, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);

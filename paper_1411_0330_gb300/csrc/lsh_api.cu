@@ -775,10 +775,10 @@ lsh_status apply_df(lsh_handle* h, const OpArgs<double>& a, const double* in, do
   const OpArgs<DF> b = df_args(h, a);
   launch_df_x(a, b.twx, -1, in, nullptr, nullptr, nullptr, s);
   launch_yfft_reg<DF>(b, false, nullptr, s);
-  launch_zgamma_reg<DF>(b, nullptr, s, 0);
+  launch_df_z(b, s);
   launch_yfft_reg<DF>(b, true, nullptr, s);
   launch_df_x(a, b.twx, 0, in, out, nullptr, nullptr, s);
-  h->launches += 5;
+  h->launches += 7;
   return last_launch();
 }
 
@@ -793,10 +793,10 @@ lsh_status residual64(lsh_handle* h, const OpArgs<double>& a, const double* x, d
     const OpArgs<DF> b = df_args(h, a);
     launch_df_x(a, b.twx, -1, x, nullptr, nullptr, nullptr, s);
     launch_yfft_reg<DF>(b, false, nullptr, s);
-    launch_zgamma_reg<DF>(b, nullptr, s, 0);
+    launch_df_z(b, s);
     launch_yfft_reg<DF>(b, true, nullptr, s);
     launch_df_x(a, b.twx, 2, x, r, sres, h->partials, s);
-    h->launches += 5;
+    h->launches += 7;
     return last_launch();
   }
   launch_xfwd<double>(a, P.L, 0, x, nullptr, nullptr, nullptr, nullptr, s);
