@@ -556,9 +556,11 @@ template <typename T, bool INV> void attr_y() {
 template <typename T> void set_smem_attrs_reg() {
   attr_y<T, false>();
   attr_y<T, true>();
-  attr_z_nc<T, 2>();
-  attr_z_nc<T, 3>();
-  attr_z_nc<T, 6>();
+  if constexpr (!is_df<T>::value) {  // the double-float z pass has kernels of its own
+    attr_z_nc<T, 2>();
+    attr_z_nc<T, 3>();
+    attr_z_nc<T, 6>();
+  }
   if constexpr (sizeof(T) == 4) {
     zp_prepare<2>();
     zp_prepare<3>();
@@ -574,6 +576,5 @@ template void launch_yfft_reg<float>(const OpArgs<float>&, bool, const SolverSta
 template void launch_zgamma_reg<double>(const OpArgs<double>&, const SolverState*, cudaStream_t, int);
 template void launch_zgamma_reg<float>(const OpArgs<float>&, const SolverState*, cudaStream_t, int);
 template void launch_yfft_reg<DF>(const OpArgs<DF>&, bool, const SolverState*, cudaStream_t);
-template void launch_zgamma_reg<DF>(const OpArgs<DF>&, const SolverState*, cudaStream_t, int);
 
 }  // namespace lsh
