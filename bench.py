@@ -150,7 +150,7 @@ def pass_flops(kind, V, c, nx, ny, nz, nxh):
 
 # DRAM bytes (read + write) of one launch of each FP32 pass over the 6 load
 # systems of the 128^3 workload, from the ncu captures summarised in
-# profiles/fp32_passes_128cube_six_systems.md (filtered operator); to be
+# the FP32-pass summary under profiles/ (filtered operator); to be
 # retaken whenever one of these kernels changes.
 PROF_EVERY = 8  # per-pass events in one CG chunk of this many
 

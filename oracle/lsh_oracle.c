@@ -12,7 +12,7 @@
  * compensated summation.  Loops over independent frequencies / voxels may run
  * under OpenMP; every reduction is serial so results are reproducible.
  *
- * Readings of points the paper leaves open (each also listed in the design doc):
+ * Readings of points the paper leaves open:
  *  - DFT^{-1} carries the factor 1/N^d (forced by Eqs. (8) and (10)).
  *  - Truncated operator, even N: every k with some k_i = N_i/2 gets A0^{-1}
  *    (Sec. 3.2.1, last paragraph); for elasticity this is C0^{-1}.
