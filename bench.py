@@ -148,12 +148,12 @@ def pass_flops(kind, V, c, nx, ny, nz, nxh):
     raise KeyError(kind)
 
 
-# DRAM bytes (read + write) of one launch of each FP32 pass over the 6 load
-# systems of the 128^3 workload, from the ncu captures summarised in
-# the FP32-pass summary under profiles/ (filtered operator); to be
-# retaken whenever one of these kernels changes.
 PROF_EVERY = 8  # per-pass events in one CG chunk of this many
 
+# DRAM bytes (read + write) of one launch of each FP32 pass over the 6 load
+# systems of the 128^3 workload, from the ncu captures in the FP32-pass
+# summary under profiles/ (filtered operator); to be retaken whenever one of
+# these kernels changes.
 NCU_TRAFFIC_FP32 = {"x_forward": 1770.9e6, "y_forward": 588.4e6, "z_gamma": 829.8e6, "y_inverse": 587.6e6,
                     "x_inverse_local": 902.0e6, "cg_update": 862.9e6}
 
