@@ -7,6 +7,8 @@ independent dense direct solve of Eq. (12), bounds, and a finite-difference
 derivative.  A plausible slip anywhere (sign, 1/N^d, transposed operand,
 dropped filter term, wrong Nyquist rule) fails at least one of them.
 """
+import os
+
 import numpy as np
 import pytest
 
@@ -456,3 +458,30 @@ def test_uniform_fraction_gives_the_averaged_uniform_medium(oracle_mod, physics)
                            frac=np.full(shape, f))
     A, _ = oracle_mod.effective(P, tol=1e-14)
     assert np.allclose(A, expected, rtol=1e-12, atol=1e-12)
+
+
+def _golden_rows(name):
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", name)
+    rows = {}
+    for line in open(path):
+        line = line.split("#")[0].split()
+        if line:
+            rows[line[0]] = [float(v) for v in line[1:]]
+    return rows
+
+
+def test_default_reference_reproduces_the_papers_reference_medium(oracle_mod):
+    """Sec. 5's table of mechanical parameters (tests/golden/sec5_mechanical_parameters.txt):
+    from the matrix and inclusion entries, the default reference rule gives the table's
+    reference medium (mu0 = mu_m / 2, nu0 = 0.3)."""
+    rows = _golden_rows("sec5_mechanical_parameters.txt")
+
+    def k_of(mu, nu):  # bulk modulus of an isotropic medium
+        return 2.0 * mu * (1.0 + nu) / (3.0 * (1.0 - 2.0 * nu))
+
+    moduli = np.array([[k_of(*rows["matrix"]), rows["matrix"][0]],
+                       [k_of(*rows["inclusions"]), rows["inclusions"][0]]])
+    K0, mu0 = oracle_mod.default_reference(3, oracle_mod.ELASTIC, moduli)
+    mu_ref, nu_ref = rows["reference"]
+    assert abs(mu0 - mu_ref) < 1e-14
+    assert abs(K0 - k_of(mu_ref, nu_ref)) < 1e-13
