@@ -69,7 +69,8 @@ enum { LSH_FP64 = 0, LSH_MIXED = 1 };
  * operator evaluated in double-float arithmetic (pairs of FP32 values, 48
  * significant bits) on the FP32 pipes -- the arithmetic of the mixed solver's
  * refinement residual; LSH_MIXED handles on 3D grids of lengths 16..256
- * (powers of two), truncated or filtered operator, 3 or 6 components. */
+ * (powers of two), truncated or filtered operator, 3 or 6 components, no
+ * scale or fraction field. */
 enum { LSH_F64 = 0, LSH_F32 = 1, LSH_F64_DF = 2 };
 /* AUTO: CG when every active phase has A_phase - A0 of one sign (K definite),
  * MINRES (Paige-Saunders, FP64) when the signs differ (K indefinite, e.g. the

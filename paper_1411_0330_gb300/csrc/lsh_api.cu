@@ -386,10 +386,11 @@ bool reg_len(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 2
 
 // The mixed solver's iterative-refinement residual runs in double-float
 // arithmetic (kernels_df.cu) on 3D grids whose lengths have register-FFT
-// plans, for tabulated operators without finite-difference phases.
+// plans, for tabulated operators without finite-difference phases and phase
+// maps without per-voxel scale or fraction fields (those keep the FP64 residual).
 bool df_eligible(const Derived& d) {
   return d.precision == LSH_MIXED && d.dim == 3 && reg_len(d.nx) && reg_len(d.ny) && reg_len(d.nz) &&
-         d.green != LSH_GREEN_FD && (d.c == 3 || d.c == 6);
+         d.green != LSH_GREEN_FD && (d.c == 3 || d.c == 6) && !d.has_scale;
 }
 
 Layout make_layout(const Derived& d) {
