@@ -103,3 +103,61 @@ def test_product_sources_do_not_use_the_oracle():
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
                 assert "lsh_oracle" not in txt, f
+
+
+def header_constants():
+    """name -> value of every enumerator in include/lsh.h."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "lsh.h")).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(LSH_[A-Z0-9_]+)\s*=\s*(\d+)", src)}
+
+
+def test_binding_constants_match_the_header():
+    """Every constant of the binding has the value of the header's enumerator of the same name
+    (LSH_ prefix; the physics and Green-operator families drop their middle word)."""
+    h = header_constants()
+    alias = {"ELASTIC": "LSH_ELASTIC_ISO", "TRUNCATED": "LSH_GREEN_TRUNCATED", "FILTERED": "LSH_GREEN_FILTERED",
+             "FD": "LSH_GREEN_FD"}
+    names = ["OK", "ERR_INVALID_ARG", "ERR_UNSUPPORTED_SIZE", "ERR_REFERENCE_INDEFINITE", "ERR_SINGULAR_CONTRAST",
+             "ERR_BREAKDOWN", "ERR_NOT_CONVERGED", "ERR_WORKSPACE", "ERR_CUDA", "ERR_UNSUPPORTED", "SCALAR",
+             "ELASTIC", "TRUNCATED", "FILTERED", "FD", "FP64", "MIXED", "F64", "F32", "F64_DF", "SOLVER_AUTO",
+             "SOLVER_CG", "SOLVER_MINRES", "SOLVER_BASIC"]
+    for n in names:
+        assert getattr(lsh, n) == h[alias.get(n, "LSH_" + n)], n
+
+
+def header_struct_fields(name):
+    """(field name, array length, kind) of `typedef struct <name> { ... }` in include/lsh.h,
+    in order; kind is int, float, double, longlong or ptr."""
+    src = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "lsh.h")).read(), flags=re.S)
+    body = re.search(r"typedef struct " + name + r"\s*\{(.*?)\}", src, flags=re.S).group(1)
+    types = {"const", "unsigned", "signed", "char", "short", "int", "long", "float", "double", "size_t"}
+    out = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        words = decl.replace("*", " * ").replace(",", " , ").split()
+        base = [w for w in words if w in types]
+        kind = "longlong" if base.count("long") == 2 else next((k for k in ("double", "float") if k in base), "int")
+        for item in " ".join(w for w in words if w not in types).split(","):
+            m = re.match(r"\s*(\*?)\s*(\w+)\s*(?:\[(\d+)\])?", item)
+            out.append((m.group(2), int(m.group(3)) if m.group(3) else 1, "ptr" if m.group(1) else kind))
+    return out
+
+
+def _ctypes_kind(t):
+    t = getattr(t, "_type_", t) if hasattr(t, "_length_") else t
+    if t is ctypes.c_void_p or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    return {ctypes.c_int: "int", ctypes.c_float: "float", ctypes.c_double: "double",
+            ctypes.c_longlong: "longlong"}[t]
+
+
+@pytest.mark.parametrize("cname,pyname", [("lsh_problem", "_Problem"), ("lsh_solve_opts", "_Opts"),
+                                          ("lsh_solve_info", "_Info"), ("lsh_tune_report", "_TuneReport"),
+                                          ("lsh_profile", "_Profile")])
+def test_binding_structs_match_the_header(cname, pyname):
+    """The ctypes mirrors of the ABI structs have the header's fields, in order, with the
+    same array lengths and element kinds (a drift would shift every later field)."""
+    py = [(n, getattr(t, "_length_", 1), _ctypes_kind(t)) for n, t in getattr(lsh, pyname)._fields_]
+    assert py == header_struct_fields(cname)
