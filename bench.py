@@ -2,23 +2,26 @@
 """Throughput of the Lippmann-Schwinger corrector solve on GB300.
 
 Metric: voxel-CG-iterations per second of the mixed-precision batched solver
-against the plain FP64 solver.  One step computes the full 6x6 effective
-stiffness C* of a 128^3 two-phase elastic sphere packing (radius 8 voxels,
-volume fraction 0.3, seed 1411; matrix E=1 nu=0.3, inclusions E=10 nu=0.2;
-reference medium mu0 = mu_min/2, nu0 = 0.3) once with the filtered and once
-with the truncated Green operator: 12 solves to relative residual 1e-10, the
-6 loads of each operator batched into one launch sequence.  `value` counts
-N^3 x the CG iterations the plain FP64 solver needs for the same 12 solves,
-divided by the mixed solver's device time (an accuracy-fair count; the raw
-inner-iteration rate and the FP64 solver's own rate are reported beside it).
+against the plain FP64 solver, at C* agreeing to 1e-8.  The default workload
+is the batched one: 64 seeded two-phase elastic sphere microstructures whose
+grids are drawn from {32, 48, 64, 96, 128}^3 (volume fractions U(0.1, 0.4),
+radius N/16 voxels, contrast 10), 6 Mandel loads each (384 systems), one batch
+handle per grid with all of that grid's microstructures x loads in the same
+launches; one step computes all 64 effective tensors C* to relative residual
+1e-10.  `value` counts N^3 x the CG iterations the plain FP64 solver needs for
+the same systems, divided by the mixed solver's device time (an accuracy-fair
+count; the raw inner-iteration rate and the FP64 solver's own rate are
+reported beside it).
 
-Also reported: an end-to-end number through the C ABI with the phase map in
-pinned host memory (host->device copy and the C* readback inside the timed
-region), the C* error of the mixed solver against the FP64 one, the roofline
-of the dominant FP32 pass (per-pass CUDA events recorded live on the solve
-stream), the GPU clocks sampled during the timed region, and the FP64 CPU
-oracle timed on a bounded sample.
+Also reported: an end-to-end number through the public API with the phase
+maps in pinned host memory (host->device copies and the C* readback inside
+the timed region), the C* error of the mixed solver against the FP64 one, the
+roofline of the dominant FP32 pass (per-pass CUDA events recorded live on the
+solve stream), the GPU clocks sampled during the timed region, and the FP64
+CPU oracle timed on a bounded sample of the same workload.
 
+Other workloads (--workload): spheres128 (one 128^3 packing, filtered and
+truncated operators), contrast256, gradient128, convergence, cufft.
 --impl reference times the CPU oracle alone (the reference arm).
 Multi-GPU (torchrun): every rank solves its own copy of the workload
 (independent replicas, no data-path collective); value = all voxel-iterations
@@ -152,12 +155,23 @@ PROF_EVERY = 8  # per-pass events in one CG chunk of this many
 
 # DRAM bytes (read + write) of one launch of each FP32 pass over the 6 load
 # systems of the 128^3 workload, from the ncu captures in the FP32-pass
-# summary under profiles/ (filtered operator); to be retaken whenever one of
-# these kernels changes.
-# z_gamma: None, the kernel gained its Gamma-row L2 prefetch after the capture
-# (829.8 MB before it).
-NCU_TRAFFIC_FP32 = {"x_forward": 1770.9e6, "y_forward": 588.4e6, "z_gamma": None, "y_inverse": 587.6e6,
-                    "x_inverse_local": 902.0e6, "cg_update": 862.9e6}
+# summary under profiles/ (filtered operator), with the algorithmic bytes of
+# the same launch; to be retaken whenever one of these kernels changes (None:
+# not captured for the current kernel).
+NCU_TRAFFIC_FP32 = {"x_forward": None, "y_forward": None, "z_gamma": None, "y_inverse": None,
+                    "x_inverse_local": None, "cg_update": None}
+NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch over 6 systems at 128^3 "
+                      "(filtered), scaled to the batch's average launch by its algorithmic bytes")
+
+
+def ncu_traffic_per_launch(kind, alg_bytes_per_launch):
+    """DRAM traffic of an average batch launch of `kind`: the 128^3 capture's ratio of DRAM
+    to algorithmic bytes times the batch launch's algorithmic bytes (None without a capture)."""
+    t = NCU_TRAFFIC_FP32.get(kind)
+    if t is None:
+        return None
+    alg = 6 * pass_traffic(kind, N ** 3, 6, N, N // 2 + 1, 0, 4) + batch_pass_bytes(kind, N)[1]
+    return t / alg * alg_bytes_per_launch
 
 
 def load_peaks():
@@ -170,8 +184,8 @@ def load_peaks():
 
 # ----------------------------------------------------------------- CPU oracle sample
 def oracle_sample(ph, mods, iters=2):
-    """The FP64 CPU oracle, as it stands, on a bounded sample of the workload:
-    `iters` CG iterations of one 128^3 solve (filtered Gamma, shear load)."""
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the 128^3
+    workload: `iters` CG iterations of one filtered solve (shear load)."""
     import oracle
     oracle.build()
     P = oracle.Problem(ph, mods, physics=oracle.ELASTIC, green=oracle.FILTERED)
@@ -184,29 +198,71 @@ def oracle_sample(ph, mods, iters=2):
         if e.code != 5:  # not converged is expected for a bounded sample
             raise
     dt = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": ph.size * iters / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+    return {"value": ph.size * iters / dt, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
             "sample": f"{iters} CG iterations of one {N}^3 filtered solve (shear load), {dt:.1f} s"}
+
+
+def oracle_cores():
+    """Threads the oracle's OpenMP loops use."""
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def batch_sample(phases, meta):
+    """One microstructure of each grid of the batch (the first one drawn)."""
+    picks = {}
+    for ph, m in zip(phases, meta):
+        picks.setdefault(m["n"], ph)
+    return [picks[n] for n in sorted(picks)]
+
+
+def oracle_batch_sample(sample, mods, iters):
+    """The FP64 CPU oracle, as it stands, on a bounded sample of the batched
+    workload: `iters` CG iterations of one filtered solve (shear load) of one
+    microstructure per grid size.  Returns (voxel-iterations, seconds)."""
+    import oracle
+    oracle.build()
+    load = np.zeros(6)
+    load[5] = 1.0
+    units, t0 = 0, time.perf_counter()
+    for ph in sample:
+        P = oracle.Problem(ph, mods, physics=oracle.ELASTIC, green=oracle.FILTERED)
+        try:
+            oracle.solve(P, load, tol=1e-30, maxit=iters, solver=oracle.SOLVER_CG)
+        except oracle.OracleError as e:
+            if e.code != 5:  # not converged is expected for a bounded sample
+                raise
+        units += ph.size * iters
+    return units, time.perf_counter() - t0
+
+
+def batch_sample_text(sample, iters):
+    grids = "/".join(str(p.shape[0]) for p in sample)
+    return f"{iters} CG iterations of one filtered solve (shear load) of one microstructure per grid ({grids})^3"
 
 
 # ----------------------------------------------------------------- reference arm
 def run_reference(args, rank, world):
+    """The FP64 CPU oracle on the batched workload's sample: each step is one CG
+    iteration of one microstructure per grid size; W such steps first, untimed."""
     if rank != 0:
         return 0
-    ph, mods, nsph = workload()
-    for _ in range(args.warmup if args.warmup < 1 else 1):
-        pass
-    vals = []
+    phases, meta = batch64_inputs()
+    mods = np.array([k_mu(1.0, 0.3), k_mu(10.0, 0.2)])
+    sample = batch_sample(phases, meta)
+    for _ in range(args.warmup):
+        oracle_batch_sample(sample, mods, 1)
+    units, secs = 0, 0.0
     for _ in range(args.steps):
-        vals.append(oracle_sample(ph, mods, iters=1))
-    v = float(np.median([x["value"] for x in vals]))
-    cb = dict(vals[0])
-    cb["value"] = v
-    cb["sample"] = f"1 CG iteration of one {N}^3 filtered solve per step, {args.steps} steps"
+        u, dt = oracle_batch_sample(sample, mods, 1)
+        units += u
+        secs += dt
+    v = units / secs
+    cb = {"value": v, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
+          "sample": batch_sample_text(sample, 1) + f" per step, {args.steps} steps"}
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ph.size / v * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": config(nsph, float(ph.mean())), "cpu_baseline": cb,
+            "data": "synthetic", "config": batch_config(meta), "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "gpu_launches": 0}
     print(json.dumps(line), flush=True)
@@ -215,19 +271,27 @@ def run_reference(args, rank, world):
 
 # ----------------------------------------------------------------- ncu case
 def profile_case(kind):
-    """4 CG iterations of the 6 load systems of the 128^3 filtered workload in one
-    wave, as the bench runs them (spectrum 306 MB FP32 / 612 MB FP64, larger than
-    L2; a few GB on the device): the small case the ncu captures run on.  The
-    mixed handle runs the kernel variants the autotuner picks at this size
-    (register x passes, TMA y pass, register z pass), set by hand so that the
-    launch sequence is fixed."""
+    """4 CG iterations of the 6 load systems of one microstructure in one wave, as the
+    bench runs them: the small case the ncu captures run on (a few GB on the device).
+    fp64 / mixed: the 128^3 packing, filtered operator (spectrum 306 MB FP32 / 612 MB
+    FP64, larger than L2); mixed96: a 96^3 packing of the batched recipe (seed 1411 + 1,
+    f = 0.25, r = 6 voxels).  The mixed handles run the FP32 plane passes with the z
+    variant the autotuner picks at that size, set by hand so that the launch sequence
+    is fixed."""
     import torch
     from paper_1411_0330_gb300 import lsh
-    ph, mods, _ = workload()
+    from paper_1411_0330_gb300 import microstructures as ms
+    if kind == "mixed96":
+        ph, _, _ = ms.sphere_microstructure(96, 6.0, 0.25, seed=1412)
+        mods = np.array([k_mu(1.0, 0.3), k_mu(10.0, 0.2)])
+    else:
+        ph, mods, _ = workload()
     h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.ELASTIC, green=lsh.FILTERED,
-                   precision=lsh.MIXED if kind == "mixed" else lsh.FP64)
+                   precision=lsh.FP64 if kind == "fp64" else lsh.MIXED)
     if kind == "mixed":
-        h.set_variants(1, 3, 1, 0)
+        h.set_variants(0, 0, 2, 0)
+    elif kind == "mixed96":
+        h.set_variants(0, 0, 2, 8)
     _, infos = h.effective(tol=1e-30, maxit=4, raise_on_fail=False)
     torch.cuda.synchronize()
     print(json.dumps({"profile_case": kind, "info": infos[0]}))
@@ -290,35 +354,148 @@ def batch64_inputs(count=64, grids=(32, 48, 64, 96, 128), seed0=1411):
     return phases, meta
 
 
-def run_batch64(args):
-    """64 microstructures of uneven grids x 6 loads, mixed precision, one handle
-    (and stream) per grid, all solved together; against the plain FP64 solver
-    on the same systems."""
+def batch_config(meta):
+    counts = {}
+    for m in meta:
+        counts[str(m["n"])] = counts.get(str(m["n"]), 0) + 1
+    vox = sum(m["n"] ** 3 for m in meta)
+    # FP32 CG state per grid handle: all its microstructures x 6 loads x 6 components, 4 fields
+    smallest = min(counts[str(n)] * 6 * 6 * n ** 3 * 4 * 4 for n in (int(k) for k in counts))
+    return {"workload": "64 two-phase elastic sphere microstructures, grids U{32,48,64,96,128}^3, "
+                        "f ~ U(0.1,0.4), r = N/16 vox, seeds 1411+i, E 1/10 nu 0.3/0.2, mu0=mu_min/2 nu0=0.3, "
+                        "filtered Gamma, 6 Mandel loads each (384 systems), CG rel.res 1e-10; mixed precision "
+                        "(FP32 inner CG, double-float / FP64 refinement residual) vs plain FP64",
+            "grids": counts, "voxel_systems": int(vox * 6), "components": 6, "tol": TOL,
+            "l2": f"inputs larger than L2: the smallest grid handle's FP32 CG fields are {smallest / 1e6:.0f} MB "
+                  "(> 129 MB), no flush needed"}
+
+
+def batch_pass_bytes(k, n, filtered=True):
+    """Algorithmic FP32 bytes of pass k per live system-iteration on an n^3 grid (6
+    components), and the Gamma-table bytes read once per launch (filtered operator)."""
+    V, nxh = n ** 3, n // 2 + 1
+    per_sys = pass_traffic(k, V, 6, n, nxh, 0, 4)
+    table = V * 21 * 4 * nxh / n if (k == "z_gamma" and filtered) else 0.0
+    return per_sys, table
+
+
+def run_batch(args, rank, world, local):
+    """The default arm: the 64-microstructure batch, mixed precision against plain FP64."""
     import torch
+    import torch.distributed as dist
     from paper_1411_0330_gb300 import lsh
-    torch.cuda.set_device(0)
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)  # every grid handle issues its work here: events see all of it
     phases, meta = batch64_inputs()
     mods = np.array([k_mu(1.0, 0.3), k_mu(10.0, 0.2)])
-    gmx = lsh.GridBatch(phases, mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
-    g64 = lsh.GridBatch(phases, mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.FP64)
-    for _ in range(max(args.warmup, 1)):
+    gmx = lsh.GridBatch(phases, mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED, device=dev,
+                        stream=stream, tune=True)
+    g64 = lsh.GridBatch(phases, mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.FP64, device=dev,
+                        stream=stream, tune=False)
+    for _ in range(args.warmup):
         gmx.effective(tol=TOL)
     g64.effective(tol=TOL)
-    for h in gmx.handles:
-        h.profile_read(reset=True)
-    clk = ClockSampler(0)
-    clk.start()
-    t_mx, (A_mx, I_mx) = _wall(lambda: [gmx.effective(tol=TOL) for _ in range(args.steps)][-1])
-    clocks = clk.stop()
-    t_mx /= args.steps
-    launches = sum(h.profile_read(reset=True)["launches"] for h in gmx.handles) // args.steps
-    t_64, (A_64, I_64) = _wall(lambda: g64.effective(tol=TOL))
-    # sequential (one grid after the other) for the gain from overlapping the grids
-    t_seq, _ = _wall(lambda: [h.effective(tol=TOL) for h in gmx.handles])
+
+    def timed(gb, steps, profile):
+        for h in gb.handles:
+            h.profile_read(reset=True)
+            h.profile_enable(bool(profile), every=max(int(profile), 1))
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clk = ClockSampler(local)
+        clk.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = None
+        for _ in range(steps):
+            out = gb.effective(tol=TOL)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        clocks = clk.stop()
+        ms = slowest_rank_ms(e0.elapsed_time(e1), world, dev)
+        profs = [h.profile_read(reset=True) for h in gb.handles]
+        for h in gb.handles:
+            h.profile_enable(False)
+        return ms / steps, out, profs, clocks
+
+    # headline: the mixed solver; per-pass events in one CG chunk of PROF_EVERY
+    ms_mx, (A_mx, I_mx), prof_mx, clocks = timed(gmx, args.steps, PROF_EVERY)
+    # comparison: the plain FP64 solver on the same systems (one step: its iteration counts and time)
+    ms_64, (A_64, I_64), _, clocks64 = timed(g64, 1, 0)
     vox = np.array([m["n"] ** 3 for m in meta], dtype=np.float64)
     it64 = np.array([sum(i["iters"] for i in inf) for inf in I_64], dtype=np.float64)
     itmx = np.array([sum(i["iters"] for i in inf) for inf in I_mx], dtype=np.float64)
     errs = [_cstar_err(a, b) for a, b in zip(A_mx, A_64)]
+    value = replica_rate(float((vox * it64).sum()), world, ms_mx)  # FP64-equivalent
+    value_raw = replica_rate(float((vox * itmx).sum()), world, ms_mx)
+    value_64 = replica_rate(float((vox * it64).sum()), world, ms_64)
+    launches = sum(p["launches"] for p in prof_mx) // args.steps
+
+    # roofline of the dominant FP32 pass over all grid handles, from the live per-pass events:
+    # algorithmic bytes of the live system-iterations inside the timed chunks / their event time
+    peaks = load_peaks()
+    grid_of = [h.shape[0] for h in gmx.handles]
+    tot_ms = {k: sum(p["pass_ms"][k] for p in prof_mx) for k in lsh.PASS_NAMES}
+    tot_n = {k: sum(p["pass_launches"][k] for p in prof_mx) for k in lsh.PASS_NAMES}
+
+    def bytes_of(p, n, k):
+        """Algorithmic bytes of pass k in the timed chunks of one grid handle (none when the
+        pass did not run: the plane passes do the y transforms inside the x passes)."""
+        if not p["pass_launches"][k]:
+            return 0.0
+        per_sys, table = batch_pass_bytes(k, n)
+        return per_sys * p["timed_sys_iters"] + table * p["pass_launches"][k]
+
+    tot_b = {k: sum(bytes_of(p, n, k) for p, n in zip(prof_mx, grid_of)) for k in lsh.PASS_NAMES}
+    dom = max(tot_ms, key=tot_ms.get)
+    achieved = tot_b[dom] / (tot_ms[dom] / 1e3) / 1e9
+    sh_sum = max(sum(tot_ms.values()), 1e-30)
+    per_grid_pass = {}
+    for p, n in zip(prof_mx, grid_of):
+        per_grid_pass[str(n)] = {k: {"ms_per_launch": p["pass_ms"][k] / p["pass_launches"][k],
+                                     "gbs": bytes_of(p, n, k) / (p["pass_ms"][k] / 1e3) / 1e9,
+                                     "frac": bytes_of(p, n, k) / (p["pass_ms"][k] / 1e3) / 1e9 / peaks["hbm_gbs"]}
+                                 for k in lsh.PASS_NAMES if p["pass_launches"][k]}
+        per_grid_pass[str(n)]["live_system_iterations_timed"] = p["timed_sys_iters"]
+    iter_b = sum(tot_b.values())
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic_per_launch(dom, tot_b[dom] / tot_n[dom]),
+                "traffic_source": NCU_TRAFFIC_SOURCE,
+                "kernel": f"{dom} (FP32, all grids)", "avg_launch_ms": tot_ms[dom] / tot_n[dom],
+                "algorithmic_bytes_per_launch": tot_b[dom] / tot_n[dom],
+                "peak_source": peaks["source"] + " hbm_gbs (copy)",
+                "pass_share_fp32": {k: tot_ms[k] / sh_sum for k in lsh.PASS_NAMES},
+                "pass_frac_fp32": {k: tot_b[k] / (tot_ms[k] / 1e3) / 1e9 / peaks["hbm_gbs"]
+                                   for k in lsh.PASS_NAMES if tot_n[k]},
+                "whole_iteration_frac": iter_b / (sh_sum / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "per_grid": per_grid_pass}
+
+    # end to end through the public API: phase maps from pinned host memory in, C* out, every step
+    pinned = [torch.from_numpy(st).pin_memory() for st in gmx.grid_stacks(phases)]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        gmx.set_microstructures(pinned)  # host -> device inside the call
+        gmx.effective(tol=TOL)  # C* back on the host
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / args.steps
+    dt = slowest_rank_ms(dt * 1e3, world, dev) / 1e3
+    e2e = {"value": replica_rate(float((vox * it64).sum()), world, dt * 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(sum(t.numel() for t in pinned)), "d2h_bytes_per_step": 64 * 36 * 8,
+           "s_per_step": dt}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        sample = batch_sample(phases, meta)
+        u, secs = oracle_batch_sample(sample, mods, 8)  # about 10 s on 16 host cores
+        cpu = {"value": u / secs, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
+               "sample": batch_sample_text(sample, 8) + f", {secs:.1f} s"}
+
     per_grid = {}
     for m, e, a, b in zip(meta, errs, itmx, it64):
         g = per_grid.setdefault(str(m["n"]), {"count": 0, "inner_iters": 0, "fp64_iters": 0, "max_err": 0.0})
@@ -326,27 +503,33 @@ def run_batch64(args):
         g["inner_iters"] += int(a)
         g["fp64_iters"] += int(b)
         g["max_err"] = max(g["max_err"], e[0])
-    value = float((vox * it64).sum() / t_mx)
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": max(args.warmup, 1), "ms_per_step": t_mx * 1e3, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "64 two-phase elastic sphere microstructures, grids U{32,48,64,96,128}^3, "
-                                   "f ~ U(0.1,0.4), r = N/16 vox, seeds 1411+i, E 1/10 nu 0.3/0.2, filtered Gamma, "
-                                   "6 Mandel loads each (384 systems), CG rel.res 1e-10",
-                       "voxel_systems": int(vox.sum() * 6), "grids": {k: v["count"] for k, v in per_grid.items()},
-                       "timing": "wall clock around the synchronous lsh_effective_batch call (5 streams)",
-                       "value_counting": "sum N^3 x FP64-solver iterations / mixed time (accuracy-fair)"},
-            "gpu_launches": launches, "clocks": clocks,
-            "mixed": {"value_raw": float((vox * itmx).sum() / t_mx), "s_per_step": t_mx,
-                      "c_star_max_err_vs_fp64": max(e[0] for e in errs),
-                      "c_star_max_true_rel_err_vs_fp64": max(e[1] for e in errs),
-                      "sequential_grids_s": t_seq, "overlap_gain": t_seq / t_mx},
-            "fp64_plain": {"value": float((vox * it64).sum() / t_64), "s_per_step": t_64,
-                           "speedup_mixed_vs_fp64": t_64 / t_mx},
-            "per_grid": per_grid}
-    print(json.dumps(line), flush=True)
+    if rank == 0:
+        cfg = batch_config(meta)
+        cfg["timing"] = "CUDA events on the one stream all grid handles use, around the steps"
+        cfg["value_counting"] = ("sum over systems of N^3 x the plain FP64 solver's CG iterations, divided by the "
+                                 "mixed solver's time (accuracy-fair); raw inner-iteration rate in mixed")
+        cfg["autotune"] = {str(n): h.tune_report for n, h in zip(grid_of, gmx.handles)}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_mx, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic", "config": cfg,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clocks,
+                "mixed": {"value_raw": value_raw, "inner_iterations_per_step": int(itmx.sum()),
+                          "pass_events": f"one CG chunk in {PROF_EVERY}",
+                          "c_star_max_err_vs_fp64": max(e[0] for e in errs),
+                          "c_star_max_true_rel_err_vs_fp64": max(e[1] for e in errs),
+                          "speedup_vs_fp64": ms_64 / ms_mx,
+                          "outer_steps_per_step": int(sum(i["outer"] for inf in I_mx for i in inf)),
+                          "residual_applies_per_step": int(sum(i["applies64"] for inf in I_mx for i in inf))},
+                "fp64_plain": {"value": value_64, "ms_per_step": ms_64, "iterations_per_step": int(it64.sum()),
+                               "clocks": clocks64},
+                "per_grid": per_grid}
+        print(json.dumps(line), flush=True)
     gmx.close()
     g64.close()
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
     return 0
 
 
@@ -619,15 +802,15 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--concurrent", action="store_true",
                     help="solve the filtered and truncated handles together, one stream each")
-    ap.add_argument("--workload", default="spheres128",
+    ap.add_argument("--workload", default="batch64",
                     choices=["spheres128", "batch64", "contrast256", "gradient128", "convergence", "cufft"],
-                    help="spheres128: the 128^3 sphere packing (default); batch64: 64 microstructures "
-                         "of uneven grids solved together; contrast256: 256^3 mixed vs FP64 at contrasts "
+                    help="batch64: 64 microstructures of uneven grids, mixed+batched vs FP64 (default); "
+                         "spheres128: the 128^3 sphere packing, filtered and truncated; contrast256: 256^3 mixed vs FP64 at contrasts "
                          "10/100/1000; gradient128: adjoint gradient of C* and its finite-difference check; "
                          "convergence: C* against the grid, centre rule vs sub-voxel averaging; cufft: "
                          "the FP32 operator passes against cuFFT R2C + C2R alone at 128^3")
-    ap.add_argument("--profile-case", choices=["fp64", "mixed"], default=None,
-                    help="small case for ncu: 4 CG iterations of one 128^3 filtered solve, then exit")
+    ap.add_argument("--profile-case", choices=["fp64", "mixed", "mixed96"], default=None,
+                    help="small case for ncu: 4 CG iterations of one 128^3 (96^3) filtered solve, then exit")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -638,7 +821,9 @@ def main():
     if args.profile_case:
         return profile_case(args.profile_case)
     if args.workload == "batch64":
-        return run_batch64(args)
+        return run_batch(args, rank, world, local)
+    if args.workload == "spheres128":
+        return run_spheres128(args, rank, world, local)
     if args.workload == "contrast256":
         return run_contrast256(args)
     if args.workload == "gradient128":
@@ -647,7 +832,12 @@ def main():
         return run_convergence(args)
     if args.workload == "cufft":
         return run_cufft(args)
+    return 0
 
+
+def run_spheres128(args, rank, world, local):
+    """One 128^3 packing (the 3D elasticity configuration), filtered and truncated
+    operators, 6 loads each: mixed precision against plain FP64."""
     import torch
     import torch.distributed as dist
     from paper_1411_0330_gb300 import lsh

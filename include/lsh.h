@@ -91,9 +91,11 @@ typedef struct lsh_problem {
   int green;                   /* LSH_GREEN_TRUNCATED, _FILTERED or _FD (scalar)          */
   int precision;               /* LSH_FP64 or LSH_MIXED                                   */
   int nphase;                  /* 1..256                                                  */
-  const double *phase_moduli;  /* host.  Scalar: dim*dim row-major conductivity per phase
-                                  (must be diagonal in this build).  Elastic: (bulk K,
-                                  shear mu) per phase.                                    */
+  const double *phase_moduli;  /* host.  Scalar: dim*dim row-major symmetric conductivity
+                                  per phase; anisotropic tensors must commute with the
+                                  reference and with each other (Eq. (hyp3): one common
+                                  eigenbasis), else LSH_ERR_UNSUPPORTED.  Elastic: (bulk
+                                  K, shear mu) per phase.                                 */
   const double *ref_moduli;    /* host, same format as one phase: the reference medium A0
                                   (Sec. 2.2.2).  NULL selects half the softest phase:
                                   elastic mu0 = min(mu)/2, nu0 = 0.3; scalar a0 I with a0 =
@@ -146,7 +148,10 @@ typedef struct lsh_tune_report {
   int x_variant;  /* FP32 inverse x pass in use: 0 shared-memory stages, 1 register FFT,
                      2 register FFT in a persistent double-buffered kernel, 3 register
                      FFT in blocks of 128 threads                                      */
-  int y_variant;  /* FP32 y pass in use: 0 register FFT, 1 TMA tiles                    */
+  int y_variant;  /* FP32 y pass in use: 0 register FFT, 1 TMA tiles, 2 none: the x and
+                     y transforms of each z plane run in one kernel (plane passes, with
+                     the z pass on a ky-major spectrum; square planes of 16, 32, 48, 64,
+                     96 or 128; the only FP32 passes for 48 and 96)                   */
   int z_variant;  /* FP32 z pass (with Gamma) in use: 0 register FFT; TMA tiles of
                      1: 4 columns double-buffered, 2: 8 columns, 3: 8 columns double-
                      buffered, 4: 16 columns with the FFT exchange in the tile, 5: the
@@ -159,6 +164,8 @@ typedef struct lsh_tune_report {
   float x_ms[4];
   float y_ms[2];
   float z_ms[10];
+  float xy_ms[2]; /* one CG iteration's passes summed: separate x/y passes, plane passes */
+  float zp_ms[4]; /* z pass on the ky-major spectrum, variants 0, 6, 8, 9             */
 } lsh_tune_report;
 
 /* Bytes of device workspace lsh_setup needs for this problem. */
@@ -216,9 +223,10 @@ lsh_status lsh_effective(lsh_handle *h, const lsh_solve_opts *opts, double *Asta
 lsh_status lsh_autotune(lsh_handle *h, lsh_tune_report *rep);
 
 /* Select the FP32 forward x / inverse x / y / z pass variants by hand (numbering of lsh_tune_report;
- * no counterpart in the paper: for tests and measurements).  Returns
- * LSH_ERR_UNSUPPORTED if a variant is not available for this problem (FP64
- * handles accept only zeros). */
+ * no counterpart in the paper: for tests and measurements).  y_variant 2
+ * selects the plane passes (x variants ignored; z variant 0, 6, 8 or 9).
+ * Returns LSH_ERR_UNSUPPORTED if a variant is not available for this problem
+ * (FP64 handles accept only zeros). */
 lsh_status lsh_set_variants(lsh_handle *h, int xf_variant, int x_variant, int y_variant, int z_variant);
 
 /* lsh_effective for several handles at once (microstructures of different
@@ -248,19 +256,24 @@ lsh_status lsh_effective_grad(lsh_handle *h, const double *tau_all, const double
  * K x: plugins inside host programs that own the device memory and offer no
  * allocator, processes whose memory is already claimed by another
  * framework's pool, or code that must not risk the device synchronisation
- * cudaMalloc / cudaFree may cause).  Computes y = K x exactly as lsh_apply on
- * a handle built from `prob` (one microstructure, FP64), without a handle or
+ * cudaMalloc / cudaFree may cause).  Computes y = K x as lsh_apply does on a
+ * handle built from `prob` (one microstructure, FP64), without a handle or
  * workspace: the scratch (spectrum, Gamma^h table, FFT and phase tables) is a
- * 64 MiB array inside the library that every device loading the library
+ * 72 MiB array inside the library that every device loading the library
  * keeps until process exit; problems needing more return
- * LSH_ERR_UNSUPPORTED_SIZE (64^3 elasticity fits, 128^3 does not).  prob->phase
- * (and prob->scale) must be device memory (phase_on_host = 0, nbatch <= 1);
- * x, y: device, c*V doubles.  It calls no allocator, host or device.
- * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress and caches it; make that first call before any stream
- * capture.  All calls share the array: calls whose device work overlaps race
- * on it and must be serialised by the caller.  Synchronises `stream`
- * (a cudaStream_t) before returning. */
+ * LSH_ERR_UNSUPPORTED_SIZE (64^3 elasticity fits, 128^3 does not).  Narrower
+ * than lsh_apply: scalar phase and reference tensors must be diagonal
+ * (anisotropic commuting ones return LSH_ERR_UNSUPPORTED) and `scale` may only
+ * hold a factor (scale_kind 0; volume fractions return LSH_ERR_UNSUPPORTED).
+ * prob->phase (and prob->scale) must be device memory (phase_on_host = 0,
+ * nbatch <= 1); x, y: device, c*V doubles.  It calls no allocator, host or
+ * device.  The first call on a device looks up the array's device address
+ * with cudaGetSymbolAddress and caches it (not revalidated after
+ * cudaDeviceReset: do not call it again on a device that was reset).  A call
+ * copies host tables and synchronises `stream` (a cudaStream_t) before
+ * returning, so a stream under capture is refused (LSH_ERR_INVALID_ARG).  All
+ * calls share the array: calls whose device work overlaps race on it and must
+ * be serialised by the caller. */
 lsh_status lsh_apply_noalloc(const lsh_problem *prob, const double *x, double *y, void *stream);
 
 /* Diagnostics (no counterpart in the paper): kernel launches issued by the
@@ -274,6 +287,9 @@ typedef struct lsh_profile {
   long long timed_iters;       /* CG iterations covered by pass_ms                 */
   double pass_ms[6];           /* summed device milliseconds per pass kind        */
   long long pass_launches[6];  /* launches that did work, per pass kind           */
+  long long timed_sys_iters;   /* CG iterations of live (not yet converged) systems
+                                  inside the timed iterations, summed over systems:
+                                  the work pass_ms covers                          */
 } lsh_profile;
 
 /* Per-pass event timing of the CG iterations: 0 off, 1 every iteration, k > 1
@@ -284,6 +300,17 @@ lsh_status lsh_profile_enable(lsh_handle *h, int enable);
 
 /* Copy the counters into `out` (host); reset them when `reset` is nonzero. */
 lsh_status lsh_profile_read(lsh_handle *h, lsh_profile *out, int reset);
+
+/* Failure-path check of the bounded device waits (no counterpart in the
+ * paper).  Every wait of the library's kernels on a shared-memory barrier
+ * gives up after one second, records a fault word and returns; the next
+ * synchronous call reports LSH_ERR_CUDA and clears the word, and the handle
+ * stays usable.  This call runs that path on purpose: one kernel on the
+ * handle's stream waits `seconds` (0 < seconds <= 10) on a barrier that
+ * expects two arrivals and receives one, gives up, and the call returns what
+ * a real give-up returns, LSH_ERR_CUDA (LSH_OK would mean the wait was not
+ * bounded).  No copy is in flight during the wait.  Synchronous. */
+lsh_status lsh_check_bounded_wait(lsh_handle *h, double seconds);
 
 /* Release the handle (host memory only; the workspace stays the caller's). */
 void lsh_destroy(lsh_handle *h);

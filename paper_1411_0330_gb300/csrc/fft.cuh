@@ -161,6 +161,41 @@ template <typename T, bool INV> struct Dft<T, 7, INV> {
   }
 };
 
+// Composite lengths R = A * B in registers (Cooley-Tukey with B-point outer
+// and A-point inner DFTs): x[B n1 + n2] -> X[k1 + A k2] =
+//   sum_n2 w_B^(n2 k2) [ w_R^(n2 k1) sum_n1 x[B n1 + n2] w_A^(n1 k1) ];
+// the twiddles w_R^m come from the line's table tw of length n (stride n / R).
+template <typename T, int A, int B, bool INV> struct DftAB {
+  static __device__ __forceinline__ void run(C2<T>* a, const C2<T>* tw, int n) {
+    constexpr int R = A * B;
+    const int st = n / R;
+    C2<T> b[B][A];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) {
+      C2<T> c[A];
+#pragma unroll
+      for (int n1 = 0; n1 < A; ++n1) c[n1] = a[B * n1 + n2];
+      Dft<T, A, INV>::run(c, tw, n);
+#pragma unroll
+      for (int k1 = 0; k1 < A; ++k1)
+        b[n2][k1] = (n2 == 0 || k1 == 0) ? c[k1]
+                                         : (INV ? cmulc<T>(c[k1], tw[n2 * k1 * st]) : cmul<T>(c[k1], tw[n2 * k1 * st]));
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < A; ++k1) {
+      C2<T> d[B];
+#pragma unroll
+      for (int n2 = 0; n2 < B; ++n2) d[n2] = b[n2][k1];
+      Dft<T, B, INV>::run(d, tw, n);
+#pragma unroll
+      for (int k2 = 0; k2 < B; ++k2) a[k1 + A * k2] = d[k2];
+    }
+  }
+};
+template <typename T, bool INV> struct Dft<T, 6, INV> : DftAB<T, 2, 3, INV> {};
+template <typename T, bool INV> struct Dft<T, 12, INV> : DftAB<T, 4, 3, INV> {};
+template <typename T, bool INV> struct Dft<T, 24, INV> : DftAB<T, 8, 3, INV> {};
+
 template <typename T, int R, bool INV>
 __device__ __forceinline__ void butterfly(C2<T>* base, int m, int te, const C2<T>* tw, int n) {
   C2<T> a[R];

@@ -73,6 +73,12 @@ template <typename T> struct OpArgs {
   int xreg;    // FP32 inverse x pass: 0 shared-memory stages, 1 register FFT, 2 register FFT persistent,
                // 3 register FFT in blocks of 128 threads
   int xfreg;   // 1: FP32 forward x pass on the register FFT (kernels_x.cu)
+  // FP32 plane passes (kernels_plane.cu): x and y transforms of a z plane in one
+  // kernel; the spectrum is then ky-major, H[S][c][ky][z][hs] (tlay = 1), and the
+  // Nyquist column kx = nx/2 also lives in nq[S][c][z][ky]
+  int plane;
+  int tlay;
+  C2<T>* nq;
 };
 
 // Thread-block sizes and tile shapes, chosen at setup for one system count.
@@ -151,6 +157,7 @@ void launch_df_z(const OpArgs<DF>& a, cudaStream_t s);
 void df_prepare();
 bool encode_z_map(CUtensorMap* out, void* H, int hs, int ny, int nz, int c, long long nsys, int tz);
 void tma_prepare();
+void launch_wait_probe(int* fault, unsigned long long limit_ns, cudaStream_t s);
 bool launch_xinv_reg(const OpArgs<float>& a, int mode, const float* xin, float* out, SolverState* st,
                      double* partials, cudaStream_t s, bool persistent, bool small = false);
 void xreg_prepare();
@@ -158,5 +165,11 @@ bool xinv_reg_fits(const OpArgs<float>& a);
 bool launch_xfwd_reg(const OpArgs<float>& a, int mode, const float* in, float* x, const float* r, float* p,
                      const SolverState* st, cudaStream_t s);
 bool xfwd_reg_fits(const OpArgs<float>& a);
+bool plane_length(int n);
+bool launch_xyfwd(const OpArgs<float>& a, int mode, const float* in, float* x, const float* r, float* p,
+                  const SolverState* st, cudaStream_t s);
+bool launch_xyinv(const OpArgs<float>& a, int mode, const float* xin, float* out, SolverState* st, double* partials,
+                  cudaStream_t s);
+void plane_prepare();
 
 }  // namespace lsh

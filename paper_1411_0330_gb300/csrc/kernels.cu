@@ -1081,6 +1081,7 @@ template <typename T>
 void launch_xfwd(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* in, T* x, const T* r, T* p,
                  const SolverState* st, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
+    if (a.plane && launch_xyfwd(a, mode, in, x, r, p, st, s)) return;
     if (a.xfreg && launch_xfwd_reg(a, mode, in, x, r, p, st, s)) return;
   }
   const int grid = a.S * a.bps;
@@ -1097,6 +1098,7 @@ void launch_xfwd(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* in, 
 template <typename T>
 void launch_yfft(const OpArgs<T>& a, const LaunchCfg& L, bool inv, const SolverState* st, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
+    if (a.plane) return;  // the plane passes transform y
     if (a.ytma) {
       launch_yfft_tma(a, inv, st, s);
       return;
@@ -1114,8 +1116,9 @@ void launch_yfft(const OpArgs<T>& a, const LaunchCfg& L, bool inv, const SolverS
 template <typename T>
 void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    if (a.ztma >= 1 && a.ztma <= 5 && launch_zgamma_tma(a, a.ztma, st, s)) return;
-    if (a.ztma == 7 && launch_zgamma_regp(a, st, s)) return;
+    // the TMA and persistent variants read the x-major layout only
+    if (!a.tlay && a.ztma >= 1 && a.ztma <= 5 && launch_zgamma_tma(a, a.ztma, st, s)) return;
+    if (!a.tlay && a.ztma == 7 && launch_zgamma_regp(a, st, s)) return;
   }
   if (a.zreg) {
     int tz = 0;
@@ -1133,6 +1136,7 @@ template <typename T>
 void launch_xinv(const OpArgs<T>& a, const LaunchCfg& L, int mode, const T* xin, T* out, SolverState* st,
                  double* partials, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
+    if (a.plane && mode <= 1 && launch_xyinv(a, mode, xin, out, st, partials, s)) return;
     if (a.xreg && mode <= 2 && launch_xinv_reg(a, mode, xin, out, st, partials, s, a.xreg == 2, a.xreg == 3)) return;
   }
   const int grid = a.S * a.bps;

@@ -176,11 +176,30 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS,
   C2<T>* tw = reinterpret_cast<C2<T>*>(smem_raw);
   C2<T>* buf = tw + N;
   __shared__ int line_yp[TZ], line_kx[TZ];
-  const int s = blockIdx.x;
+  const int nleft = a.nxh - nreg;
+  int s, tile;
+  if (a.tlay) {
+    // ky-major spectrum (plane passes): the kx tiles of one (system, ky) slab
+    // are consecutive blocks, so their columns share the slab's contiguous range
+    const long long nregb = (long long)a.ny * a.S * nrt;
+    const long long lin = blockIdx.x;
+    if (lin < nregb) {
+      const int yp = (int)(lin / ((long long)a.S * nrt));
+      const int rem = (int)(lin - (long long)yp * a.S * nrt);
+      s = rem / nrt;
+      tile = yp * nrt + (rem - s * nrt);
+    } else {
+      const int ntl = (a.ny * nleft + TZ - 1) / TZ;
+      const int l2 = (int)(lin - nregb);
+      s = l2 / ntl;
+      tile = a.ny * nrt + (l2 - s * ntl);
+    }
+  } else {
+    s = blockIdx.x;
+    tile = blockIdx.y;
+  }
   if (st != nullptr && st[s].done) return;
   for (int u = threadIdx.x; u < N; u += blockDim.x) tw[u] = a.twz[u];
-  const int tile = blockIdx.y;
-  const int nleft = a.nxh - nreg;
   if (threadIdx.x < TZ) {
     const int i = threadIdx.x;
     int yp = -1, kx = 0;
@@ -211,9 +230,19 @@ __global__ void __launch_bounds__(ZCfg<T, NC, N, TZV>::THREADS,
   const int i = threadIdx.x % TZ, comp = (threadIdx.x / TZ) % NC, t = threadIdx.x / (TZ * NC);
   const int yp = line_yp[i], kx = line_kx[i];
   const bool valid = yp >= 0;
-  const long long zstride = (long long)a.ny * a.hs;  // z planes of H
+  long long zstride = (long long)a.ny * a.hs;  // z planes of H
   const long long cstride = zstride * N;
   C2<T>* __restrict__ Hl = a.H + ((long long)s * NC + comp) * cstride + (valid ? (long long)yp * a.hs + kx : 0);
+  if (a.tlay) {
+    if (valid && 2 * kx == a.nx) {
+      // the Nyquist column: NQ[s][comp][z][ky]
+      Hl = a.nq + ((long long)s * NC + comp) * N * a.ny + yp;
+      zstride = a.ny;
+    } else {
+      Hl = a.H + ((long long)s * NC + comp) * cstride + (valid ? (long long)yp * N * a.hs + kx : 0);
+      zstride = a.hs;
+    }
+  }
   C2<T>* exl = buf + (comp * TZ + i) * RL::LS;
   C2<T> v[R1];
 #pragma unroll
@@ -402,10 +431,24 @@ template <typename T, int NC, int N, int TZV> void launch_z_n(const OpArgs<T>& a
   const int nrt = a.nxh / ZC::TZ, nreg = nrt * ZC::TZ;
   const int ntiles = a.ny * nrt + (a.ny * (a.nxh - nreg) + ZC::TZ - 1) / ZC::TZ;
   const size_t smem = sizeof(C2<T>) * (N + ZC::BUF);
-  k_zgamma_reg<T, NC, N, TZV><<<dim3(a.S, ntiles), ZC::THREADS, smem, s>>>(a, st, nrt, nreg);
+  if (a.tlay)
+    k_zgamma_reg<T, NC, N, TZV><<<(unsigned)((long long)a.S * ntiles), ZC::THREADS, smem, s>>>(a, st, nrt, nreg);
+  else
+    k_zgamma_reg<T, NC, N, TZV><<<dim3(a.S, ntiles), ZC::THREADS, smem, s>>>(a, st, nrt, nreg);
 }
 
 template <typename T, int NC, int TZV> void launch_z_nc(const OpArgs<T>& a, const SolverState* st, cudaStream_t s) {
+  if constexpr (sizeof(T) == 4) {
+    // radix-3 lengths of the FP32 passes
+    if (a.nz == 48) {
+      launch_z_n<T, NC, 48, TZV>(a, st, s);
+      return;
+    }
+    if (a.nz == 96) {
+      launch_z_n<T, NC, 96, TZV>(a, st, s);
+      return;
+    }
+  }
   switch (a.nz) {
     case 16: launch_z_n<T, NC, 16, TZV>(a, st, s); break;
     case 32: launch_z_n<T, NC, 32, TZV>(a, st, s); break;
@@ -545,6 +588,10 @@ template <typename T, int NC> void attr_z_nc() {
   attr_z_n<T, NC, 64>();
   attr_z_n<T, NC, 128>();
   attr_z_n<T, NC, 256>();
+  if constexpr (sizeof(T) == 4) {
+    attr_z_n<T, NC, 48>();
+    attr_z_n<T, NC, 96>();
+  }
 }
 template <typename T, bool INV> void attr_y() {
   attr_y_n<T, INV, 16>();

@@ -700,4 +700,25 @@ bool encode_z_map(CUtensorMap* out, void* H, int hs, int ny, int nz, int c, long
   return r == CUDA_SUCCESS;
 }
 
+// Failure-path probe of the bounded waits: a barrier initialised for two
+// arrivals receives one, so its phase never completes; the wait gives up after
+// limit_ns and records the fault word exactly as a TMA kernel whose copies
+// did not land would.  No copy is in flight.
+__global__ void k_wait_probe(int* fault, unsigned long long limit_ns) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 2);
+    mbar_init_fence();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_arrive(&bar);
+  __syncthreads();
+  const bool ok = mbar_wait(&bar, 0, limit_ns);
+  if (!ok && threadIdx.x == 0) atomicOr(fault, 1);
+}
+
+void launch_wait_probe(int* fault, unsigned long long limit_ns, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(fault, limit_ns);
+}
+
 }  // namespace lsh

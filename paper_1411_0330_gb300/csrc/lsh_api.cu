@@ -34,6 +34,11 @@ constexpr int kMaxSmem = 227 * 1024;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
+bool getenv_flag(const char* name) {
+  const char* e = getenv(name);
+  return e && e[0] == '1';
+}
+
 // ---------------------------------------------------------------- FFT plans
 bool make_plan(int n, Plan1D* p) {
   p->n = n;
@@ -101,6 +106,9 @@ struct Derived {
   bool rotated = false;
   double R[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
   double A0full[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+  // FP32 plane passes available (kernels_plane.cu): mixed precision, 3D, square
+  // planes of a plane length, z a register-FFT length
+  bool plane = false;
 };
 
 // Eigenvectors of a symmetric n x n matrix (n <= 3) by cyclic Jacobi rotations:
@@ -185,6 +193,8 @@ lsh_status derive(const lsh_problem* pr, Derived* d) {
   if (d->frac && pr->nphase != 2) return LSH_ERR_INVALID_ARG;
   if (!make_plan(d->nx, &d->px) || !make_plan(d->ny, &d->py) || !make_plan(d->nz, &d->pz))
     return LSH_ERR_UNSUPPORTED_SIZE;
+  d->plane = d->precision == LSH_MIXED && d->dim == 3 && d->nx == d->ny && plane_length(d->nx) &&
+             (reg_length(d->nz) || d->nz == 48 || d->nz == 96) && !getenv_flag("LSH_NO_PLANE");
   const int c = d->c, dim = d->dim;
   // reference medium
   if (!pr->ref_moduli && d->has_scale && !d->frac) return LSH_ERR_INVALID_ARG;
@@ -376,6 +386,8 @@ struct Layout {
   size_t off_ff[4], off_Hf, off_gf;
   size_t off_wa, off_wb, off_ms;  // MINRES: two direction fields (FP64) and per-system scalars
   size_t off_gdf, off_twdf;       // double-float Gamma table and twiddles (mixed handles)
+  size_t off_nq;                  // FP32 Nyquist columns of the plane passes
+  size_t off_kofy32, off_kofz32;  // frequency of each y / z position in the FP32 spectrum
   bool df;                        // double-float residual passes available
   bool minres;                    // MINRES buffers present
   size_t total;
@@ -408,7 +420,8 @@ Layout make_layout(const Derived& d) {
   LaunchCfg Ld = make_cfg<double>(d), Lf = make_cfg<float>(d);
   long long np = std::max<long long>({(long long)S * Ld.grid_x, (long long)S * Lf.grid_x, (long long)S * Ld.ew_per_sys,
                                       (long long)S * Lf.ew_per_sys, (long long)S * d.c * 152,
-                                      (long long)d.B * 1216, (long long)S * (rps_of(d) / 2 + 1)});
+                                      (long long)d.B * 1216, (long long)S * (rps_of(d) / 2 + 1),
+                                      (long long)S * d.c * d.nz});
   l.nparts = np;
   l.off_state = take(sizeof(SolverState) * (size_t)(3 * S + d.B));
   l.off_partials = take(sizeof(double) * (size_t)np);
@@ -418,6 +431,8 @@ Layout make_layout(const Derived& d) {
   l.off_posx = take(sizeof(int) * d.nx);
   l.off_kofy = take(sizeof(int) * d.ny);
   l.off_kofz = take(sizeof(int) * d.nz);
+  l.off_kofy32 = take(sizeof(int) * d.ny);
+  l.off_kofz32 = take(sizeof(int) * d.nz);
   l.off_sums = take(sizeof(double) * (size_t)S * d.c);
   l.off_W = take(sizeof(double) * 64);
   l.off_tabd = take(sizeof(double) * 2 * 256 * 6);
@@ -450,6 +465,7 @@ Layout make_layout(const Derived& d) {
     l.off_Hf = take(sizeof(float2) * (size_t)(S * d.c * nfh));
     l.off_gf = take(sizeof(float) * (size_t)(ncop * nf));
   }
+  l.off_nq = take(d.plane ? sizeof(float2) * (size_t)S * d.c * d.nz * d.ny : 0);
   l.df = df_eligible(d);
   l.off_gdf = take(l.df ? sizeof(DF) * (size_t)(ncop * nf) : 0);
   l.off_twdf = take(l.df ? sizeof(DF2) * (size_t)(d.nx + d.ny + d.nz) : 0);
@@ -491,6 +507,7 @@ struct lsh_handle {
   unsigned char *phase, *act, *flags;
   float* scale;
   int *posx, *kofy, *kofz;
+  int *kofy32, *kofz32;  // FP32 spectrum positions (natural order with the plane passes)
   double *sums, *Wdev, *tabd, *bbdev;
   PrecBufs<double> pd;
   PrecBufs<float> pf;
@@ -509,6 +526,7 @@ struct lsh_handle {
   double pass_ms[6] = {0, 0, 0, 0, 0, 0};
   long long pass_n[6] = {0, 0, 0, 0, 0, 0};
   long long timed_iters = 0;
+  long long timed_sys_iters = 0;  // live system-iterations inside the timed chunks
   // CUDA graphs of check_every CG iterations, one per (precision, wave, chunk,
   // profiling), captured on a private stream and replayed on `stream`
   struct Graph {
@@ -621,6 +639,19 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.fault = h->fault;
   a.xreg = 0;  // lsh_autotune measures the register x passes against the shared-memory ones
   a.xfreg = 0;
+  a.plane = 0;
+  a.tlay = 0;
+  a.nq = nullptr;
+  if (sizeof(T) == 4 && d.plane) {
+    // natural frequency order along y and z in every FP32 pass; the plane
+    // passes (ky-major spectrum) are the default
+    a.nq = (C2<T>*)(h->base + h->lay.off_nq);
+    a.kofy = h->kofy32;
+    a.kofz = h->kofz32;
+    a.zreg = 1;
+    a.plane = 1;
+    a.tlay = 1;
+  }
   a.ytma = 0;
   a.tmy = &P.tmy;
   if (sizeof(T) == 4 && a.yreg && d.nz > 1 && !h->no_tma)
@@ -739,7 +770,7 @@ template <typename T> lsh_status apply_internal(lsh_handle* h, const OpArgs<T>& 
   launch_zgamma<T>(a, P.L, nullptr, s);
   launch_yfft<T>(a, P.L, true, nullptr, s);
   launch_xinv<T>(a, P.L, 0, in, out, nullptr, nullptr, s);
-  h->launches += 5;
+  h->launches += a.plane ? 3 : 5;
   return last_launch();
 }
 
@@ -831,8 +862,13 @@ template <typename T> void enqueue_cg_iteration(lsh_handle* h, PrecBufs<T>& P, c
     cudaEventRecordWithFlags(e[6], s, rf);
     h->ev_used += 7;
   }
-  // the FP32 register inverse x pass adds one small reduction kernel
-  h->launches += 6 + ((sizeof(T) == 4 && (a.xreg == 1 || a.xreg == 3)) ? 1 : 0);
+  // the FP32 register inverse x pass adds one small reduction kernel; the plane
+  // passes replace the x and y passes (xy forward, z, xy inverse, reduction, update)
+  if (a.plane) {
+    h->launches += 5;
+  } else {
+    h->launches += 6 + ((sizeof(T) == 4 && (a.xreg == 1 || a.xreg == 3)) ? 1 : 0);
+  }
 }
 
 // The graph replaying `chunk` CG iterations of this wave, captured on first use.
@@ -879,10 +915,11 @@ lsh_status chunk_graph(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int ch
 // After a host synchronisation: add the pass times of the first `real`
 // recorded iterations (later ones returned at once because every system of
 // the wave was done).
-void harvest_profile(lsh_handle* h, int real) {
+void harvest_profile(lsh_handle* h, int real, bool plane) {
   const int groups = h->ev_used / 7;
   for (int g = 0; g < groups && g < real; ++g) {
     for (int k = 0; k < 6; ++k) {
+      if (plane && (k == 1 || k == 3)) continue;  // no separate y passes
       float ms = 0.f;
       if (cudaEventElapsedTime(&ms, h->ev[7 * g + k], h->ev[7 * g + k + 1]) == cudaSuccess) {
         h->pass_ms[k] += ms;
@@ -931,8 +968,14 @@ lsh_status cg_run(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int maxit, 
     }
     if ((stt = last_launch())) return stt;
     it += chunk;
+    long long live0 = 0;
+    for (int k = 0; k < S; ++k) live0 += out[k].iter;
     if ((stt = read_states(h, P.st, S, out.data()))) return stt;
-    if (h->prof_now) harvest_profile(h, max_iter() - before);
+    if (h->prof_now) {
+      for (int k = 0; k < S; ++k) h->timed_sys_iters += out[k].iter;
+      h->timed_sys_iters -= live0;
+      harvest_profile(h, max_iter() - before, a.plane != 0);
+    }
     h->prof_now = false;
   }
   launch_cg_finalize<T>(P.x, P.p, (long long)a.c * a.V, S, P.st, P.L.ew_per_sys, h->stream);
@@ -1317,6 +1360,8 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   h->posx = (int*)(h->base + l.off_posx);
   h->kofy = (int*)(h->base + l.off_kofy);
   h->kofz = (int*)(h->base + l.off_kofz);
+  h->kofy32 = (int*)(h->base + l.off_kofy32);
+  h->kofz32 = (int*)(h->base + l.off_kofz32);
   h->sums = (double*)(h->base + l.off_sums);
   h->Wdev = (double*)(h->base + l.off_W);
   h->tabd = (double*)(h->base + l.off_tabd);
@@ -1353,6 +1398,11 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   for (int k = 0; k < d.nx; ++k) posx[k] = dif_position(d.px, k);
   for (int k = 0; k < d.ny; ++k) kofy[h->pd.a.yreg ? k : dif_position(d.py, k)] = k;
   for (int k = 0; k < d.nz; ++k) kofz[h->pd.a.zreg ? k : dif_position(d.pz, k)] = k;
+  std::vector<int> kofy32(kofy), kofz32(kofz);
+  if (d.plane) {
+    for (int k = 0; k < d.ny; ++k) kofy32[k] = k;
+    for (int k = 0; k < d.nz; ++k) kofz32[k] = k;
+  }
   std::vector<double> twd, tmpd;
   twiddles<double>(d.nx, tmpd); twd.insert(twd.end(), tmpd.begin(), tmpd.end());
   twiddles<double>(d.ny, tmpd); twd.insert(twd.end(), tmpd.begin(), tmpd.end());
@@ -1376,6 +1426,8 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   SETUP_CK(cudaMemcpyAsync(h->posx, posx.data(), sizeof(int) * d.nx, cudaMemcpyHostToDevice, st));
   SETUP_CK(cudaMemcpyAsync(h->kofy, kofy.data(), sizeof(int) * d.ny, cudaMemcpyHostToDevice, st));
   SETUP_CK(cudaMemcpyAsync(h->kofz, kofz.data(), sizeof(int) * d.nz, cudaMemcpyHostToDevice, st));
+  SETUP_CK(cudaMemcpyAsync(h->kofy32, kofy32.data(), sizeof(int) * d.ny, cudaMemcpyHostToDevice, st));
+  SETUP_CK(cudaMemcpyAsync(h->kofz32, kofz32.data(), sizeof(int) * d.nz, cudaMemcpyHostToDevice, st));
   SETUP_CK(cudaMemcpyAsync(h->base + l.off_tw_d, twd.data(), sizeof(double) * twd.size(), cudaMemcpyHostToDevice, st));
   SETUP_CK(cudaMemcpyAsync(h->base + l.off_tw_f, twf.data(), sizeof(float) * twf.size(), cudaMemcpyHostToDevice, st));
   SETUP_CK(cudaMemcpyAsync(h->base + l.off_tabd, tabd.data(), sizeof(double) * tabd.size(), cudaMemcpyHostToDevice, st));
@@ -1385,11 +1437,12 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   set_smem_attrs<float>();
   tma_prepare();
   xreg_prepare();
+  if (d.plane) plane_prepare();
   if (l.df) df_prepare();
   launch_gamma_table<double>(h->pd.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st,
                              d.rotated ? d.A0full : nullptr, d.rotated ? d.R : nullptr);
   if (d.precision == LSH_MIXED)
-    launch_gamma_table<float>(h->pf.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st,
+    launch_gamma_table<float>(h->pf.a, d.dim, d.physics, d.green, d.ref_user, h->kofy32, h->kofz32, st,
                               d.rotated ? d.A0full : nullptr, d.rotated ? d.R : nullptr);
   if (l.df) {
     const long long nf = (long long)d.nz * d.ny * d.ts, ncop = (d.ncoef + 3) & ~3;
@@ -1601,11 +1654,13 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   r.x_variant = h->pf.a.xreg;
   r.xf_variant = h->pf.a.xfreg;
   for (int k = 0; k < 2; ++k) r.xf_ms[k] = -1.f;
-  r.y_variant = h->pf.a.ytma;
+  r.y_variant = h->pf.a.plane ? 2 : h->pf.a.ytma;
   r.z_variant = h->pf.a.ztma;
   for (int k = 0; k < 4; ++k) r.x_ms[k] = -1.f;
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
   for (int k = 0; k < 10; ++k) r.z_ms[k] = -1.f;
+  for (int k = 0; k < 2; ++k) r.xy_ms[k] = -1.f;
+  for (int k = 0; k < 4; ++k) r.zp_ms[k] = -1.f;
   const Derived& d = h->d;
   if (d.precision == LSH_MIXED) {
     PrecBufs<float>& P = h->pf;
@@ -1641,7 +1696,12 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       f.rr = 1.0;
     }
     LSH_CK(cudaMemcpyAsync(P.st, fake.data(), sizeof(SolverState) * d.Smax, cudaMemcpyHostToDevice, s));
-    if (xfwd_reg_fits(a)) {
+    // the separate x and y passes need natural y order for the FP32 table on
+    // plane grids (powers of two); radix-3 planes have the plane passes only
+    const bool sep_ok = !d.plane || reg_length(d.ny);
+    a.plane = 0;
+    a.tlay = 0;
+    if (sep_ok && xfwd_reg_fits(a)) {
       for (int v = 0; v < 2; ++v) {
         a.xfreg = v;
         r.xf_ms[v] = timeit([&]() {
@@ -1654,7 +1714,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       r.xf_variant = (r.xf_ms[1] > 0.f && r.xf_ms[1] < r.xf_ms[0]) ? 1 : 0;
       a.xfreg = r.xf_variant;
     }
-    {
+    if (sep_ok) {
       // inverse x pass with the local term and the (p, Kp) reduction
       int bx = 0;
       for (int v = 0; v < 4; ++v) {
@@ -1671,7 +1731,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       r.x_variant = bx;
       a.xreg = r.x_variant;
     }
-    if (a.yreg && P.ytma_ok) {
+    if (sep_ok && a.yreg && P.ytma_ok) {
       for (int v = 0; v < 2; ++v) {
         a.ytma = v;
         r.y_ms[v] = timeit([&]() {
@@ -1682,7 +1742,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       r.y_variant = (r.y_ms[1] > 0.f && (r.y_ms[0] < 0.f || r.y_ms[1] < r.y_ms[0])) ? 1 : 0;
       a.ytma = r.y_variant;
     }
-    if (a.zreg) {
+    if (sep_ok && a.zreg) {
       int best = 0;
       for (int v = 0; v < 10; ++v) {
         if (v >= 1 && v <= 5 && !P.ztma_ok) continue;  // TMA tiles need the tensor map
@@ -1700,6 +1760,44 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       r.z_variant = best;
       a.ztma = best;
     }
+    if (d.plane) {
+      // the plane passes with the register z kernels on the ky-major spectrum,
+      // against the best separate passes, summed over one CG iteration
+      OpArgs<float> b = a;
+      b.plane = 1;
+      b.tlay = 1;
+      const int zc[4] = {0, 6, 8, 9};
+      int bz = 0;
+      for (int k = 0; k < 4; ++k) {
+        b.ztma = zc[k];
+        r.zp_ms[k] = timeit([&]() {
+          launch_zgamma<float>(b, P.L, nullptr, s);
+          return true;
+        });
+        if (r.zp_ms[k] > 0.f && (r.zp_ms[bz] < 0.f || r.zp_ms[k] < r.zp_ms[bz])) bz = k;
+      }
+      b.ztma = zc[bz];
+      const float f = timeit([&]() {
+        cudaMemcpyAsync(P.st, fake.data(), sizeof(SolverState) * d.Smax, cudaMemcpyHostToDevice, s);
+        return launch_xyfwd(b, 1, nullptr, P.x, P.r, P.p, P.st, s);
+      });
+      const float i = timeit([&]() {
+        cudaMemcpyAsync(P.st, fake.data(), sizeof(SolverState) * d.Smax, cudaMemcpyHostToDevice, s);
+        return launch_xyinv(b, 1, P.p, P.q, P.st, h->partials, s);
+      });
+      r.xy_ms[1] = (f > 0.f && i > 0.f && r.zp_ms[bz] > 0.f) ? f + r.zp_ms[bz] + i : -1.f;
+      if (sep_ok) {
+        const float xf = r.xf_ms[a.xfreg] > 0.f ? r.xf_ms[a.xfreg] : r.xf_ms[0];
+        const float yy = r.y_ms[a.ytma] > 0.f ? r.y_ms[a.ytma] : -1.f;
+        const float zz = r.z_ms[a.ztma], xi = r.x_ms[a.xreg];
+        if (xf > 0.f && yy > 0.f && zz > 0.f && xi > 0.f) r.xy_ms[0] = xf + 2.f * yy + zz + xi;
+      }
+      if (!sep_ok || (r.xy_ms[1] > 0.f && (r.xy_ms[0] < 0.f || r.xy_ms[1] < r.xy_ms[0]))) {
+        a = b;
+        r.y_variant = 2;
+        r.z_variant = b.ztma;
+      }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     lsh_status st = last_launch();
@@ -1709,6 +1807,8 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
     P.a.xfreg = a.xfreg;
     P.a.ytma = a.ytma;
     P.a.ztma = a.ztma;
+    P.a.plane = a.plane;
+    P.a.tlay = a.tlay;
     h->drop_graphs();  // captured with the previous choices
   }
   if (rep) *rep = r;
@@ -1717,12 +1817,23 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
 
 lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
-  if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 3 || y_variant < 0 || y_variant > 1 ||
+  if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 3 || y_variant < 0 || y_variant > 2 ||
       z_variant < 0 || z_variant > 9)
     return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;
   if (h->d.precision != LSH_MIXED)
     return (xf_variant || x_variant || y_variant || z_variant) ? LSH_ERR_UNSUPPORTED : LSH_OK;
+  if (y_variant == 2) {
+    // plane passes: the register z kernels on the ky-major spectrum
+    if (!h->d.plane || !(z_variant == 0 || z_variant == 6 || z_variant == 8 || z_variant == 9))
+      return LSH_ERR_UNSUPPORTED;
+    P.a.plane = 1;
+    P.a.tlay = 1;
+    P.a.ztma = z_variant;
+    h->drop_graphs();
+    return LSH_OK;
+  }
+  if (h->d.plane && !reg_length(h->d.ny)) return LSH_ERR_UNSUPPORTED;  // radix-3 planes: plane passes only
   if (x_variant >= 1 && !xinv_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (xf_variant == 1 && !xfwd_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;
@@ -1743,8 +1854,18 @@ lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_
   P.a.xfreg = xf_variant;
   P.a.ytma = y_variant;
   P.a.ztma = z_variant;
+  P.a.plane = 0;
+  P.a.tlay = 0;
   h->drop_graphs();
   return LSH_OK;
+}
+
+lsh_status lsh_check_bounded_wait(lsh_handle* h, double seconds) {
+  if (!h || !(seconds > 0.0) || seconds > 10.0) return LSH_ERR_INVALID_ARG;
+  launch_wait_probe(h->fault, (unsigned long long)(seconds * 1e9), h->stream);
+  h->launches += 1;
+  if (last_launch() != LSH_OK) return LSH_ERR_CUDA;
+  return check_fault(h);
 }
 
 lsh_status lsh_profile_enable(lsh_handle* h, int enable) {
@@ -1768,6 +1889,7 @@ lsh_status lsh_profile_read(lsh_handle* h, lsh_profile* out, int reset) {
   if (!h || !out) return LSH_ERR_INVALID_ARG;
   out->launches = h->launches;
   out->timed_iters = h->timed_iters;
+  out->timed_sys_iters = h->timed_sys_iters;
   for (int k = 0; k < 6; ++k) {
     out->pass_ms[k] = h->pass_ms[k];
     out->pass_launches[k] = h->pass_n[k];
@@ -1775,6 +1897,7 @@ lsh_status lsh_profile_read(lsh_handle* h, lsh_profile* out, int reset) {
   if (reset) {
     h->launches = 0;
     h->timed_iters = 0;
+    h->timed_sys_iters = 0;
     for (int k = 0; k < 6; ++k) {
       h->pass_ms[k] = 0.0;
       h->pass_n[k] = 0;

@@ -11,13 +11,17 @@
 // per-phase tables live in `g_lsh_noalloc_scratch` below.
 //
 // The array is a file-scope __device__ variable: every device that loads the
-// library holds its 64 MiB until the process exits.  Host code cannot use the
-// symbol as a device address (it is a host-side stand-in), so the first call
-// on each device looks the address up with cudaGetSymbolAddress while that
-// device is current and caches it; that first call should therefore come
-// before any stream capture.  The host side here allocates nothing either:
-// plans and per-phase tables live in fixed-size structures, the FFT tables
-// are computed on the device.
+// library holds its 72 MiB until the process exits (enough for 64^3 elasticity:
+// two rotated fields, the spectrum and the padded Gamma table take 69.6 MB).
+// Host code cannot use the symbol as a device address (it is a host-side
+// stand-in), so the first call on each device looks the address up with
+// cudaGetSymbolAddress while that device is current and caches it.  The cache
+// is not revalidated: after cudaDeviceReset the module may load elsewhere, so
+// a process that resets a device must not call this entry point on it again.
+// A call copies host tables and synchronises its stream, neither of which a
+// capturing stream allows: calls on a stream under capture are refused.  The
+// host side here allocates nothing either: plans and per-phase tables live in
+// fixed-size structures, the FFT tables are computed on the device.
 //
 // All calls share the one array and keep the last call's contents.  Nothing
 // in it needs to start at zero (every buffer is fully written before it is
@@ -35,7 +39,7 @@
 
 using namespace lsh;
 
-#define LSH_NOALLOC_SCRATCH_BYTES (64ull << 20)
+#define LSH_NOALLOC_SCRATCH_BYTES (72ull << 20)
 
 static __device__ __align__(256) unsigned char g_lsh_noalloc_scratch[LSH_NOALLOC_SCRATCH_BYTES];
 
@@ -118,6 +122,14 @@ size_t up(size_t v) { return (v + 255) / 256 * 256; }
 extern "C" lsh_status lsh_apply_noalloc(const lsh_problem* pr, const double* x, double* y, void* stream) {
   if (!pr || !x || !y || !pr->phase || !pr->phase_moduli) return LSH_ERR_INVALID_ARG;
   if (pr->phase_on_host || pr->nbatch > 1) return LSH_ERR_INVALID_ARG;
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing((cudaStream_t)stream, &cs) != cudaSuccess) {
+      cudaGetLastError();
+      return LSH_ERR_CUDA;
+    }
+    if (cs != cudaStreamCaptureStatusNone) return LSH_ERR_INVALID_ARG;  // host copies and a synchronisation follow
+  }
   if (pr->dim != 2 && pr->dim != 3) return LSH_ERR_INVALID_ARG;
   if (pr->physics != LSH_SCALAR && pr->physics != LSH_ELASTIC_ISO) return LSH_ERR_INVALID_ARG;
   if (pr->physics == LSH_ELASTIC_ISO && pr->dim != 3) return LSH_ERR_INVALID_ARG;

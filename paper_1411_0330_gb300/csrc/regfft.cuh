@@ -21,6 +21,9 @@ template <> struct RegPlan<16> { static constexpr int R1 = 4, P = 4; };
 template <> struct RegPlan<32> { static constexpr int R1 = 8, P = 4; };
 template <> struct RegPlan<64> { static constexpr int R1 = 8, P = 8; };
 template <> struct RegPlan<128> { static constexpr int R1 = 16, P = 8; };
+// radix-3 lengths (FP32 passes): R1 = 3 P keeps Q = R1 / P whole
+template <> struct RegPlan<48> { static constexpr int R1 = 12, P = 4; };
+template <> struct RegPlan<96> { static constexpr int R1 = 24, P = 4; };
 template <> struct RegPlan<256> { static constexpr int R1 = 16, P = 16; };
 
 template <typename T, int N> struct RegLine {
@@ -114,6 +117,50 @@ template <typename T, int N> struct RegLine {
   template <int ST> static __device__ __forceinline__ void inv_b_s(C2<T>* a, int t, const C2<T>* tw, const C2<T>* ex) {
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) a[k1] = ex[(k1 * P + t) * ST];
+    if (t != 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < R1; ++k1) a[k1] = cmulc<T>(a[k1], tw[t * k1]);
+    }
+    Dft<T, R1, true>::run(a, tw, N);
+  }
+  // The four steps with the exchange held in a line of N + N / R1 elements,
+  // element e at ex[e + e / R1]: the R1 values a thread writes stay adjacent,
+  // the ones it reads sit R1 + 1 apart (conflict-free for odd R1 + 1 banks).
+  static __device__ __forceinline__ int xp(int e) { return e + e / R1; }
+  static __device__ __forceinline__ void fwd_a_p(C2<T>* a, int t, const C2<T>* tw, C2<T>* ex) {
+    Dft<T, R1, false>::run(a, tw, N);
+    if (t != 0) {
+#pragma unroll
+      for (int k1 = 1; k1 < R1; ++k1) a[k1] = cmul<T>(a[k1], tw[t * k1]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) ex[xp(k1 * P + t)] = a[k1];
+  }
+  static __device__ __forceinline__ void fwd_b_p(C2<T>* a, int t, const C2<T>* tw, const C2<T>* ex) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      C2<T> b[P];
+#pragma unroll
+      for (int u = 0; u < P; ++u) b[u] = ex[t * (R1 + 1) + q * P + u];
+      Dft<T, P, false>::run(b, tw, N);
+#pragma unroll
+      for (int k2 = 0; k2 < P; ++k2) a[q * P + k2] = b[k2];
+    }
+  }
+  static __device__ __forceinline__ void inv_a_p(const C2<T>* a, int t, const C2<T>* tw, C2<T>* ex) {
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      C2<T> b[P];
+#pragma unroll
+      for (int u = 0; u < P; ++u) b[u] = a[q * P + u];
+      Dft<T, P, true>::run(b, tw, N);
+#pragma unroll
+      for (int u = 0; u < P; ++u) ex[t * (R1 + 1) + q * P + u] = b[u];
+    }
+  }
+  static __device__ __forceinline__ void inv_b_p(C2<T>* a, int t, const C2<T>* tw, const C2<T>* ex) {
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) a[k1] = ex[xp(k1 * P + t)];
     if (t != 0) {
 #pragma unroll
       for (int k1 = 1; k1 < R1; ++k1) a[k1] = cmulc<T>(a[k1], tw[t * k1]);

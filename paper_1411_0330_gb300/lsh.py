@@ -58,7 +58,8 @@ class _Opts(ctypes.Structure):
 class _TuneReport(ctypes.Structure):
     _fields_ = [("xf_variant", ctypes.c_int), ("x_variant", ctypes.c_int), ("y_variant", ctypes.c_int),
                 ("z_variant", ctypes.c_int), ("xf_ms", ctypes.c_float * 2), ("x_ms", ctypes.c_float * 4),
-                ("y_ms", ctypes.c_float * 2), ("z_ms", ctypes.c_float * 10)]
+                ("y_ms", ctypes.c_float * 2), ("z_ms", ctypes.c_float * 10), ("xy_ms", ctypes.c_float * 2),
+                ("zp_ms", ctypes.c_float * 4)]
 
 
 class _Info(ctypes.Structure):
@@ -72,7 +73,8 @@ class _Info(ctypes.Structure):
 
 class _Profile(ctypes.Structure):
     _fields_ = [("launches", ctypes.c_longlong), ("timed_iters", ctypes.c_longlong),
-                ("pass_ms", ctypes.c_double * 6), ("pass_launches", ctypes.c_longlong * 6)]
+                ("pass_ms", ctypes.c_double * 6), ("pass_launches", ctypes.c_longlong * 6),
+                ("timed_sys_iters", ctypes.c_longlong)]
 
 
 PASS_NAMES = ["x_forward", "y_forward", "z_gamma", "y_inverse", "x_inverse_local", "cg_update"]
@@ -80,7 +82,7 @@ PASS_NAMES = ["x_forward", "y_forward", "z_gamma", "y_inverse", "x_inverse_local
 EXPORTS = ["lsh_workspace_size", "lsh_setup", "lsh_set_microstructure", "lsh_apply", "lsh_solve",
            "lsh_effective", "lsh_effective_grad", "lsh_profile_enable", "lsh_profile_read", "lsh_destroy",
            "lsh_status_string", "lsh_apply_noalloc", "lsh_effective_batch", "lsh_autotune",
-           "lsh_set_variants"]
+           "lsh_set_variants", "lsh_check_bounded_wait"]
 
 
 def library_path() -> str:
@@ -117,6 +119,7 @@ def load_library(build_if_missing: bool = True):
             lib.lsh_apply_noalloc.argtypes = [P, vp, vp, vp]
             lib.lsh_autotune.argtypes = [vp, ctypes.POINTER(_TuneReport)]
             lib.lsh_set_variants.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.lsh_check_bounded_wait.argtypes = [vp, ctypes.c_double]
             lib.lsh_effective_batch.argtypes = [ctypes.c_int, ctypes.POINTER(vp), ctypes.POINTER(_Opts), dp,
                                                 ctypes.POINTER(_Info)]
             _lib = lib
@@ -374,11 +377,13 @@ class Handle:
         _check(self.lib.lsh_autotune(self._h, ctypes.byref(r)), "lsh_autotune")
         self.tune_report = {"xf_variant": r.xf_variant, "x_variant": r.x_variant, "y_variant": r.y_variant,
                             "z_variant": r.z_variant, "xf_ms": list(r.xf_ms), "x_ms": list(r.x_ms),
-                            "y_ms": list(r.y_ms), "z_ms": list(r.z_ms)}
+                            "y_ms": list(r.y_ms), "z_ms": list(r.z_ms), "xy_ms": list(r.xy_ms),
+                            "zp_ms": list(r.zp_ms)}
         return self.tune_report
 
     def set_variants(self, xf_variant, x_variant, y_variant, z_variant):
-        """Force the FP32 forward x / inverse x / y / z pass variants (see lsh_tune_report)."""
+        """Force the FP32 forward x / inverse x / y / z pass variants (see lsh_tune_report;
+        y_variant 2: the plane passes)."""
         _check(self.lib.lsh_set_variants(self._h, int(xf_variant), int(x_variant), int(y_variant), int(z_variant)),
                "lsh_set_variants")
 
@@ -392,7 +397,14 @@ class Handle:
         _check(self.lib.lsh_profile_read(self._h, ctypes.byref(p), 1 if reset else 0), "lsh_profile_read")
         return {"launches": p.launches, "timed_iters": p.timed_iters,
                 "pass_ms": {n: p.pass_ms[i] for i, n in enumerate(PASS_NAMES)},
-                "pass_launches": {n: p.pass_launches[i] for i, n in enumerate(PASS_NAMES)}}
+                "pass_launches": {n: p.pass_launches[i] for i, n in enumerate(PASS_NAMES)},
+                "timed_sys_iters": p.timed_sys_iters}
+
+    def check_bounded_wait(self, seconds=0.05):
+        """Run the give-up path of the bounded device waits on purpose (a barrier that
+        expects two arrivals gets one); returns the status code: ERR_CUDA when the wait
+        gave up and the fault word reached the host."""
+        return int(self.lib.lsh_check_bounded_wait(self._h, float(seconds)))
 
     def effective_grad(self, tau_all, W, out=None):
         """d(sum_ij W_ij e_i.A*_h e_j)/d s_beta for the per-voxel scale field."""
@@ -438,14 +450,17 @@ def effective_batch(handles, tol=1e-10, maxit=10000, solver=SOLVER_AUTO, inner_t
 
 class GridBatch:
     """Many microstructures of uneven grids (Sec. 5 computes one effective
-    tensor per microstructure): one batch handle per distinct grid, each on its
-    own CUDA stream, all solved together by lsh_effective_batch.
+    tensor per microstructure): one batch handle per distinct grid.
 
     phases: list of uint8 arrays / tensors (any grid each); the other arguments
-    as for Handle.  effective() returns the effective tensors in input order."""
+    as for Handle.  stream=None gives every grid handle its own CUDA stream and
+    effective() solves them together (lsh_effective_batch, one host thread per
+    handle); with a stream, every handle issues its work on that one stream and
+    effective() solves the grids one after the other.  effective() returns the
+    effective tensors in input order."""
 
     def __init__(self, phases, phase_moduli, physics=ELASTIC, green=FILTERED, precision=MIXED, ref=None,
-                 device=None, max_systems=0, tune=True):
+                 device=None, max_systems=0, tune=True, stream=None):
         import torch
         self._torch = torch
         groups = {}
@@ -454,13 +469,14 @@ class GridBatch:
         self.order = []
         self.handles = []
         self.streams = []
+        self.shared = stream is not None
         for shape, idx in sorted(groups.items(), key=lambda kv: -int(np.prod(kv[0])) * len(kv[1])):
             if isinstance(phases[idx[0]], np.ndarray):
                 stack = torch.from_numpy(np.stack([np.asarray(phases[i], dtype=np.uint8) for i in idx]))
             else:
                 stack = torch.stack([phases[i] for i in idx])
             dev = torch.device(device if device is not None else "cuda")
-            st = torch.cuda.Stream(device=dev)
+            st = stream if stream is not None else torch.cuda.Stream(device=dev)
             self.streams.append(st)
             self.handles.append(Handle(stack.to(dev), phase_moduli, physics=physics, green=green,
                                        precision=precision, ref=ref, device=dev, stream=st, batch=True,
@@ -468,11 +484,25 @@ class GridBatch:
             self.order.append(idx)
         self.n = len(phases)
 
+    def grid_stacks(self, phases):
+        """The phase maps regrouped as the handles hold them: one (nbatch, *grid) uint8 array per handle."""
+        return [np.stack([np.asarray(phases[i], dtype=np.uint8) for i in idx]) for idx in self.order]
+
+    def set_microstructures(self, stacks):
+        """Replace every handle's phase maps; stacks as grid_stacks() returns them (numpy, or CPU
+        tensors -- pinned memory lets the copies run asynchronously -- or device tensors)."""
+        for h, st in zip(self.handles, stacks):
+            h.set_microstructure(st)
+
     def effective(self, **kw):
-        # the phase uploads ran on the handles' streams: wait for them before solving
-        for st in self.streams:
-            st.synchronize()
-        As, Is = effective_batch(self.handles, **kw)
+        if self.shared:
+            res = [h.effective(**kw) for h in self.handles]
+            As, Is = [r[0] for r in res], [r[1] for r in res]
+        else:
+            # the phase uploads ran on the handles' streams: wait for them before solving
+            for st in self.streams:
+                st.synchronize()
+            As, Is = effective_batch(self.handles, **kw)
         A = [None] * self.n
         infos = [None] * self.n
         for idx, Ah, Ih, h in zip(self.order, As, Is, self.handles):

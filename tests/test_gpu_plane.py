@@ -1,0 +1,184 @@
+"""The FP32 plane passes (x and y transforms of a z plane in one kernel, z pass on
+the ky-major spectrum, radix-3 register FFTs for 48 and 96) against the FP64 CPU
+oracle, through the C ABI.
+
+Tolerances as for the other FP32 paths: one operator application to 2e-5 of the
+output's max norm (FP32 FFT rounding, O(eps log2 V) times the local contrast),
+C* of the mixed solver to 1e-8 of its largest entry.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from helpers import k_mu
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import oracle  # noqa: E402
+from paper_1411_0330_gb300 import lsh  # noqa: E402
+from paper_1411_0330_gb300 import microstructures as ms  # noqa: E402
+
+KM, MUM = k_mu(1.0, 0.3)
+KI, MUI = k_mu(10.0, 0.2)
+EL = np.array([[KM, MUM], [KI, MUI]])
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(np.asarray(b)).max(), 1e-300)
+
+
+def _problem(shape, physics, seed):
+    rng = np.random.default_rng(seed)
+    if physics == 1:
+        return (rng.random(shape) < 0.35).astype(np.uint8), EL
+    ph = rng.integers(0, 3, shape).astype(np.uint8)
+    return ph, np.array([np.diag(rng.uniform(1.0, 10.0, 3)) for _ in range(3)])
+
+
+PLANE_CASES = [
+    # numpy shape (nz, ny, nx): every plane length, z lengths of both FFT families,
+    # several kx tiles and the Nyquist column, scalar and elastic, all operators
+    ((16, 16, 16), 1, 1),
+    ((32, 32, 32), 1, 0),
+    ((48, 48, 48), 1, 1),
+    ((8 * 2, 96, 96), 1, 1),
+    ((96, 48, 48), 0, 1),
+    ((64, 64, 64), 0, 0),
+    ((32, 128, 128), 1, 1),
+    ((256, 32, 32), 1, 0),
+    ((48, 16, 16), 0, 2),
+    ((16, 96, 96), 0, 2),
+]
+
+
+@pytest.mark.parametrize("shape,physics,green", PLANE_CASES)
+def test_plane_apply_matches_oracle(shape, physics, green):
+    ph, mods = _problem(shape, physics, sum(shape) + physics + green)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=physics, green=green, precision=lsh.MIXED)
+    rep = h.autotune()
+    assert rep["y_variant"] in (0, 1, 2)
+    h.set_variants(0, 0, 2, 0)  # the plane passes
+    P = oracle.Problem(ph, mods, physics=physics, green=green)
+    x = np.random.default_rng(1).standard_normal(P.field_shape)
+    yo = oracle.apply(P, x)
+    for zv in (0, 6, 8, 9):
+        h.set_variants(0, 0, 2, zv)
+        y = h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy()
+        assert rel(y, yo) < 2e-5, zv
+
+
+@pytest.mark.parametrize("shape", [(16, 32, 32), (16, 64, 64), (16, 128, 128)])
+def test_plane_passes_agree_with_separate_passes(shape):
+    """On power-of-two planes both schedules are available: FP32 results within
+    FP32 rounding of each other (different transform algorithms)."""
+    ph, mods = _problem(shape, 1, 3)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
+    x = torch.from_numpy(np.random.default_rng(2).standard_normal(h.field_shape)).float().cuda()
+    h.set_variants(1, 3, 1, 0)
+    y_sep = h.apply(x).cpu().numpy()
+    h.set_variants(0, 0, 2, 0)
+    y_pl = h.apply(x).cpu().numpy()
+    assert rel(y_pl, y_sep) < 2e-5
+
+
+def test_radix3_grids_refuse_separate_passes():
+    """48 and 96 planes run the plane passes only (natural y order in every FP32 pass)."""
+    ph, mods = _problem((16, 48, 48), 1, 4)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
+    with pytest.raises(lsh.LSHError) as e:
+        h.set_variants(1, 3, 0, 0)
+    assert e.value.status == lsh.ERR_UNSUPPORTED
+    with pytest.raises(lsh.LSHError) as e:
+        h.set_variants(0, 0, 2, 1)  # TMA z tiles read the x-major spectrum only
+    assert e.value.status == lsh.ERR_UNSUPPORTED
+    assert h.autotune()["y_variant"] == 2
+
+
+def _golden(name):
+    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_cstar.json")) as fh:
+        g = json.load(fh)[name]
+    ph, _, _ = ms.sphere_microstructure(g["n"], g["radius"], g["fraction"], seed=g["seed"])
+    assert abs(ph.mean() - g["realised_fraction"]) < 1e-12  # the same seeded geometry
+    return ph, np.array(g["moduli_K_mu"]), g["green"], np.array(g["cstar_mandel"])
+
+
+@pytest.mark.parametrize("n,green", [(32, 0), (16, 1)])
+def test_plane_mixed_effective_matches_oracle(n, green):
+    """The mixed solver (FP32 inner CG on the plane passes, FP64 refinement) reaches
+    the oracle's C* to the mixed tolerance on a seeded sphere packing."""
+    ph, _, _ = ms.sphere_microstructure(n, n / 8.0, 0.25, seed=100 + n)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=green, precision=lsh.MIXED)
+    h.set_variants(0, 0, 2, 0)
+    A, infos = h.effective(tol=1e-10)
+    Ao, _ = oracle.effective(oracle.Problem(ph, EL, physics=1, green=green), tol=1e-13)
+    assert rel(A, Ao) < 1e-8, rel(A, Ao)
+    assert all(i["status"] == 0 for i in infos)
+
+
+@pytest.mark.parametrize("precision", [lsh.MIXED, lsh.FP64])
+def test_radix3_effective_48_matches_stored_oracle(precision):
+    """48^3 (a radix-3 grid of the batched configuration): C* of the mixed solver (plane
+    passes) and of the FP64 solver against the oracle's, stored by
+    tests/golden/make_oracle_cstar.py."""
+    ph, mods, green, Ao = _golden("spheres48_f25_s148_filtered")
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.ELASTIC, green=green, precision=precision)
+    A, infos = h.effective(tol=1e-11)
+    assert rel(A, Ao) < (1e-8 if precision == lsh.MIXED else 1e-10), rel(A, Ao)
+    assert all(i["status"] == 0 for i in infos)
+
+
+def test_plane_cg_graphs_equal_direct_launches():
+    """CUDA-graph replay of the plane-pass CG iterations is bit-identical to launching
+    the kernels one by one (the reductions are deterministic)."""
+    ph, _, _ = ms.sphere_microstructure(32, 4.0, 0.25, seed=5)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
+    h.set_variants(0, 0, 2, 0)
+    A1, I1 = h.effective(tol=1e-10, graphs=True)
+    A2, I2 = h.effective(tol=1e-10, graphs=False)
+    assert np.array_equal(A1, A2)
+    assert [i["iters"] for i in I1] == [i["iters"] for i in I2]
+
+
+@pytest.mark.parametrize("kind", ["scale", "fraction"])
+def test_plane_apply_with_voxel_fields(kind):
+    """Per-voxel scale s (A = s A_phase) and volume fractions (Eq. (def_ah)) enter the
+    local term of the plane inverse pass."""
+    rng = np.random.default_rng(9)
+    shape = (16, 48, 48)
+    ph = (rng.random(shape) < 0.3).astype(np.uint8)
+    f = rng.uniform(0.5, 2.0, shape).astype(np.float32) if kind == "scale" else \
+        rng.uniform(0.0, 1.0, shape).astype(np.float32)
+    ref = np.array([0.25 * KM, 0.25 * MUM])
+    if kind == "scale":
+        h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, ref=ref,
+                       precision=lsh.MIXED, scale=torch.from_numpy(f).cuda())
+        P = oracle.Problem(ph, EL, physics=1, green=1, ref=ref, scale=f.astype(np.float64))
+    else:
+        ph0 = np.zeros_like(ph)
+        h = lsh.Handle(torch.from_numpy(ph0).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, ref=ref,
+                       precision=lsh.MIXED, fraction=torch.from_numpy(f).cuda())
+        P = oracle.Problem(ph0, EL, physics=1, green=1, ref=ref, frac=f.astype(np.float64))
+    h.set_variants(0, 0, 2, 0)
+    x = rng.standard_normal(P.field_shape)
+    y = h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy()
+    assert rel(y, oracle.apply(P, x)) < 2e-5
+
+
+def test_plane_batched_microstructures_match_oracle():
+    """Several microstructures of one 48^3 grid in one batch handle (system-major
+    planes, per-system reductions, waves of 12 systems) give each microstructure's
+    stored oracle C*."""
+    cases = [_golden(k) for k in ("spheres48_f15_s1_r3_filtered", "spheres48_f30_s2_r3_filtered",
+                                  "spheres48_f25_s3_r3_filtered")]
+    stack = np.stack([c[0] for c in cases])
+    h = lsh.Handle(torch.from_numpy(stack).cuda(), cases[0][1], physics=lsh.ELASTIC, green=cases[0][2],
+                   precision=lsh.MIXED, batch=True, max_systems=12)
+    A, infos = h.effective(tol=1e-10)
+    for b, c in enumerate(cases):
+        assert rel(A[b], c[3]) < 1e-8, (b, rel(A[b], c[3]))
