@@ -79,8 +79,11 @@ enum { LSH_F64 = 0, LSH_F32 = 1, LSH_F64_DF = 2 };
  * BASIC: the fixed-point scheme of Moulinec and Suquet written on the
  * polarisation, tau <- tau + (A - A0)(b - K tau) (FP64; converges when A0 lies
  * between the phases, e.g. the mean of the extreme moduli, at the rate
- * (A_max - A_min) / (A_max + A_min) for that choice). */
-enum { LSH_SOLVER_AUTO = 0, LSH_SOLVER_CG = 1, LSH_SOLVER_MINRES = 2, LSH_SOLVER_BASIC = 3 };
+ * (A_max - A_min) / (A_max + A_min) for that choice); SYMMLQ: the Lanczos
+ * method of Paige and Saunders for symmetric indefinite systems that the paper
+ * names (Sec. 1), FP64, same buffers and limits as MINRES, stopping on the
+ * residual estimate of its CG point, which it returns. */
+enum { LSH_SOLVER_AUTO = 0, LSH_SOLVER_CG = 1, LSH_SOLVER_MINRES = 2, LSH_SOLVER_BASIC = 3, LSH_SOLVER_SYMMLQ = 4 };
 
 /* Problem description (Sec. 2.2 and Sec. 3).  All pointers are read during
  * lsh_setup only. */
@@ -119,7 +122,7 @@ typedef struct lsh_problem {
 typedef struct lsh_solve_opts {
   double tol;        /* stop when ||b - K tau||_2 <= tol ||b||_2 (Sec. 5 uses 1e-5)    */
   int maxit;         /* iteration limit (FP64 CG iterations, or inner iterations summed) */
-  int solver;        /* LSH_SOLVER_AUTO, _CG, _MINRES or _BASIC                            */
+  int solver;        /* LSH_SOLVER_AUTO, _CG, _MINRES, _BASIC or _SYMMLQ                   */
   double inner_tol;  /* LSH_MIXED: relative residual reduction of each inner solve
                         (<= 0 selects 0.5 sqrt(tol) within [1e-6, 1e-3]: two
                         refinement steps)                                               */

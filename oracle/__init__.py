@@ -25,7 +25,7 @@ _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liblsh_oracle.so")
 
 SCALAR, ELASTIC = 0, 1
-TRUNCATED, FILTERED, FINITE_DIFF = 0, 1, 2
+TRUNCATED, FILTERED, FINITE_DIFF, CONSISTENT = 0, 1, 2, 3
 SOLVER_AUTO, SOLVER_CG, SOLVER_MINRES = 0, 1, 2
 _STATUS = {0: "ok", 1: "invalid argument", 2: "A_beta - A0 singular", 3: "A0 not SPD",
            4: "breakdown", 5: "not converged", 6: "problem too large", 7: "out of memory"}

@@ -264,6 +264,73 @@ void or_gamma0(const or_problem *p, const double xi[3], double *G) {
   }
 }
 
+/* Consistent discrete Green operator, Eq. (11), 2D scalar, A0 = diag(a1, a2):
+ *   G_k = sum_{n in Z^2} F(2 pi (k/N + n))^2 Gamma0(k/N + n),
+ *   F(2 pi (x + n))^2 = prod_i sin^2(pi x_i) / (pi (x_i + n_i))^2,  x = k / N,
+ *   Gamma0(xi) = xi xi^T / (a1 xi_1^2 + a2 xi_2^2).
+ * Write s_i = sin(pi x_i), y = x2 + n2, u = x1 + n1, b = sqrt(a2 / a1) |y|.  For
+ * fixed n2 the sums over n1 are classical lattice sums:
+ *   A(x, b) = sum_n 1 / ((x + n)^2 + b^2)       = (pi / b) sinh(2 pi b) / (cosh(2 pi b) - cos(2 pi x)),
+ *   U(x, b) = sum_n (x + n) / ((x + n)^2 + b^2) = pi sin(2 pi x) / (cosh(2 pi b) - cos(2 pi x)),
+ *   sum_n 1 / (x + n) = pi cot(pi x) (symmetric),  sum_n 1 / (x + n)^2 = pi^2 / s^2,
+ * and partial fractions give, with T = sum_n2 s2^2 / (pi y)^2 * s1^2 / pi^2 * A(x1, b),
+ *   G11 = T / a1,   G22 = (1 - T) / a2   (sum_n2 s2^2 / (pi y)^2 = 1),
+ *   G12 = sum_n2 s2^2 / (pi^2 y) * s1^2 / (pi^2 a1 b^2) * (pi cot(pi x1) - U(x1, b)).
+ * Once 2 pi b >= 40, A = pi / b and U = 0 to double precision, so the terms with
+ * |n2| > M0 are power sums of 1 / y^3, taken from the Hurwitz zeta function
+ * Z3(q) = sum_{j >= 0} (q + j)^-3 (direct sum, then the Euler-Maclaurin tail).
+ * Axis frequencies (x1 = 0 or x2 = 0) keep the single n term whose weight does
+ * not vanish. */
+static double hurwitz3(double q) {
+  double s = 0.0;
+  for (int j = 0; j < 50; ++j) s += 1.0 / ((q + j) * (q + j) * (q + j));
+  const double a = q + 50.0, a2 = a * a;
+  /* integral, f(a)/2 and the B2, B4, B6 terms of Euler-Maclaurin for x^-3 */
+  return s + 1.0 / (2.0 * a2) + 1.0 / (2.0 * a2 * a) + 1.0 / (4.0 * a2 * a2) - 1.0 / (12.0 * a2 * a2 * a2) +
+         1.0 / (12.0 * a2 * a2 * a2 * a2);
+}
+static double lat_A(double x, double b) {
+  double e = exp(-2.0 * OR_PI * b), e2 = e * e;
+  return OR_PI / b * (1.0 - e2) / (1.0 + e2 - 2.0 * e * cos(2.0 * OR_PI * x));
+}
+static double lat_U(double x, double b) {
+  double e = exp(-2.0 * OR_PI * b), e2 = e * e;
+  return OR_PI * 2.0 * e * sin(2.0 * OR_PI * x) / (1.0 + e2 - 2.0 * e * cos(2.0 * OR_PI * x));
+}
+static void gamma_consistent_2d(double a1, double a2, const int k[3], const int n[3], double *G) {
+  G[0] = G[1] = G[2] = G[3] = 0.0;
+  const int k1 = k[0] % n[0], k2 = k[1] % n[1];
+  if (k1 == 0 && k2 == 0) return;
+  if (k2 == 0) { /* only n2 = 0 survives: xi = (x1 + n1, 0), weights summing to 1 */
+    G[0] = 1.0 / a1;
+    return;
+  }
+  if (k1 == 0) {
+    G[3] = 1.0 / a2;
+    return;
+  }
+  const double x1 = (double)k1 / n[0], x2 = (double)k2 / n[1];
+  const double s1 = sin(OR_PI * x1), s2 = sin(OR_PI * x2), pi2 = OR_PI * OR_PI;
+  const double r = sqrt(a2 / a1);
+  const long M0 = (long)ceil(40.0 / (2.0 * OR_PI * r)) + 1;
+  const double cot1 = cos(OR_PI * x1) / s1;
+  ksum T, C;
+  T.s = T.c = C.s = C.c = 0.0;
+  for (long n2 = -M0; n2 <= M0; ++n2) {
+    const double y = x2 + (double)n2, b = r * fabs(y);
+    const double w2 = s2 * s2 / (pi2 * y * y);
+    ksum_add(&T, w2 * s1 * s1 / pi2 * lat_A(x1, b));
+    ksum_add(&C, w2 * s1 * s1 * y / (pi2 * a1 * b * b) * (OR_PI * cot1 - lat_U(x1, b)));
+  }
+  const double zp = hurwitz3((double)(M0 + 1) + x2), zm = hurwitz3((double)(M0 + 1) - x2);
+  ksum_add(&T, s1 * s1 * s2 * s2 / (pi2 * OR_PI * r) * (zp + zm));
+  ksum_add(&C, s1 * s1 * s2 * s2 * cot1 / (pi2 * OR_PI * a2) * (zp - zm));
+  const double t = ksum_get(&T);
+  G[0] = t / a1;
+  G[3] = (1.0 - t) / a2;
+  G[1] = G[2] = ksum_get(&C);
+}
+
 void or_gamma_hat(const or_problem *p, const int k[3], double *G) {
   int c = or_ncomp(p), n[3];
   grid_dims(p, n);
@@ -313,6 +380,10 @@ void or_gamma_hat(const or_problem *p, const int k[3], double *G) {
       or_gamma0(p, xi, g);
       for (int i = 0; i < c * c; ++i) G[2 * i] += w * g[i];
     }
+  } else if (p->green == OR_CONSISTENT) {
+    double g2[4];
+    gamma_consistent_2d(p->ref_moduli[0], p->ref_moduli[3], k, n, g2);
+    for (int i = 0; i < 4; ++i) G[2 * i] = g2[i];
   } else {
     /* Sec. 3.2.3 (scalar problems): V_k V_k^H / (V_k^H A0 V_k) with
      * V_k,i = exp(2 i pi k_i / N_i) - 1. */
@@ -467,6 +538,9 @@ static int check_problem(const or_problem *p) {
   if (p->dim != 2 && p->dim != 3) return OR_ERR_ARG;
   if (p->physics == OR_ELASTIC && p->dim != 3) return OR_ERR_ARG;
   if (p->physics == OR_ELASTIC && p->green == OR_FINITE_DIFF) return OR_ERR_ARG;
+  if (p->green == OR_CONSISTENT &&
+      (p->physics != OR_SCALAR || p->dim != 2 || p->ref_moduli[1] != 0.0 || p->ref_moduli[2] != 0.0))
+    return OR_ERR_ARG;
   for (int i = 0; i < p->dim; ++i)
     if (p->n[i] < 1) return OR_ERR_ARG;
   if (!p->ref_moduli || !p->phase_moduli || !p->phase || p->nphase < 1) return OR_ERR_ARG;

@@ -29,7 +29,9 @@ extern "C" {
 #endif
 
 enum { OR_SCALAR = 0, OR_ELASTIC = 1 };
-enum { OR_TRUNCATED = 0, OR_FILTERED = 1, OR_FINITE_DIFF = 2 };
+/* OR_CONSISTENT: the consistent discrete Green operator of Eq. (11) (2D scalar
+ * problems with a diagonal A0 only; not a GPU operator: a check of the others) */
+enum { OR_TRUNCATED = 0, OR_FILTERED = 1, OR_FINITE_DIFF = 2, OR_CONSISTENT = 3 };
 enum { OR_SOLVER_AUTO = 0, OR_SOLVER_CG = 1, OR_SOLVER_MINRES = 2 };
 enum {
   OR_OK = 0,
@@ -46,7 +48,7 @@ typedef struct {
   int dim;                     /* 2 or 3 */
   int n[3];                    /* cells per axis; n[2] is ignored for dim 2 */
   int physics;                 /* OR_SCALAR (c = dim) or OR_ELASTIC (dim 3, c = 6) */
-  int green;                   /* OR_TRUNCATED, OR_FILTERED, OR_FINITE_DIFF */
+  int green;                   /* OR_TRUNCATED, OR_FILTERED, OR_FINITE_DIFF, OR_CONSISTENT */
   int nphase;
   const double *phase_moduli;  /* scalar: dim*dim symmetric matrix per phase;
                                   elastic: (bulk K, shear mu) per phase        */

@@ -206,4 +206,16 @@ struct MinresScalars {
   int pad;
 };
 
+// Scalars of one system's SYMMLQ recurrence (Lanczos as for MINRES, whose
+// MinresScalars keep beta1, beta, oldb and alfa; LQ factorisation of the
+// tridiagonal matrix by rotations from the right, Paige-Saunders 1975).
+struct SymmlqScalars {
+  double gbar, dbar, rhs1, rhs2;
+  double bstep, snprod;     // step along the first Lanczos vector, product of the sines
+  double s, t, cs, sn;      // this iteration's update x += s w + t v, w <- sn w - cs v
+  double zbar, cb;          // at exit: x += zbar w + cb b (the CG point)
+  int pending;
+  int pad;
+};
+
 }  // namespace lsh

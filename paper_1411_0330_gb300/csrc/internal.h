@@ -79,6 +79,8 @@ template <typename T> struct OpArgs {
   int plane;
   int tlay;
   C2<T>* nq;
+  int l2pf;  // plane passes, input planes requested into L2 at a block's start: bit 0 the
+             // forward pass's x, r, p; bit 1 the inverse pass's p and phase planes
 };
 
 // Thread-block sizes and tile shapes, chosen at setup for one system count.
@@ -136,6 +138,10 @@ void launch_minres_begin(SolverState* st, MinresScalars* ms, const double* rhs2,
                          cudaStream_t s);
 void launch_minres_step(double* x, double* r1, double* r2, double* q, double* wa, double* wb, long long n, int S,
                         SolverState* st, MinresScalars* ms, double* partials, int G, cudaStream_t s);
+void launch_symmlq_begin(SymmlqScalars* sq, int S, cudaStream_t s);
+void launch_symmlq_step(double* x, double* r1, double* r2, double* q, double* w, const double* b, long long n, int S,
+                        SolverState* st, MinresScalars* ms, SymmlqScalars* sq, double* partials, int G,
+                        cudaStream_t s);
 template <typename T> void set_smem_attrs();
 template <typename T> void set_smem_attrs_reg();
 template <typename T> void launch_yfft_reg(const OpArgs<T>& a, bool inv, const SolverState* st, cudaStream_t s);
@@ -151,6 +157,7 @@ struct DF;
 struct DF2;
 bool df_supported(const OpArgs<double>& a);
 void launch_d2df(const double* in, DF* out, long long n, cudaStream_t s);
+void launch_d2df_inplace(void* buf, long long n, cudaStream_t s);
 void launch_df_x(const OpArgs<double>& a, const DF2* twx, int mode, const double* in, double* out, SolverState* st,
                  double* partials, cudaStream_t s);
 void launch_df_z(const OpArgs<DF>& a, cudaStream_t s);

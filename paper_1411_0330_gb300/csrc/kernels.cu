@@ -549,6 +549,117 @@ __global__ void __launch_bounds__(kThreads) k_mr_c(double* __restrict__ x, doubl
   }
 }
 
+// ------------------------------------------------------------------ SYMMLQ vector kernels
+// The Lanczos step is MINRES's (k_mr_a, then the first half of k_sq_b); the
+// tridiagonal T_k is factorised T_k = L_k Q_k by rotations from the right,
+// each iteration adds s w + t v to the LQ iterate and turns w, and at
+// convergence the CG point x_LQ + zbar w + cb b (cb: the accumulated step
+// along the first Lanczos vector b / beta1) is taken.  The estimate of the CG
+// point's residual norm is |snprod beta1 beta / gbar|.
+__global__ void __launch_bounds__(kThreads) k_sq_b(double* __restrict__ q, double* __restrict__ r1,
+                                                   double* __restrict__ r2, long long n,
+                                                   SolverState* __restrict__ st, MinresScalars* __restrict__ ms,
+                                                   SymmlqScalars* __restrict__ sq, double* __restrict__ partials) {
+  const int s = blockIdx.y;
+  SolverState* sst = st + s;
+  if (sst->done) return;
+  const double c2 = ms[s].alfa / ms[s].beta;
+  double* qs = q + s * n;
+  double* r1s = r1 + s * n;
+  double* r2s = r2 + s * n;
+  double acc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double y = qs[i] - c2 * r2s[i];
+    r1s[i] = r2s[i];
+    r2s[i] = y;
+    acc += y * y;
+  }
+  const double tot = block_sum(acc);
+  double* part = partials + (long long)s * gridDim.x;
+  if (publish_partial_sys(part, blockIdx.x, gridDim.x, tot, &sst->counter[2])) {
+    const double yy = gather_partials_sys(part, gridDim.x, &sst->counter[2]);
+    if (threadIdx.x == 0) {
+      MinresScalars& m = ms[s];
+      SymmlqScalars& l = sq[s];
+      const double bnew = sqrt(fmax(yy, 0.0));
+      m.oldb = m.beta;
+      m.beta = bnew;
+      if (sst->iter == 0) {
+        l.gbar = m.alfa;
+        l.dbar = bnew;
+        l.rhs1 = m.beta1;
+        l.rhs2 = 0.0;
+        l.bstep = 0.0;
+        l.snprod = 1.0;
+        l.s = l.t = 0.0;  // no update of x or w on the first step
+        l.cs = 0.0;
+        l.sn = 1.0;
+      } else {
+        const double gamma = fmax(hypot(l.gbar, m.oldb), 1e-300);
+        const double cs = l.gbar / gamma, sn = m.oldb / gamma;
+        const double delta = cs * l.dbar + sn * m.alfa;
+        l.gbar = sn * l.dbar - cs * m.alfa;
+        const double epsln = sn * bnew;
+        l.dbar = -cs * bnew;
+        const double z = l.rhs1 / gamma;
+        l.s = z * cs;
+        l.t = z * sn;
+        l.cs = cs;
+        l.sn = sn;
+        l.bstep += l.snprod * cs * z;
+        l.snprod *= sn;
+        l.rhs1 = l.rhs2 - delta * z;
+        l.rhs2 = -epsln * z;
+      }
+      sst->iter += 1;
+      const double cg = l.gbar != 0.0 ? fabs(l.snprod * m.beta1 * bnew / l.gbar) : (bnew == 0.0 ? 0.0 : INFINITY);
+      sst->rr = cg * cg;  // CG-point residual norm estimate, squared
+      if (!isfinite(yy) || !isfinite(l.rhs1)) {
+        sst->status = 5;
+        sst->done = 1;
+      } else if (cg * cg <= sst->tol2 || bnew == 0.0) {
+        l.zbar = l.gbar != 0.0 ? l.rhs1 / l.gbar : 0.0;
+        l.cb = (l.bstep + l.snprod * l.zbar) / m.beta1;
+        l.pending = 1;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) k_sq_c(double* __restrict__ x, double* __restrict__ w,
+                                                   const double* __restrict__ b, const double* __restrict__ r1,
+                                                   long long n, SolverState* __restrict__ st,
+                                                   const MinresScalars* __restrict__ ms,
+                                                   const SymmlqScalars* __restrict__ sq, double* __restrict__ partials) {
+  const int s = blockIdx.y;
+  SolverState* sst = st + s;
+  if (sst->done) return;
+  const SymmlqScalars l = sq[s];
+  const double iv = 1.0 / ms[s].oldb;  // v = r1 / oldb (r1 holds the previous r2)
+  double* xs = x + s * n;
+  double* ws = w + s * n;
+  const double* bs = b + s * n;
+  const double* r1s = r1 + s * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = r1s[i] * iv, wo = ws[i];
+    const double wn = l.sn * wo - l.cs * v;
+    double xv = xs[i] + l.s * wo + l.t * v;
+    if (l.pending) xv += l.zbar * wn + l.cb * bs[i];
+    xs[i] = xv;
+    ws[i] = wn;
+  }
+  double* part = partials + (long long)s * gridDim.x;
+  if (publish_partial_sys(part, blockIdx.x, gridDim.x, 0.0, &sst->counter[3])) {
+    gather_partials_sys(part, gridDim.x, &sst->counter[3]);
+    if (threadIdx.x == 0 && l.pending) sst->done = 1;
+  }
+}
+
+__global__ void k_sq_begin(SymmlqScalars* __restrict__ sq, int S) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s < S) sq[s] = SymmlqScalars{};
+}
+
 // Basic fixed-point scheme (Moulinec-Suquet): with r = b - K tau, the update
 // tau += (A - A0) r equals tau_new = (A - A0)(b - Gamma tau), the classic
 // iteration written on the polarisation.  Grid (G, S); systems whose flag is
@@ -1167,6 +1278,16 @@ void launch_minres_begin(SolverState* st, MinresScalars* ms, const double* rhs2,
                          cudaStream_t s) {
   k_mr_begin<<<(S + 127) / 128, 128, 0, s>>>(st, ms, rhs2, bb, tol, S);
 }
+void launch_symmlq_begin(SymmlqScalars* sq, int S, cudaStream_t s) { k_sq_begin<<<(S + 127) / 128, 128, 0, s>>>(sq, S); }
+
+void launch_symmlq_step(double* x, double* r1, double* r2, double* q, double* w, const double* b, long long n, int S,
+                        SolverState* st, MinresScalars* ms, SymmlqScalars* sq, double* partials, int G,
+                        cudaStream_t s) {
+  k_mr_a<<<dim3(G, S), kThreads, 0, s>>>(q, r1, r2, n, st, ms, partials);
+  k_sq_b<<<dim3(G, S), kThreads, 0, s>>>(q, r1, r2, n, st, ms, sq, partials);
+  k_sq_c<<<dim3(G, S), kThreads, 0, s>>>(x, w, b, r1, n, st, ms, sq, partials);
+}
+
 void launch_minres_step(double* x, double* r1, double* r2, double* q, double* wa, double* wb, long long n, int S,
                         SolverState* st, MinresScalars* ms, double* partials, int G, cudaStream_t s) {
   k_mr_a<<<dim3(G, S), kThreads, 0, s>>>(q, r1, r2, n, st, ms, partials);

@@ -107,7 +107,7 @@ __global__ void __launch_bounds__(128) k_df_xfwd(OpArgs<double> a, const DF2* __
     ya.x = ya.y = yb.x = yb.y = DF(0.f, 0.f);
     if (kx < nxh) {
       const DF2 z1 = Zs[ln * ZS + kx];
-      const DF2 z2 = Zs[ln * ZS + ((N - kx) & (N - 1))];
+      const DF2 z2 = Zs[ln * ZS + (kx == 0 ? 0 : N - kx)];
       ya.x = df_scale2(z1.x + z2.x, 0.5f);
       ya.y = df_scale2(z1.y - z2.y, 0.5f);
       yb.x = df_scale2(z1.y + z2.y, 0.5f);
@@ -326,6 +326,8 @@ template <bool INV, int N> void launch_df_zfft_n(const OpArgs<DF>& a, cudaStream
 
 template <bool INV> void launch_df_zfft(const OpArgs<DF>& a, cudaStream_t s) {
   switch (a.nz) {
+    case 48: launch_df_zfft_n<INV, 48>(a, s); break;
+    case 96: launch_df_zfft_n<INV, 96>(a, s); break;
     case 16: launch_df_zfft_n<INV, 16>(a, s); break;
     case 32: launch_df_zfft_n<INV, 32>(a, s); break;
     case 64: launch_df_zfft_n<INV, 64>(a, s); break;
@@ -344,7 +346,7 @@ void launch_df_z(const OpArgs<DF>& a, cudaStream_t s) {
   launch_df_zfft<true>(a, s);
 }
 
-bool df_length(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 256; }
+bool df_length(int n) { return n == 16 || n == 32 || n == 48 || n == 64 || n == 96 || n == 128 || n == 256; }
 
 // The double-float passes cover 3D grids whose three lengths have register
 // plans and operators without finite-difference phases.
@@ -356,6 +358,20 @@ void launch_d2df(const double* in, DF* out, long long n, cudaStream_t s) {
   if (n <= 0) return;
   const long long g = std::min<long long>((n + 255) / 256, 4096);
   k_d2df<<<(unsigned)g, 256, 0, s>>>(in, out, n);
+}
+
+// FP64 values converted to double-float pairs in place (both 8 bytes per value).
+__global__ void k_d2df_inplace(void* buf, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double v = reinterpret_cast<const double*>(buf)[i];
+    reinterpret_cast<DF*>(buf)[i] = df_from(v);
+  }
+}
+
+void launch_d2df_inplace(void* buf, long long n, cudaStream_t s) {
+  if (n <= 0) return;
+  const long long g = std::min<long long>((n + 255) / 256, 4096);
+  k_d2df_inplace<<<(unsigned)g, 256, 0, s>>>(buf, n);
 }
 
 template <int N> void launch_df_x_n(const OpArgs<double>& a, const DF2* twx, int mode, const double* in, double* out,
@@ -374,6 +390,8 @@ template <int N> void launch_df_x_n(const OpArgs<double>& a, const DF2* twx, int
 void launch_df_x(const OpArgs<double>& a, const DF2* twx, int mode, const double* in, double* out, SolverState* st,
                  double* partials, cudaStream_t s) {
   switch (a.nx) {
+    case 48: launch_df_x_n<48>(a, twx, mode, in, out, st, partials, s); break;
+    case 96: launch_df_x_n<96>(a, twx, mode, in, out, st, partials, s); break;
     case 16: launch_df_x_n<16>(a, twx, mode, in, out, st, partials, s); break;
     case 32: launch_df_x_n<32>(a, twx, mode, in, out, st, partials, s); break;
     case 64: launch_df_x_n<64>(a, twx, mode, in, out, st, partials, s); break;
@@ -396,6 +414,8 @@ template <int N> void df_attrs_n() {
 void df_prepare() {
   df_attrs_n<16>();
   df_attrs_n<32>();
+  df_attrs_n<48>();
+  df_attrs_n<96>();
   df_attrs_n<64>();
   df_attrs_n<128>();
   df_attrs_n<256>();

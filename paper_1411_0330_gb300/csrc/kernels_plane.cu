@@ -252,6 +252,16 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH) k_xyfwd(OpArgs<float> a, cons
     alpha = (float)st[s].alpha;
     beta = (float)st[s].beta;
   }
+  // optionally the block's input planes go to L2 in a few large requests first
+  // (off by default: measured slower for this pass)
+  if ((a.l2pf & 1) && threadIdx.x < 32) {
+    constexpr uint32_t PB = (uint32_t)(sizeof(float) * N * N);
+    constexpr uint32_t CH = PB / 8;  // 8 requests per plane
+    const int w = threadIdx.x & 7, arr = threadIdx.x >> 3;
+    const float* src = MODE == 0 ? (arr == 0 ? in : nullptr)
+                                 : (arr == 0 ? r : (k > 0 ? (arr == 1 ? p : (arr == 2 ? x : nullptr)) : nullptr));
+    if (src) bulk_prefetch_l2(reinterpret_cast<const char*>(src + plane) + w * CH, CH);
+  }
   if (MODE == 0) __syncthreads();  // aloc
 #pragma unroll 4
   for (int it = 0; it < PC::IT; ++it) {
@@ -334,6 +344,14 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH) k_xyinv(OpArgs<float> a, cons
   const int ntab = a.nphase * a.c;
   for (int u = threadIdx.x; u < ntab; u += TH) mloc[u] = (a.scale && !a.frac) ? a.modtab[u] : a.mtab[u];
   for (int u = threadIdx.x; u < a.nphase; u += TH) aloc[u] = a.act[u];
+  // the epilogue's p plane and phase plane go to L2 while the transforms run
+  const long long plane = (long long)blockIdx.x * N * N;
+  const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V + (long long)z * N * N;
+  if ((a.l2pf & 2) && threadIdx.x < 9) {
+    constexpr uint32_t PB = (uint32_t)(sizeof(float) * N * N);
+    if (threadIdx.x < 8) bulk_prefetch_l2(reinterpret_cast<const char*>(xin + plane) + threadIdx.x * (PB / 8), PB / 8);
+    else if ((pbase & 15) == 0) bulk_prefetch_l2(a.phase + pbase, (uint32_t)(N * N));
+  }
   float2 nqv = make_float2(0.f, 0.f);
   if (threadIdx.x < N) nqv = a.nq[(long long)blockIdx.x * N + threadIdx.x];
   if (__syncthreads_or(!mbar_wait(&bar, 0))) {
@@ -349,8 +367,6 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH) k_xyinv(OpArgs<float> a, cons
   plane_y_inv<N>(PL, tw);
   plane_x_inv<N>(PL, tw);
   __syncthreads();
-  const long long plane = (long long)blockIdx.x * N * N;
-  const long long pbase = (long long)((a.sys0 + s) / a.sys_per_ms) * a.V + (long long)z * N * N;
   Acc<float> acc;
 #pragma unroll 4
   for (int it = 0; it < PC::IT; ++it) {

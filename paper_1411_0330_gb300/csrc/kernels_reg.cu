@@ -408,6 +408,17 @@ template <typename T, bool INV, int N> void launch_y_n(const OpArgs<T>& a, const
 }
 
 template <typename T, bool INV> void launch_y_reg(const OpArgs<T>& a, const SolverState* st, cudaStream_t s) {
+  if constexpr (is_df<T>::value) {
+    // radix-3 lengths of the double-float refinement residual
+    if (a.ny == 48) {
+      launch_y_n<T, INV, 48>(a, st, s);
+      return;
+    }
+    if (a.ny == 96) {
+      launch_y_n<T, INV, 96>(a, st, s);
+      return;
+    }
+  }
   switch (a.ny) {
     case 16: launch_y_n<T, INV, 16>(a, st, s); break;
     case 32: launch_y_n<T, INV, 32>(a, st, s); break;
@@ -599,6 +610,10 @@ template <typename T, bool INV> void attr_y() {
   attr_y_n<T, INV, 64>();
   attr_y_n<T, INV, 128>();
   attr_y_n<T, INV, 256>();
+  if constexpr (is_df<T>::value) {
+    attr_y_n<T, INV, 48>();
+    attr_y_n<T, INV, 96>();
+  }
 }
 template <typename T> void set_smem_attrs_reg() {
   attr_y<T, false>();

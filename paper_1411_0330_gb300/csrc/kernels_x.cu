@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(256, 2) k_xfwd_reg(OpArgs<float> a, const floa
     float2 xa = make_float2(0.f, 0.f), xb = xa;
     if (kx < nxh) {
       const float2 z1 = Zs[ln * ZS + kx];
-      const float2 z2 = Zs[ln * ZS + ((N - kx) & (N - 1))];
+      const float2 z2 = Zs[ln * ZS + (kx == 0 ? 0 : N - kx)];
       xa = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
       xb = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
     }

@@ -401,8 +401,11 @@ bool reg_len(int n) { return n == 16 || n == 32 || n == 64 || n == 128 || n == 2
 // plans, for tabulated operators without finite-difference phases and phase
 // maps without per-voxel scale or fraction fields (those keep the FP64 residual).
 bool df_eligible(const Derived& d) {
-  return d.precision == LSH_MIXED && d.dim == 3 && reg_len(d.nx) && reg_len(d.ny) && reg_len(d.nz) &&
-         d.green != LSH_GREEN_FD && (d.c == 3 || d.c == 6) && !d.has_scale;
+  // powers of two; the radix-3 lengths 48 and 96 on grids with the plane passes,
+  // whose FP32 spectrum order (natural along y and z) the double-float table follows
+  const bool pow2 = reg_len(d.nx) && reg_len(d.ny) && reg_len(d.nz);
+  return d.precision == LSH_MIXED && d.dim == 3 && (pow2 || d.plane) && d.green != LSH_GREEN_FD &&
+         (d.c == 3 || d.c == 6) && !d.has_scale;
 }
 
 Layout make_layout(const Derived& d) {
@@ -456,7 +459,7 @@ Layout make_layout(const Derived& d) {
   }
   l.off_wa = take(l.minres ? sizeof(double) * (size_t)(S * n) : 0);
   l.off_wb = take(l.minres ? sizeof(double) * (size_t)(S * n) : 0);
-  l.off_ms = take(sizeof(MinresScalars) * (size_t)S);
+  l.off_ms = take((sizeof(MinresScalars) + sizeof(SymmlqScalars)) * (size_t)S);
   l.off_Hd = take(sizeof(double2) * (size_t)(S * d.c * nfh));
   const int ncop = (d.ncoef + 3) & ~3;  // Gamma coefficients per frequency, padded
   l.off_gd = take(sizeof(double) * (size_t)(ncop * nf));
@@ -497,6 +500,7 @@ struct lsh_handle {
   int device = 0;
   double *wa = nullptr, *wb = nullptr;  // MINRES direction fields (null: not available)
   MinresScalars* ms = nullptr;
+  SymmlqScalars* sq = nullptr;  // after the S MinresScalars
   int* fault = nullptr;  // device word set by a kernel whose bounded wait ran out
   bool no_tma = false;
   Layout lay;
@@ -642,6 +646,10 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
   a.plane = 0;
   a.tlay = 0;
   a.nq = nullptr;
+  // measured on the batched workload: the inverse pass gains (0.61 -> 0.66 of the
+  // copy bandwidth), the forward pass loses (0.81 -> 0.70); LSH_L2PF overrides
+  a.l2pf = 2;
+  if (const char* e = getenv("LSH_L2PF")) a.l2pf = atoi(e) & 3;
   if (sizeof(T) == 4 && d.plane) {
     // natural frequency order along y and z in every FP32 pass; the plane
     // passes (ky-major spectrum) are the default
@@ -990,7 +998,7 @@ lsh_status cg_run(lsh_handle* h, PrecBufs<T>& P, const OpArgs<T>& a, int maxit, 
 // base).  Eight launches per iteration: the five operator passes on r2 and the
 // three recurrence kernels.
 lsh_status minres_run(lsh_handle* h, const OpArgs<double>& a, int maxit, int check_every, const double* rhs2,
-                      double tol, std::vector<SolverState>& out) {
+                      double tol, std::vector<SolverState>& out, bool symmlq = false) {
   PrecBufs<double>& P = h->pd;
   cudaStream_t s = h->stream;
   const int S = a.S;
@@ -998,9 +1006,16 @@ lsh_status minres_run(lsh_handle* h, const OpArgs<double>& a, int maxit, int che
   const int G = P.L.ew_per_sys;
   LSH_CK(cudaMemcpyAsync(P.p, P.r, sizeof(double) * (size_t)(S * n), cudaMemcpyDeviceToDevice, s));
   LSH_CK(cudaMemsetAsync(h->wa, 0, sizeof(double) * (size_t)(S * n), s));
-  LSH_CK(cudaMemsetAsync(h->wb, 0, sizeof(double) * (size_t)(S * n), s));
+  if (symmlq)  // SYMMLQ: one direction field (wa) and the right-hand side of this run (wb)
+    LSH_CK(cudaMemcpyAsync(h->wb, P.r, sizeof(double) * (size_t)(S * n), cudaMemcpyDeviceToDevice, s));
+  else
+    LSH_CK(cudaMemsetAsync(h->wb, 0, sizeof(double) * (size_t)(S * n), s));
   launch_minres_begin(P.st, h->ms, rhs2, h->bbdev, tol, S, s);
   h->launches += 1;
+  if (symmlq) {
+    launch_symmlq_begin(h->sq, S, s);
+    h->launches += 1;
+  }
   lsh_status stt;
   out.resize(S);
   if ((stt = read_states(h, P.st, S, out.data()))) return stt;
@@ -1018,7 +1033,10 @@ lsh_status minres_run(lsh_handle* h, const OpArgs<double>& a, int maxit, int che
       launch_zgamma<double>(a, P.L, P.st, s);
       launch_yfft<double>(a, P.L, true, P.st, s);
       launch_xinv<double>(a, P.L, 3, P.p, P.q, P.st, h->partials, s);
-      launch_minres_step(P.x, P.r, P.p, P.q, h->wa, h->wb, n, S, P.st, h->ms, h->partials, G, s);
+      if (symmlq)
+        launch_symmlq_step(P.x, P.r, P.p, P.q, h->wa, h->wb, n, S, P.st, h->ms, h->sq, h->partials, G, s);
+      else
+        launch_minres_step(P.x, P.r, P.p, P.q, h->wa, h->wb, n, S, P.st, h->ms, h->partials, G, s);
       h->launches += 8;
     }
     if ((stt = last_launch())) return stt;
@@ -1118,7 +1136,9 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
   const int G = Pd.L.ew_per_sys;
   std::vector<SolverState> st;
   const int solver = o ? o->solver : LSH_SOLVER_AUTO;
-  const bool use_minres = solver == LSH_SOLVER_MINRES || (solver == LSH_SOLVER_AUTO && d.definite == 0);
+  if (solver < LSH_SOLVER_AUTO || solver > LSH_SOLVER_SYMMLQ) return LSH_ERR_INVALID_ARG;
+  const bool use_symmlq = solver == LSH_SOLVER_SYMMLQ;
+  const bool use_minres = use_symmlq || solver == LSH_SOLVER_MINRES || (solver == LSH_SOLVER_AUTO && d.definite == 0);
   if (solver == LSH_SOLVER_BASIC) {
     // Moulinec-Suquet fixed point, FP64 whatever the precision
     if (!warm) {
@@ -1155,7 +1175,7 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
       rhs2 = h->sums;
     }
     if ((stt = last_launch())) return stt;
-    if ((stt = minres_run(h, ad, maxit, check, rhs2, tol, st))) return stt;
+    if ((stt = minres_run(h, ad, maxit, check, rhs2, tol, st, use_symmlq))) return stt;
     for (int s = 0; s < S; ++s) {
       infos[s].iters = st[s].iter;
       infos[s].applies64 += st[s].iter;
@@ -1369,6 +1389,7 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   h->flags = h->base + l.off_flags;
   h->fault = (int*)(h->base + l.off_fault);
   h->ms = (MinresScalars*)(h->base + l.off_ms);
+  h->sq = (SymmlqScalars*)(h->ms + d.Smax);
   if (l.minres) {
     h->wa = (double*)(h->base + l.off_wa);
     h->wb = (double*)(h->base + l.off_wb);
@@ -1446,7 +1467,20 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
                               d.rotated ? d.A0full : nullptr, d.rotated ? d.R : nullptr);
   if (l.df) {
     const long long nf = (long long)d.nz * d.ny * d.ts, ncop = (d.ncoef + 3) & ~3;
-    launch_d2df(h->pd.gtab, h->gdf, ncop * nf, st);
+    if (d.plane && !(reg_len(d.ny) && reg_len(d.nz))) {
+      // the FP64 table follows the digit-reversed y / z positions of the FP64
+      // passes: build one in natural order in the double-float table's own
+      // memory (8 bytes per value either way) and convert it there
+      OpArgs<double> an = h->pd.a;
+      an.gtab = reinterpret_cast<double*>(h->gdf);
+      an.kofy = h->kofy32;
+      an.kofz = h->kofz32;
+      launch_gamma_table<double>(an, d.dim, d.physics, d.green, d.ref_user, h->kofy32, h->kofz32, st,
+                                 d.rotated ? d.A0full : nullptr, d.rotated ? d.R : nullptr);
+      launch_d2df_inplace(h->gdf, ncop * nf, st);
+    } else {
+      launch_d2df(h->pd.gtab, h->gdf, ncop * nf, st);
+    }
     launch_d2df((const double*)(h->base + l.off_tw_d), reinterpret_cast<DF*>(h->twdf), 2ll * (d.nx + d.ny + d.nz), st);
   }
   if (last_launch() != LSH_OK) { delete h; return LSH_ERR_CUDA; }
@@ -1503,13 +1537,21 @@ lsh_status lsh_apply(lsh_handle* h, int dtype, const void* x, void* y) {
       PrecBufs<float>& P = h->pf;
       const float* in = (const float*)x + b0 * n;
       float* o = (float*)y + b0 * n;
+      // the plane passes move fields in 16-byte pieces: unaligned caller buffers
+      // go through the handle's own
+      const bool stage = !rot && P.a.plane && (((uintptr_t)in | (uintptr_t)o) & 15) != 0;
       if (rot) {
         rotate(in, P.p, 1);
         in = P.p;
+      } else if (stage) {
+        LSH_CK(cudaMemcpyAsync(P.p, in, sizeof(float) * (size_t)(S * n), cudaMemcpyDeviceToDevice, h->stream));
+        in = P.p;
       }
-      lsh_status s = apply_internal<float>(h, wave_args<float>(h, w), in, rot ? P.q : o);
+      lsh_status s = apply_internal<float>(h, wave_args<float>(h, w), in, (rot || stage) ? P.q : o);
       if (s) return s;
       if (rot) rotate((const float*)P.q, o, 0);
+      else if (stage)
+        LSH_CK(cudaMemcpyAsync(o, P.q, sizeof(float) * (size_t)(S * n), cudaMemcpyDeviceToDevice, h->stream));
     }
   }
   return last_launch();

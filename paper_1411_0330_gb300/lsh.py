@@ -23,7 +23,7 @@ SCALAR, ELASTIC = 0, 1
 TRUNCATED, FILTERED, FD = 0, 1, 2
 FP64, MIXED = 0, 1
 F64, F32, F64_DF = 0, 1, 2
-SOLVER_AUTO, SOLVER_CG, SOLVER_MINRES, SOLVER_BASIC = 0, 1, 2, 3
+SOLVER_AUTO, SOLVER_CG, SOLVER_MINRES, SOLVER_BASIC, SOLVER_SYMMLQ = 0, 1, 2, 3, 4
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED_SIZE, ERR_REFERENCE_INDEFINITE, ERR_SINGULAR_CONTRAST, \
     ERR_BREAKDOWN, ERR_NOT_CONVERGED, ERR_WORKSPACE, ERR_CUDA, ERR_UNSUPPORTED = range(10)

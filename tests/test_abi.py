@@ -120,7 +120,7 @@ def test_binding_constants_match_the_header():
     names = ["OK", "ERR_INVALID_ARG", "ERR_UNSUPPORTED_SIZE", "ERR_REFERENCE_INDEFINITE", "ERR_SINGULAR_CONTRAST",
              "ERR_BREAKDOWN", "ERR_NOT_CONVERGED", "ERR_WORKSPACE", "ERR_CUDA", "ERR_UNSUPPORTED", "SCALAR",
              "ELASTIC", "TRUNCATED", "FILTERED", "FD", "FP64", "MIXED", "F64", "F32", "F64_DF", "SOLVER_AUTO",
-             "SOLVER_CG", "SOLVER_MINRES", "SOLVER_BASIC"]
+             "SOLVER_CG", "SOLVER_MINRES", "SOLVER_BASIC", "SOLVER_SYMMLQ"]
     for n in names:
         assert getattr(lsh, n) == h[alias.get(n, "LSH_" + n)], n
 

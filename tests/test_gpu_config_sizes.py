@@ -5,8 +5,8 @@
   double-float (the arithmetic of the mixed solver's refinement residual) and in
   FP32 with the autotuned kernel variants, element by element against the FP64
   CPU oracle, filtered and truncated Green operators.
-* 96^3 and 48^3 (the radix-3 grids of the batched configuration): FP64 and FP32
-  (plane passes) applications against the oracle.
+* 96^3 and 48^3 (the radix-3 grids of the batched configuration): FP64,
+  double-float and FP32 (plane passes) applications against the oracle.
 
 Tolerances (max |difference| / max |oracle|): FP64 1e-12, double-float 1e-13,
 FP32 2e-5 -- rounding of FFTs of log2 V <= 24 levels times the local contrast.
@@ -78,4 +78,5 @@ def test_apply_radix3_grids_fp64_and_fp32_match_oracle(n):
     hmx = lsh.Handle(ph_d, EL, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED, max_systems=1)
     assert hmx.autotune()["y_variant"] == 2
     assert rel(hmx.apply(xd).cpu().numpy(), yo) < 1e-12  # the mixed handle's FP64 operator
+    assert rel(hmx.apply(xd, double_float=True).cpu().numpy(), yo) < 1e-13  # the refinement residual's
     assert rel(hmx.apply(xd.float()).cpu().numpy(), yo) < 2e-5

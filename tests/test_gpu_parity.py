@@ -523,7 +523,8 @@ def test_persistent_z_pass_matches_register_z_pass(shape, physics, green):
 
 
 @pytest.mark.parametrize("shape,physics,green", [((32, 32, 32), 1, 1), ((16, 64, 32), 1, 0), ((64, 16, 128), 1, 1),
-                                                 ((32, 16, 64), 0, 1), ((16, 32, 16), 0, 0), ((16, 16, 256), 1, 0)])
+                                                 ((32, 16, 64), 0, 1), ((16, 32, 16), 0, 0), ((16, 16, 256), 1, 0),
+                                                 ((48, 48, 48), 1, 1), ((16, 96, 96), 1, 0), ((96, 32, 32), 0, 1)])
 def test_double_float_apply_matches_fp64(shape, physics, green):
     """K x in double-float arithmetic (FP64 fields, every pass on the FP32 pipes
     with 48-bit significands) against the native FP64 passes and the oracle: the
@@ -748,3 +749,49 @@ def test_bounded_wait_gives_up_and_the_handle_stays_usable():
     assert rel(h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy(), oracle.apply(P, x)) < 2e-5
     A, infos = h.effective(tol=1e-10)
     assert all(i["status"] == 0 for i in infos)
+
+
+def test_symmlq_indefinite_scalar_and_elastic_match_oracle():
+    """SYMMLQ (the indefinite-system solver the paper names, Sec. 1) reaches the
+    unique solution of Eq. (13): the 2D square inclusion with k0 = (1 + 10) / 2
+    (indefinite K) and elastic spheres with the reference between the phases, A*
+    against the oracle; its reported residual is the CG point's."""
+    ph = ms.square_inclusion(32)
+    mods = np.array([np.eye(2), 10 * np.eye(2)])
+    ref = 5.5 * np.eye(2)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.TRUNCATED, ref=ref)
+    Ao, _ = oracle.effective(oracle.Problem(ph, mods, green=0, ref=ref), tol=1e-13)
+    A, infos = h.effective(tol=1e-11, solver=lsh.SOLVER_SYMMLQ)
+    assert rel(A, Ao) < 1e-10, rel(A, Ao)
+    assert all(i["status"] == 0 and i["relres"] <= 1e-11 for i in infos)
+    _, inf_m = h.effective(tol=1e-11, solver=lsh.SOLVER_MINRES)
+    # the same Krylov spaces: the CG point needs about as many iterations as MINRES
+    assert all(a["iters"] <= 1.5 * b["iters"] + 10 for a, b in zip(infos, inf_m))
+    ph3, _, _ = ms.sphere_microstructure(12, 1.5, 0.25, seed=31)
+    ref3 = np.array([2.0 * KM, 2.0 * MUM])
+    h3 = lsh.Handle(torch.from_numpy(ph3).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED, ref=ref3)
+    P3 = oracle.Problem(ph3, EL, physics=1, green=1, ref=ref3)
+    A3, inf3 = h3.effective(tol=1e-11, solver=lsh.SOLVER_SYMMLQ)
+    Ao3, _ = oracle.effective(P3, tol=1e-13)
+    assert rel(A3, Ao3) < 1e-10, rel(A3, Ao3)
+    load = np.array([0.2, -0.1, 0.4, 0.0, 0.3, 0.1])
+    tau, info = h3.solve(load, tol=1e-11, solver=lsh.SOLVER_SYMMLQ)
+    to, _, _ = oracle.solve(P3, load, tol=1e-13)
+    assert rel(tau.cpu().numpy(), to) < 1e-9
+    # the true residual of the returned polarisation, by the oracle's operator
+    inside = np.ones(ph3.shape, bool)  # every phase differs from the reference here: I0 is the whole cell
+    b = inside[None] * load[:, None, None, None]
+    r = b - oracle.apply(P3, tau.cpu().numpy())
+    assert np.linalg.norm(r) <= 2e-11 * np.linalg.norm(b)
+    tau2, info2 = h3.solve(load, tau=tau.clone(), tol=1e-11, warm_start=True, solver=lsh.SOLVER_SYMMLQ)
+    assert info2["iters"] <= 2 and rel(tau2.cpu().numpy(), to) < 1e-9
+
+
+def test_symmlq_definite_equals_cg_solution():
+    """On a definite operator SYMMLQ's CG point is the CG iterate: same A* as CG."""
+    ph, _, _ = ms.sphere_microstructure(16, 2.0, 0.3, seed=8)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=lsh.TRUNCATED)
+    A_cg, _ = h.effective(tol=1e-12, solver=lsh.SOLVER_CG)
+    A_sq, inf = h.effective(tol=1e-12, solver=lsh.SOLVER_SYMMLQ)
+    assert rel(A_sq, A_cg) < 1e-10
+    assert all(i["status"] == 0 for i in inf)

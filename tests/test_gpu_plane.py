@@ -182,3 +182,21 @@ def test_plane_batched_microstructures_match_oracle():
     A, infos = h.effective(tol=1e-10)
     for b, c in enumerate(cases):
         assert rel(A[b], c[3]) < 1e-8, (b, rel(A[b], c[3]))
+
+
+def test_plane_apply_with_unaligned_caller_buffers():
+    """The plane passes move fields in 16-byte pieces: a caller's FP32 buffers that
+    start 4 bytes off a 16-byte boundary are staged through the handle's own, with
+    the result of aligned buffers."""
+    ph, mods = _problem((16, 32, 32), 0, 21)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.SCALAR, green=lsh.FILTERED, precision=lsh.MIXED)
+    h.set_variants(0, 0, 2, 0)
+    n = int(np.prod(h.field_shape))
+    xb = torch.from_numpy(np.random.default_rng(3).standard_normal(n + 1)).float().cuda()
+    yb = torch.zeros(n + 1, dtype=torch.float32, device="cuda")
+    x_un = xb[1:].view(h.field_shape)
+    y_un = yb[1:].view(h.field_shape)
+    assert x_un.data_ptr() % 16 != 0
+    h.apply(x_un, out=y_un)
+    y_al = h.apply(x_un.clone())
+    assert torch.equal(y_un, y_al)

@@ -485,3 +485,106 @@ def test_default_reference_reproduces_the_papers_reference_medium(oracle_mod):
     mu_ref, nu_ref = rows["reference"]
     assert abs(mu0 - mu_ref) < 1e-14
     assert abs(K0 - k_of(mu_ref, nu_ref)) < 1e-13
+
+
+# --------------------------------------------------------------------------- consistent operator (Eq. (11))
+def _brute_consistent(k, N, a1, a2):
+    """Eq. (11) summed literally over |n_i| <= L for L = 300, 600, 1200, then
+    extrapolated (the truncated sums carry errors of order 1/L and 1/L^2)."""
+    x = np.array(k, dtype=float) / N
+
+    def trunc(L):
+        n = np.arange(-L, L + 1)
+        u, y = x[0] + n[:, None], x[1] + n[None, :]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            w1 = np.where(u == 0, 1.0, np.sin(np.pi * x[0]) ** 2 / (np.pi * u) ** 2)
+            w2 = np.where(y == 0, 1.0, np.sin(np.pi * x[1]) ** 2 / (np.pi * y) ** 2)
+            q = a1 * u * u + a2 * y * y
+            w = np.where(q == 0, 0.0, w1 * w2 / q)
+        return np.array([[(w * u * u).sum(), (w * u * y).sum()], [(w * u * y).sum(), (w * y * y).sum()]])
+
+    b1, b2, b4 = trunc(300), trunc(600), trunc(1200)
+    r1, r2 = 2 * b2 - b1, 2 * b4 - b2
+    return (4 * r2 - r1) / 3
+
+
+def _consistent_problem(oracle_mod, N, A0, mods=None):
+    ph = np.zeros((N, N), np.uint8)
+    ph[N // 4:N // 2, N // 8:(5 * N) // 8] = 1
+    mods = np.array([np.eye(2), 4.0 * np.eye(2)]) if mods is None else mods
+    return oracle_mod.Problem(ph, mods, green=oracle_mod.CONSISTENT, ref=A0)
+
+
+@pytest.mark.parametrize("A0", [np.diag([0.5, 0.5]), np.diag([0.5, 1.7])])
+def test_consistent_operator_matches_the_lattice_sum(oracle_mod, A0):
+    """The accelerated evaluation (closed-form inner lattice sums, Hurwitz tails) equals
+    the series of Eq. (11) summed term by term."""
+    N = 12
+    P = _consistent_problem(oracle_mod, N, A0)
+    for k in [(1, 1), (3, 5), (6, 6), (11, 2), (0, 4), (5, 0), (7, 9)]:
+        G = np.real(oracle_mod.gamma_hat(P, k)).reshape(2, 2)
+        assert np.abs(G - _brute_consistent(k, N, A0[0, 0], A0[1, 1])).max() < 1e-8, k
+
+
+def test_consistent_operator_properties(oracle_mod):
+    """Even and real in k; tr(A0 G_k) = 1 at every k != 0 (the weights F^2 sum to one
+    and tr(A0 Gamma0) = 1); at low frequencies G_k -> Gamma0(k) as N grows, the gap
+    shrinking like (k/N)^2; axis frequencies give Gamma0 exactly."""
+    A0 = np.diag([0.5, 1.7])
+    N = 16
+    P = _consistent_problem(oracle_mod, N, A0)
+    for k in [(1, 2), (3, 7), (5, 11), (8, 3)]:
+        G = oracle_mod.gamma_hat(P, k)
+        Gm = oracle_mod.gamma_hat(P, ((N - k[0]) % N, (N - k[1]) % N))
+        assert np.abs(np.imag(G)).max() == 0.0
+        assert np.allclose(G, Gm, atol=1e-13)
+        Gr = np.real(G).reshape(2, 2)
+        assert abs(np.trace(A0 @ Gr) - 1.0) < 1e-12
+        assert np.allclose(Gr, Gr.T, atol=1e-15)
+    g0 = lambda k: np.outer(k, k) / (np.asarray(k) @ A0 @ np.asarray(k))
+    gaps = []
+    for N in (16, 32, 64):
+        P = _consistent_problem(oracle_mod, N, A0)
+        gaps.append(np.abs(np.real(oracle_mod.gamma_hat(P, (1, 2))).reshape(2, 2) - g0([1, 2])).max())
+    assert gaps[0] > gaps[1] > gaps[2] and 3.0 < gaps[0] / gaps[1] < 5.0 and 3.0 < gaps[1] / gaps[2] < 5.0
+    Gx = np.real(oracle_mod.gamma_hat(P, (5, 0))).reshape(2, 2)
+    assert np.allclose(Gx, g0([1, 0]), atol=1e-15)
+
+
+def test_consistent_operator_galerkin_monotone_under_refinement(oracle_mod):
+    """With the consistent operator, Eq. (13) is the exact Galerkin projection of the
+    LS variational problem on piecewise-constant fields.  For A0 below both phases the
+    form is coercive and A*_h p.p = A0 p.p + max over the subspace of a concave
+    functional, so on nested grids (a grid-aligned square inclusion at N = 4, 8, 16) it
+    increases with N and stays below the Voigt bound; CG equals the dense solve of
+    Eq. (12) (N = 4); the filtered and truncated operators approach the same values as N
+    grows."""
+    mods = np.array([np.eye(2), 10.0 * np.eye(2)])
+    A0 = 0.5 * np.eye(2)
+    e1 = np.array([1.0, 0.0])
+    vals = {}
+    for N in (4, 8, 16):
+        ph = ms.square_inclusion(N)
+        for green in (oracle_mod.CONSISTENT, oracle_mod.FILTERED, oracle_mod.TRUNCATED):
+            P = oracle_mod.Problem(ph, mods, green=green, ref=A0)
+            tau, _, _ = oracle_mod.solve(P, e1, tol=1e-14, solver=1)
+            vals[(green, N)] = A0[0, 0] + tau[0].mean()  # e1 . A*_h e1, Eq. (tau_Astar)
+            if N == 4 and green == oracle_mod.CONSISTENT:
+                assert np.allclose(tau, oracle_mod.dense_solve(P, e1), atol=1e-11)
+                assert abs(tau[1].mean()) < 1e-13  # A*_12 = 0 by the square's symmetry
+    c = oracle_mod.CONSISTENT
+    assert vals[(c, 4)] < vals[(c, 8)] < vals[(c, 16)] < 0.75 * 1.0 + 0.25 * 10.0
+    for green in (oracle_mod.FILTERED, oracle_mod.TRUNCATED):
+        assert abs(vals[(green, 16)] - vals[(c, 16)]) < abs(vals[(green, 4)] - vals[(c, 4)])
+
+
+def test_consistent_operator_refuses_what_it_does_not_cover(oracle_mod):
+    """Elastic problems, 3D and non-diagonal references are outside its scope."""
+    ph = np.zeros((6, 6), np.uint8)
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.effective(oracle_mod.Problem(ph, np.array([2.0 * np.eye(2)]), green=oracle_mod.CONSISTENT,
+                                                ref=np.array([[1.0, 0.2], [0.2, 1.0]])), tol=1e-10)
+    ph3 = np.zeros((4, 4, 4), np.uint8)
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.effective(oracle_mod.Problem(ph3, np.array([2.0 * np.eye(3)]), green=oracle_mod.CONSISTENT,
+                                                ref=np.eye(3)), tol=1e-10)
