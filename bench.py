@@ -465,6 +465,15 @@ def run_batch(args, rank, world, local):
                                  for k in lsh.PASS_NAMES if p["pass_launches"][k]}
         per_grid_pass[str(n)]["live_system_iterations_timed"] = p["timed_sys_iters"]
     iter_b = sum(tot_b.values())
+    # the step's time split: FP32 inner CG passes (sampled events scaled by all live
+    # system-iterations / the sampled ones, per grid) and the rest (refinement residuals,
+    # precision conversions, host-side convergence checks, graph launch gaps)
+    cg_ms = 0.0
+    for p, hh in zip(prof_mx, gmx.handles):
+        live = sum(sum(i["iters"] for i in I_mx[k]) for k in range(len(I_mx)) if meta[k]["n"] == hh.shape[0])
+        if p["timed_sys_iters"]:
+            cg_ms += sum(p["pass_ms"].values()) * live * args.steps / p["timed_sys_iters"]
+    step_split = {"inner_cg_ms_est": cg_ms / args.steps, "other_ms_est": ms_mx - cg_ms / args.steps}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": ncu_traffic_per_launch(dom, tot_b[dom] / tot_n[dom]),
                 "traffic_source": NCU_TRAFFIC_SOURCE,
@@ -475,6 +484,7 @@ def run_batch(args, rank, world, local):
                 "pass_frac_fp32": {k: tot_b[k] / (tot_ms[k] / 1e3) / 1e9 / peaks["hbm_gbs"]
                                    for k in lsh.PASS_NAMES if tot_n[k]},
                 "whole_iteration_frac": iter_b / (sh_sum / 1e3) / 1e9 / peaks["hbm_gbs"],
+                "step_split": step_split,
                 "per_grid": per_grid_pass}
 
     # end to end through the public API: phase maps from pinned host memory in, C* out, every step
@@ -554,15 +564,33 @@ def run_contrast256(args):
         row = {"contrast": contrast}
         res = {}
         for name, prec in (("mixed", lsh.MIXED), ("fp64", lsh.FP64)):
-            h = lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=prec)
+            h = lsh.Handle(ph_dev, mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=prec,
+                           tune=prec == lsh.MIXED)
             h.profile_read(reset=True)
+            h.profile_enable(True, every=PROF_EVERY)
             dt, (A, infos) = _wall(lambda: h.effective(tol=TOL, maxit=40000))
+            pf = h.profile_read(reset=True)
+            h.profile_enable(False)
             its = sum(i["iters"] for i in infos)
             res[name] = (A, its, dt)
             row[name] = {"s": dt, "iterations": its, "voxel_it_per_s": its * V / dt,
-                         "launches": h.profile_read(reset=True)["launches"],
+                         "launches": pf["launches"],
                          "max_relres": max(i["relres"] for i in infos),
                          "outer": sum(i["outer"] for i in infos)}
+            if prec == lsh.MIXED:
+                # per-pass events of the FP32 inner CG (one chunk in PROF_EVERY), algorithmic
+                # bytes of the live system-iterations over their event time
+                passes = {}
+                for k in lsh.PASS_NAMES:
+                    if not pf["pass_launches"][k]:
+                        continue
+                    per_sys, table = batch_pass_bytes(k, n)
+                    byts = per_sys * pf["timed_sys_iters"] + table * pf["pass_launches"][k]
+                    gbs = byts / (pf["pass_ms"][k] / 1e3) / 1e9
+                    passes[k] = {"ms_per_launch": pf["pass_ms"][k] / pf["pass_launches"][k], "gbs": gbs,
+                                 "frac_of_copy_peak": gbs / load_peaks()["hbm_gbs"]}
+                row[name]["fp32_passes"] = passes
+                row[name]["autotune"] = h.tune_report
             h.close()
             del h
             torch.cuda.empty_cache()
@@ -626,16 +654,17 @@ def run_gradient128(args, nfd=32, hfd=1e-6):
     dt, (obj, g) = _wall(grad_once)
     g = g.double().cpu().numpy()
 
-    def obj_var(scale_np, taus):
-        """Variational estimate sum_p W_pp (p.A0 p + h^d (2 b_p.tau_p - tau_p.K tau_p)),
-        returned as per-voxel terms so that differences are taken voxel by voxel."""
-        h.set_microstructure(ph, scale_np)
+    def obj_var(hv, phase_np, taus):
+        """Variational estimate sum_p W_pp (p.A0 p + h^d (2 b_p.tau_p - tau_p.K tau_p)) on the
+        handle hv with the phase map phase_np, returned as per-voxel terms so that differences
+        are taken voxel by voxel."""
+        hv.set_microstructure(phase_np, s)
         terms = []
         for j, tau0 in zip((0, 5), taus):
             load = np.zeros(6)
             load[j] = 1.0
-            tau, info = h.solve(load, tau=tau0.clone(), tol=1e-13, warm_start=True, maxit=20000)
-            Kt = h.apply(tau)
+            tau, info = hv.solve(load, tau=tau0.clone(), tol=1e-13, warm_start=True, maxit=20000)
+            Kt = hv.apply(tau)
             t_np, k_np = tau.cpu().numpy(), Kt.cpu().numpy()
             # b = p on I0 and tau = 0 off I0, so b.tau = p.tau summed over all voxels
             terms.append(W[j, j] * (2.0 * t_np[j] - (t_np * k_np).sum(axis=0)))
@@ -650,19 +679,28 @@ def run_gradient128(args, nfd=32, hfd=1e-6):
         load[j] = 1.0
         tau, _ = h.solve(load, tol=1e-13)
         base.append(tau)
+    h.close()
+    torch.cuda.empty_cache()
     fd, ad = [], []
     t0 = time.perf_counter()
+    ph_flat, s_flat = ph.reshape(-1), s.reshape(-1)
     for v in vox:
-        sp = s.copy().reshape(-1)
-        sm = s.copy().reshape(-1)
-        sp[v] += hfd
-        sm[v] -= hfd
-        # the scale field is stored in FP32: use the steps actually taken
-        step = float(sp[v]) - float(sm[v])
-        dp = obj_var(sp.reshape(s.shape), base)
-        dm = obj_var(sm.reshape(s.shape), base)
-        fd.append(float((dp - dm).sum()) / V / step)
+        # the perturbation s_v -> s_v +- h in FP64: voxel v moves to an extra phase whose
+        # moduli are (1 +- h / s_v) A_phase(v), so that s_v A stays the stored FP32 s_v
+        # times an FP64 factor (the scale field itself is FP32)
+        sv, pv = float(s_flat[v]), int(ph_flat[v])
+        m4 = np.vstack([mods, (1.0 + hfd / sv) * mods[pv], (1.0 - hfd / sv) * mods[pv]])
+        hv = lsh.Handle(torch.from_numpy(ph).cuda(), m4, physics=lsh.ELASTIC, green=lsh.FILTERED, ref=ref,
+                        scale=torch.from_numpy(s).cuda(), max_systems=1)
+        pp, pm = ph_flat.copy(), ph_flat.copy()
+        pp[v], pm[v] = 2, 3
+        dp = obj_var(hv, pp.reshape(ph.shape), base)
+        dm = obj_var(hv, pm.reshape(ph.shape), base)
+        fd.append(float((dp - dm).sum()) / V / (2.0 * hfd))
         ad.append(float(g.reshape(-1)[v]))
+        hv.close()
+        del hv
+        torch.cuda.empty_cache()
     t_fd = time.perf_counter() - t0
     fd, ad = np.array(fd), np.array(ad)
     relerr = np.abs(fd - ad) / np.abs(ad).max()
@@ -672,13 +710,13 @@ def run_gradient128(args, nfd=32, hfd=1e-6):
             "config": {"workload": f"128^3 sphere packing (seed 1411, {nsph} spheres), per-voxel scale "
                                    "s ~ U(0.5,2) (seed 1412) on the phase moduli, filtered Gamma, tol 1e-12",
                        "fd": f"central differences of the variational estimate on {nfd} voxels (seed 1413), "
-                             f"h={hfd:g}, FP64 solves at 1e-13 warm-started"},
+                             f"h={hfd:g} applied in FP64 (an extra phase with moduli (1 +- h/s_v) A_phase at "
+                             "the perturbed voxel), FP64 solves at 1e-13 warm-started"},
             "objective": obj, "fd_vs_adjoint_max_err_over_max_grad": float(relerr.max()),
             "fd_vs_adjoint_median_err_over_max_grad": float(np.median(relerr)),
             "grad_abs_max": float(np.abs(g).max()), "fd_seconds": t_fd,
             "samples": [{"voxel": int(v), "adjoint": a, "fd": f} for v, a, f in zip(vox[:8], ad[:8], fd[:8])]}
     print(json.dumps(line), flush=True)
-    h.close()
     return 0
 
 

@@ -168,7 +168,7 @@ typedef struct lsh_tune_report {
   float y_ms[2];
   float z_ms[10];
   float xy_ms[2]; /* one CG iteration's passes summed: separate x/y passes, plane passes */
-  float zp_ms[4]; /* z pass on the ky-major spectrum, variants 0, 6, 8, 9             */
+  float zp_ms[5]; /* z pass on the ky-major spectrum, variants 0, 6, 8, 9, 7          */
 } lsh_tune_report;
 
 /* Bytes of device workspace lsh_setup needs for this problem. */
@@ -227,7 +227,7 @@ lsh_status lsh_autotune(lsh_handle *h, lsh_tune_report *rep);
 
 /* Select the FP32 forward x / inverse x / y / z pass variants by hand (numbering of lsh_tune_report;
  * no counterpart in the paper: for tests and measurements).  y_variant 2
- * selects the plane passes (x variants ignored; z variant 0, 6, 8 or 9).
+ * selects the plane passes (x variants ignored; z variant 0, 6, 7, 8 or 9).
  * Returns LSH_ERR_UNSUPPORTED if a variant is not available for this problem
  * (FP64 handles accept only zeros). */
 lsh_status lsh_set_variants(lsh_handle *h, int xf_variant, int x_variant, int y_variant, int z_variant);

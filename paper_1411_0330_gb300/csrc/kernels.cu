@@ -1227,9 +1227,9 @@ void launch_yfft(const OpArgs<T>& a, const LaunchCfg& L, bool inv, const SolverS
 template <typename T>
 void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st, cudaStream_t s) {
   if constexpr (sizeof(T) == 4) {
-    // the TMA and persistent variants read the x-major layout only
+    // the TMA variants read the x-major layout only
     if (!a.tlay && a.ztma >= 1 && a.ztma <= 5 && launch_zgamma_tma(a, a.ztma, st, s)) return;
-    if (!a.tlay && a.ztma == 7 && launch_zgamma_regp(a, st, s)) return;
+    if (a.ztma == 7 && launch_zgamma_regp(a, st, s)) return;
   }
   if (a.zreg) {
     int tz = 0;

@@ -368,7 +368,7 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH) k_xyinv(OpArgs<float> a, cons
   plane_x_inv<N>(PL, tw);
   __syncthreads();
   Acc<float> acc;
-#pragma unroll 4
+#pragma unroll 8
   for (int it = 0; it < PC::IT; ++it) {
     const int idx = threadIdx.x + it * TH;
     const int row = idx / NV, xx = (idx - row * NV) * 4;

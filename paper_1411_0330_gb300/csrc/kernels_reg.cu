@@ -297,7 +297,10 @@ __global__ void __launch_bounds__(ZPCfg<NC, N>::THREADS, ZPCfg<NC, N>::THREADS <
   for (int u = threadIdx.x; u < N; u += THREADS) tw[u] = a.twz[u];
   const int S = a.S, nleft = a.nxh - nreg, nregt = a.ny * nrt;
   const int total = S * ntiles;  // below 2^31 (checked by the launcher)
-  const int zstride = a.ny * a.hs, cstride = zstride * N;
+  // element strides of H: x-major [S][c][z][y][hs] or ky-major [S][c][y][z][hs]
+  const long long ys = a.tlay ? (long long)N * a.hs : a.hs;
+  const long long zs = a.tlay ? a.hs : (long long)a.ny * a.hs;
+  const long long cstride = (long long)a.ny * a.hs * N;
   // line li of tile `tile`: y position (-1: past the last column) and kx
   auto line = [&](int tile, int li, int& yp, int& kx) {
     if (tile < nregt) {
@@ -313,23 +316,50 @@ __global__ void __launch_bounds__(ZPCfg<NC, N>::THREADS, ZPCfg<NC, N>::THREADS <
       }
     }
   };
+  // the system and tile of work item tl: systems fastest (x-major spectrum: the
+  // systems share the tile's Gamma rows), or kx tiles fastest within a (system,
+  // ky) slab (ky-major spectrum: the slab is one contiguous range)
+  auto item = [&](int tl, int& s, int& tile) {
+    if (!a.tlay) {
+      s = tl % S;
+      tile = tl / S;
+    } else if (tl < nregt * S) {
+      const int yp = tl / (S * nrt), rem = tl - yp * S * nrt;
+      s = rem / nrt;
+      tile = yp * nrt + (rem - s * nrt);
+    } else {
+      const int ntl = ntiles - nregt, l2 = tl - nregt * S;
+      s = l2 / ntl;
+      tile = nregt + (l2 - s * ntl);
+    }
+  };
+  // complex element (s, comp, z) of line (yp, kx): the Nyquist column of a
+  // ky-major spectrum lives in NQ[S][c][z][ky]
+  auto elem = [&](int s, int comp, int z, int yp, int kx) -> float2* {
+    if (a.tlay && 2 * kx == a.nx) return a.nq + (((long long)s * NC + comp) * N + z) * a.ny + yp;
+    return a.H + ((long long)s * NC + comp) * cstride + (long long)z * zs + (long long)yp * ys + kx;
+  };
   auto next_live = [&](int tl) {
-    while (tl < total && st != nullptr && st[tl % S].done) tl += gridDim.x;
+    int s, tile;
+    while (tl < total && st != nullptr) {
+      item(tl, s, tile);
+      if (!st[s].done) break;
+      tl += gridDim.x;
+    }
     return tl;
   };
   // stage the columns of tile tl; its Gamma^h rows go to L2 meanwhile
   auto prefetch = [&](int tl) {
-    const int s = tl % S, tile = tl / S;
-    const float2* Hs = a.H + (long long)s * NC * cstride;
+    int s, tile;
+    item(tl, s, tile);
     if (tile < nregt) {
       // TZ consecutive columns: rows of TZ / 2 aligned 16-byte pieces
       constexpr int CH = TZ / 2, NCOP = GammaPack<NC>::NCOP;
       const int yp = tile / nrt, kx0 = (tile - yp * nrt) * TZ;
-      const float2* src = Hs + (long long)yp * a.hs + kx0;
       for (int q = threadIdx.x; q < N * NC * CH; q += THREADS) {
         const int row = q / CH, piece = q - row * CH;  // row = z NC + comp
         const int z = row / NC, comp = row - z * NC;
-        cp_async16(stage + row * TZ + 2 * piece, src + (long long)comp * cstride + (long long)z * zstride + 2 * piece);
+        cp_async16(stage + row * TZ + 2 * piece, elem(s, comp, z, yp, kx0) + 2 * piece);
       }
       if (!a.onfly)
         for (int kz = threadIdx.x; kz < N; kz += THREADS)
@@ -341,8 +371,7 @@ __global__ void __launch_bounds__(ZPCfg<NC, N>::THREADS, ZPCfg<NC, N>::THREADS <
         const int z = row / NC, comp = row - z * NC;
         int yp, kx;
         line(tile, li, yp, kx);
-        if (yp >= 0)
-          cp_async8(stage + q, Hs + (long long)comp * cstride + (long long)z * zstride + (long long)yp * a.hs + kx);
+        if (yp >= 0) cp_async8(stage + q, elem(s, comp, z, yp, kx));
       }
     }
     cp_async_commit();
@@ -353,7 +382,8 @@ __global__ void __launch_bounds__(ZPCfg<NC, N>::THREADS, ZPCfg<NC, N>::THREADS <
   if (cur < total) prefetch(cur);
   while (cur < total) {
     const int nxt = next_live(cur + gridDim.x);
-    const int s = cur % S, tile = cur / S;
+    int s, tile;
+    item(cur, s, tile);
     cp_async_wait_all();
     __syncthreads();  // the tile is staged; the previous tile is done with buf and the line table
     if (threadIdx.x < TZ) {
@@ -385,9 +415,10 @@ __global__ void __launch_bounds__(ZPCfg<NC, N>::THREADS, ZPCfg<NC, N>::THREADS <
     __syncthreads();
     RL::inv_b(v, t, tw, exl);
     if (valid) {
-      float2* Hl = a.H + ((long long)s * NC + comp) * cstride + (long long)yp * a.hs + kx;
+      float2* Hl = elem(s, comp, 0, yp, kx);
+      const long long step = (a.tlay && 2 * kx == a.nx) ? (long long)a.ny : zs;
 #pragma unroll
-      for (int j = 0; j < R1; ++j) Hl[(long long)(t + P * j) * zstride] = v[j];
+      for (int j = 0; j < R1; ++j) Hl[(long long)(t + P * j) * step] = v[j];
     }
     cur = nxt;
   }
@@ -545,6 +576,8 @@ template <int NC, int N> bool launch_zp_n(const OpArgs<float>& a, const SolverSt
 
 template <int NC> bool launch_zp_nc(const OpArgs<float>& a, const SolverState* st, cudaStream_t s) {
   switch (a.nz) {
+    case 48: return launch_zp_n<NC, 48>(a, st, s);
+    case 96: return launch_zp_n<NC, 96>(a, st, s);
     case 16: return launch_zp_n<NC, 16>(a, st, s);
     case 32: return launch_zp_n<NC, 32>(a, st, s);
     case 64: return launch_zp_n<NC, 64>(a, st, s);
@@ -565,6 +598,8 @@ bool launch_zgamma_regp(const OpArgs<float>& a, const SolverState* st, cudaStrea
 }
 
 template <int NC> void zp_prepare() {
+  zp_blocks_per_sm<NC, 48>();
+  zp_blocks_per_sm<NC, 96>();
   zp_blocks_per_sm<NC, 16>();
   zp_blocks_per_sm<NC, 32>();
   zp_blocks_per_sm<NC, 64>();

@@ -1702,7 +1702,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
   for (int k = 0; k < 10; ++k) r.z_ms[k] = -1.f;
   for (int k = 0; k < 2; ++k) r.xy_ms[k] = -1.f;
-  for (int k = 0; k < 4; ++k) r.zp_ms[k] = -1.f;
+  for (int k = 0; k < 5; ++k) r.zp_ms[k] = -1.f;
   const Derived& d = h->d;
   if (d.precision == LSH_MIXED) {
     PrecBufs<float>& P = h->pf;
@@ -1808,11 +1808,12 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       OpArgs<float> b = a;
       b.plane = 1;
       b.tlay = 1;
-      const int zc[4] = {0, 6, 8, 9};
+      const int zc[5] = {0, 6, 8, 9, 7};
       int bz = 0;
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < 5; ++k) {
         b.ztma = zc[k];
         r.zp_ms[k] = timeit([&]() {
+          if (zc[k] == 7) return launch_zgamma_regp(b, nullptr, s);
           launch_zgamma<float>(b, P.L, nullptr, s);
           return true;
         });
@@ -1867,8 +1868,12 @@ lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_
     return (xf_variant || x_variant || y_variant || z_variant) ? LSH_ERR_UNSUPPORTED : LSH_OK;
   if (y_variant == 2) {
     // plane passes: the register z kernels on the ky-major spectrum
-    if (!h->d.plane || !(z_variant == 0 || z_variant == 6 || z_variant == 8 || z_variant == 9))
-      return LSH_ERR_UNSUPPORTED;
+    if (!h->d.plane || !(z_variant == 0 || (z_variant >= 6 && z_variant <= 9))) return LSH_ERR_UNSUPPORTED;
+    if (z_variant == 7) {
+      OpArgs<float> a = P.a;
+      a.S = 0;
+      if (!launch_zgamma_regp(a, nullptr, 0)) return LSH_ERR_UNSUPPORTED;
+    }
     P.a.plane = 1;
     P.a.tlay = 1;
     P.a.ztma = z_variant;

@@ -26,22 +26,24 @@ CASES = {
     "spheres48_f25_s148_filtered": (48, 6.0, 0.25, 148, oracle.FILTERED),
     "spheres48_f15_s1_r3_filtered": (48, 3.0, 0.15, 1, oracle.FILTERED),
     "spheres48_f30_s2_r3_filtered": (48, 3.0, 0.30, 2, oracle.FILTERED),
-    "spheres48_f25_s3_r3_filtered": (48, 3.0, 0.25, 3, oracle.FILTERED),
 }
 
 
 def main():
     oracle.build()
-    out = {}
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_cstar.json")
+    out = json.load(open(path)) if os.path.exists(path) else {}
     for name, (n, r, f, seed, green) in CASES.items():
+        if name in out:
+            continue
         ph, _, _ = ms.sphere_microstructure(n, r, f, seed=seed)
         A, infos = oracle.effective(oracle.Problem(ph, np.array(EL), physics=oracle.ELASTIC, green=green), tol=1e-13)
         out[name] = {"n": n, "radius": r, "fraction": f, "seed": seed, "green": int(green),
                      "realised_fraction": float(ph.mean()), "moduli_K_mu": EL, "tol": 1e-13,
                      "cstar_mandel": np.asarray(A).tolist()}
         print(name, float(A[0, 0]), flush=True)
-    with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_cstar.json"), "w") as fh:
-        json.dump(out, fh, indent=1)
+        with open(path, "w") as fh:  # after every case: a long run keeps what it finished
+            json.dump(out, fh, indent=1)
 
 
 if __name__ == "__main__":

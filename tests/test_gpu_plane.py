@@ -67,7 +67,7 @@ def test_plane_apply_matches_oracle(shape, physics, green):
     P = oracle.Problem(ph, mods, physics=physics, green=green)
     x = np.random.default_rng(1).standard_normal(P.field_shape)
     yo = oracle.apply(P, x)
-    for zv in (0, 6, 8, 9):
+    for zv in (0, 6, 7, 8, 9):
         h.set_variants(0, 0, 2, zv)
         y = h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy()
         assert rel(y, yo) < 2e-5, zv
@@ -172,13 +172,12 @@ def test_plane_apply_with_voxel_fields(kind):
 
 def test_plane_batched_microstructures_match_oracle():
     """Several microstructures of one 48^3 grid in one batch handle (system-major
-    planes, per-system reductions, waves of 12 systems) give each microstructure's
-    stored oracle C*."""
-    cases = [_golden(k) for k in ("spheres48_f15_s1_r3_filtered", "spheres48_f30_s2_r3_filtered",
-                                  "spheres48_f25_s3_r3_filtered")]
+    planes, per-system reductions, waves of 5 systems straddling microstructures) give
+    each microstructure's stored oracle C*."""
+    cases = [_golden(k) for k in ("spheres48_f15_s1_r3_filtered", "spheres48_f30_s2_r3_filtered")]
     stack = np.stack([c[0] for c in cases])
     h = lsh.Handle(torch.from_numpy(stack).cuda(), cases[0][1], physics=lsh.ELASTIC, green=cases[0][2],
-                   precision=lsh.MIXED, batch=True, max_systems=12)
+                   precision=lsh.MIXED, batch=True, max_systems=5)
     A, infos = h.effective(tol=1e-10)
     for b, c in enumerate(cases):
         assert rel(A[b], c[3]) < 1e-8, (b, rel(A[b], c[3]))
