@@ -153,13 +153,13 @@ def pass_flops(kind, V, c, nx, ny, nz, nxh):
 
 PROF_EVERY = 8  # per-pass events in one CG chunk of this many
 
-# DRAM bytes (read + write) of one launch of each FP32 pass over the 6 load
-# systems of the 128^3 workload, from the ncu captures in the FP32-pass
-# summary under profiles/ (filtered operator), with the algorithmic bytes of
-# the same launch; to be retaken whenever one of these kernels changes (None:
-# not captured for the current kernel).
-NCU_TRAFFIC_FP32 = {"x_forward": None, "y_forward": None, "z_gamma": None, "y_inverse": None,
-                    "x_inverse_local": None, "cg_update": None}
+# DRAM bytes (read + write) of one launch of each FP32 pass (plane schedule)
+# over the 6 load systems of the 128^3 workload, from the ncu captures in the
+# plane-pass summary under profiles/ (filtered operator); to be retaken
+# whenever one of these kernels changes (None: not captured for the current
+# kernel).
+NCU_TRAFFIC_FP32 = {"x_forward": None, "y_forward": None, "z_gamma": 730.8e6, "y_inverse": None,
+                    "x_inverse_local": 919.2e6, "cg_update": 862.0e6}
 NCU_TRAFFIC_SOURCE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch over 6 systems at 128^3 "
                       "(filtered), scaled to the batch's average launch by its algorithmic bytes")
 
@@ -504,9 +504,9 @@ def run_batch(args, rank, world, local):
     cpu = None
     if rank == 0 and not args.no_cpu:
         sample = batch_sample(phases, meta)
-        u, secs = oracle_batch_sample(sample, mods, 8)  # about 10 s on 16 host cores
+        u, secs = oracle_batch_sample(sample, mods, 4)  # about 20 s on 16 host cores
         cpu = {"value": u / secs, "unit": UNIT, "cores": oracle_cores(), "kind": "oracle",
-               "sample": batch_sample_text(sample, 8) + f", {secs:.1f} s"}
+               "sample": batch_sample_text(sample, 4) + f", {secs:.1f} s"}
 
     per_grid = {}
     for m, e, a, b in zip(meta, errs, itmx, it64):

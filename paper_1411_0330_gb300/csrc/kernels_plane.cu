@@ -51,6 +51,8 @@ template <int N> struct PlaneCfg {
   static constexpr int NV = N / 4;     // float4 groups per real row
   static constexpr int IT = N * NV / TH;
   static constexpr size_t SMEM = sizeof(float2) * ((size_t)N * RS + N);
+  // resident blocks per SM the register budget must allow (three 70 KB planes at 128^2)
+  static constexpr int MINB = N == 128 ? 3 : 4;
   static_assert(LINES % LPR == 0 && (N * NV) % TH == 0, "tiling");
   static_assert(N + N / R1 <= 2 * RS, "padded exchange fits in a row pair");
 };
@@ -225,7 +227,7 @@ template <int N> __device__ __forceinline__ void plane_x_inv(float2* PL, const f
 // MODE 0: spectrum of P in (apply).  MODE 1 (CG): x += alpha p_old, p = r +
 // beta p_old (p = r at the first iteration), spectrum of p.
 template <int N, int MODE>
-__global__ void __launch_bounds__(PlaneCfg<N>::TH) k_xyfwd(OpArgs<float> a, const float* __restrict__ in,
+__global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyfwd(OpArgs<float> a, const float* __restrict__ in,
                                                            float* __restrict__ x, const float* __restrict__ r,
                                                            float* __restrict__ p, const SolverState* __restrict__ st) {
   typedef PlaneCfg<N> PC;
@@ -252,47 +254,86 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH) k_xyfwd(OpArgs<float> a, cons
     alpha = (float)st[s].alpha;
     beta = (float)st[s].beta;
   }
-  // optionally the block's input planes go to L2 in a few large requests first
-  // (off by default: measured slower for this pass)
-  if ((a.l2pf & 1) && threadIdx.x < 32) {
-    constexpr uint32_t PB = (uint32_t)(sizeof(float) * N * N);
-    constexpr uint32_t CH = PB / 8;  // 8 requests per plane
-    const int w = threadIdx.x & 7, arr = threadIdx.x >> 3;
-    const float* src = MODE == 0 ? (arr == 0 ? in : nullptr)
-                                 : (arr == 0 ? r : (k > 0 ? (arr == 1 ? p : (arr == 2 ? x : nullptr)) : nullptr));
-    if (src) bulk_prefetch_l2(reinterpret_cast<const char*>(src + plane) + w * CH, CH);
-  }
-  if (MODE == 0) __syncthreads();  // aloc
+  if (MODE == 0) {
+    __syncthreads();  // aloc
 #pragma unroll 4
-  for (int it = 0; it < PC::IT; ++it) {
-    const int idx = threadIdx.x + it * TH;
-    const int row = idx / NV, xx = (idx - row * NV) * 4;
-    const long long g = plane + (long long)row * N + xx;
-    float4 v;
-    if (MODE == 0) {
-      v = *reinterpret_cast<const float4*>(in + g);
+    for (int it = 0; it < PC::IT; ++it) {
+      const int idx = threadIdx.x + it * TH;
+      const int row = idx / NV, xx = (idx - row * NV) * 4;
+      const long long g = plane + (long long)row * N + xx;
+      float4 v = *reinterpret_cast<const float4*>(in + g);
       const uchar4 ph = *reinterpret_cast<const uchar4*>(a.phase + pbase + row * N + xx);
       if (!aloc[ph.x]) v.x = 0.f;
       if (!aloc[ph.y]) v.y = 0.f;
       if (!aloc[ph.z]) v.z = 0.f;
       if (!aloc[ph.w]) v.w = 0.f;
-    } else {
-      const float4 r4 = *reinterpret_cast<const float4*>(r + g);
-      if (k == 0) {
-        v = r4;
-      } else {
-        const float4 p4 = *reinterpret_cast<const float4*>(p + g);
-        float4 x4 = *reinterpret_cast<const float4*>(x + g);
-        x4.x += alpha * p4.x;
-        x4.y += alpha * p4.y;
-        x4.z += alpha * p4.z;
-        x4.w += alpha * p4.w;
-        *reinterpret_cast<float4*>(x + g) = x4;
-        v = make_float4(r4.x + beta * p4.x, r4.y + beta * p4.y, r4.z + beta * p4.z, r4.w + beta * p4.w);
-      }
-      *reinterpret_cast<float4*>(p + g) = v;
+      *reinterpret_cast<float4*>(PR + 2 * RS * row + xx) = v;
     }
-    *reinterpret_cast<float4*>(PR + 2 * RS * row + xx) = v;
+  } else {
+    // The r plane comes into the real rows of the plane buffer by one bulk copy
+    // per row; p and x go through registers in batches of B groups of four
+    // reals, each batch's loads in flight while the previous batch is combined.
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+      mbar_init(&bar, 1);
+      mbar_init_fence();
+      mbar_expect_tx(&bar, (uint32_t)(sizeof(float) * N * N));
+    }
+    __syncthreads();
+    for (int row = threadIdx.x; row < N; row += TH)
+      bulk_load_1d(PR + 2 * RS * row, r + plane + (long long)row * N, (uint32_t)(sizeof(float) * N), &bar);
+    constexpr int B = PC::IT % 4 == 0 ? 4 : (PC::IT % 3 == 0 ? 3 : (PC::IT % 2 == 0 ? 2 : 1));
+    static_assert(PC::IT % B == 0, "batches");
+    float4 pb[B], xb[B];
+    auto load_batch = [&](int it0) {
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int idx = threadIdx.x + (it0 + b) * TH;
+        const int row = idx / NV, xx = (idx - row * NV) * 4;
+        const long long g = plane + (long long)row * N + xx;
+        pb[b] = *reinterpret_cast<const float4*>(p + g);
+        xb[b] = *reinterpret_cast<const float4*>(x + g);
+      }
+    };
+    if (k > 0) load_batch(0);
+    if (__syncthreads_or(!mbar_wait(&bar, 0))) {
+      if (threadIdx.x == 0) {
+        mbar_wait(&bar, 0);  // no copy may still be writing this block's shared memory
+        atomicOr(a.fault, 1);
+      }
+      return;
+    }
+#pragma unroll 1
+    for (int it0 = 0; it0 < PC::IT; it0 += B) {
+      float4 pc[B], xc[B];
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        pc[b] = pb[b];
+        xc[b] = xb[b];
+      }
+      if (k > 0 && it0 + B < PC::IT) load_batch(it0 + B);
+#pragma unroll
+      for (int b = 0; b < B; ++b) {
+        const int idx = threadIdx.x + (it0 + b) * TH;
+        const int row = idx / NV, xx = (idx - row * NV) * 4;
+        const long long g = plane + (long long)row * N + xx;
+        float4* rs = reinterpret_cast<float4*>(PR + 2 * RS * row + xx);
+        const float4 r4 = *rs;
+        float4 v = r4;
+        if (k > 0) {
+          const float4 p4 = pc[b];
+          float4 x4 = xc[b];
+          x4.x += alpha * p4.x;
+          x4.y += alpha * p4.y;
+          x4.z += alpha * p4.z;
+          x4.w += alpha * p4.w;
+          *reinterpret_cast<float4*>(x + g) = x4;
+          v = make_float4(r4.x + beta * p4.x, r4.y + beta * p4.y, r4.z + beta * p4.z, r4.w + beta * p4.w);
+          *rs = v;
+        }
+        *reinterpret_cast<float4*>(p + g) = v;
+      }
+    }
   }
   __syncthreads();
   plane_x_fwd<N>(PL, tw);
@@ -313,7 +354,7 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH) k_xyfwd(OpArgs<float> a, cons
 // MODE 0: out = P (M xin + g).  MODE 4 (CG): q = P (M p + g) and this block's
 // part of (p, q) in partials[s * c nz + block of the system].
 template <int N, int MODE>
-__global__ void __launch_bounds__(PlaneCfg<N>::TH) k_xyinv(OpArgs<float> a, const float* __restrict__ xin,
+__global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyinv(OpArgs<float> a, const float* __restrict__ xin,
                                                            float* __restrict__ out, const SolverState* __restrict__ st,
                                                            double* __restrict__ partials) {
   typedef PlaneCfg<N> PC;
@@ -365,36 +406,60 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH) k_xyinv(OpArgs<float> a, cons
     PL[ky * RS + N / 2] = ky == (int)threadIdx.x ? nqv : a.nq[(long long)blockIdx.x * N + ky];
   __syncthreads();
   plane_y_inv<N>(PL, tw);
+  // the epilogue's p and phase loads go out in batches of B groups of four
+  // voxels, each batch in flight while the previous one is worked on
+  constexpr int B = PC::IT % 4 == 0 ? 4 : (PC::IT % 3 == 0 ? 3 : (PC::IT % 2 == 0 ? 2 : 1));
+  float4 xb[B];
+  uchar4 hb[B];
+  auto load_batch = [&](int it0) {
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int idx = threadIdx.x + (it0 + b) * TH;
+      const int row = idx / NV, xx = (idx - row * NV) * 4;
+      xb[b] = *reinterpret_cast<const float4*>(xin + plane + (long long)row * N + xx);
+      hb[b] = *reinterpret_cast<const uchar4*>(a.phase + pbase + (long long)row * N + xx);
+    }
+  };
   plane_x_inv<N>(PL, tw);
+  load_batch(0);
   __syncthreads();
   Acc<float> acc;
-#pragma unroll 8
-  for (int it = 0; it < PC::IT; ++it) {
-    const int idx = threadIdx.x + it * TH;
-    const int row = idx / NV, xx = (idx - row * NV) * 4;
-    const long long g = plane + (long long)row * N + xx;
-    const long long vox = pbase + (long long)row * N + xx;
-    const float4 xq4 = *reinterpret_cast<const float4*>(xin + g);
-    const uchar4 ph4 = *reinterpret_cast<const uchar4*>(a.phase + vox);
-    const float4 g4 = *reinterpret_cast<const float4*>(PR + 2 * RS * row + xx);
-    const float xq[4] = {xq4.x, xq4.y, xq4.z, xq4.w};
-    const unsigned char ph[4] = {ph4.x, ph4.y, ph4.z, ph4.w};
-    const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
-    float ov[4];
+#pragma unroll 1
+  for (int it0 = 0; it0 < PC::IT; it0 += B) {
+    float4 xc[B];
+    uchar4 hc[B];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int pp = ph[u];
-      const bool active = aloc[pp] != 0;
-      float m = mloc[pp * a.c + comp];
-      if (a.scale) {
-        const float f = a.scale[vox + u];
-        m = a.frac ? f * mloc[a.c + comp] + (1.f - f) * mloc[comp]  // Eq. (def_ah)
-                   : 1.f / (f * m - a.ref[comp]);
-      }
-      ov[u] = active ? m * xq[u] + gv[u] : 0.f;
-      if (MODE == 4) acc.add(xq[u] * ov[u]);
+    for (int b = 0; b < B; ++b) {
+      xc[b] = xb[b];
+      hc[b] = hb[b];
     }
-    *reinterpret_cast<float4*>(out + g) = make_float4(ov[0], ov[1], ov[2], ov[3]);
+    if (it0 + B < PC::IT) load_batch(it0 + B);
+#pragma unroll
+    for (int b = 0; b < B; ++b) {
+      const int idx = threadIdx.x + (it0 + b) * TH;
+      const int row = idx / NV, xx = (idx - row * NV) * 4;
+      const long long g = plane + (long long)row * N + xx;
+      const long long vox = pbase + (long long)row * N + xx;
+      const float4 g4 = *reinterpret_cast<const float4*>(PR + 2 * RS * row + xx);
+      const float xq[4] = {xc[b].x, xc[b].y, xc[b].z, xc[b].w};
+      const unsigned char ph[4] = {hc[b].x, hc[b].y, hc[b].z, hc[b].w};
+      const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
+      float ov[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int pp = ph[u];
+        const bool active = aloc[pp] != 0;
+        float m = mloc[pp * a.c + comp];
+        if (a.scale) {
+          const float f = a.scale[vox + u];
+          m = a.frac ? f * mloc[a.c + comp] + (1.f - f) * mloc[comp]  // Eq. (def_ah)
+                     : 1.f / (f * m - a.ref[comp]);
+        }
+        ov[u] = active ? m * xq[u] + gv[u] : 0.f;
+        if (MODE == 4) acc.add(xq[u] * ov[u]);
+      }
+      *reinterpret_cast<float4*>(out + g) = make_float4(ov[0], ov[1], ov[2], ov[3]);
+    }
   }
   if (MODE == 4) {
     const double tot = block_reduce(acc);

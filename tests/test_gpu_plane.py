@@ -199,3 +199,48 @@ def test_plane_apply_with_unaligned_caller_buffers():
     h.apply(x_un, out=y_un)
     y_al = h.apply(x_un.clone())
     assert torch.equal(y_un, y_al)
+
+
+def _rotation3(seed):
+    q, _ = np.linalg.qr(np.random.default_rng(seed).standard_normal((3, 3)))
+    return q
+
+
+def test_plane_anisotropic_commuting_phases():
+    """Scalar conductivity with anisotropic phase tensors commuting with the reference
+    (Eq. (hyp3)): the plane schedule works in their common eigenbasis like the other
+    passes; FP32 apply on a radix-3 plane and the mixed C* on a power-of-two plane
+    against the oracle's full-tensor computation."""
+    Q = _rotation3(5)
+    rng = np.random.default_rng(6)
+    mods = np.array([Q @ np.diag(rng.uniform(1.0, 8.0, 3)) @ Q.T for _ in range(3)])
+    mods = 0.5 * (mods + mods.transpose(0, 2, 1))
+    ref = Q @ np.diag([0.4, 0.5, 0.35]) @ Q.T
+    ref = 0.5 * (ref + ref.T)
+    for shape, check_effective in (((16, 48, 48), False), ((16, 32, 32), True)):
+        ph = rng.integers(0, 3, shape).astype(np.uint8)
+        P = oracle.Problem(ph, mods, physics=0, green=1, ref=ref)
+        h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, green=lsh.FILTERED, ref=ref, precision=lsh.MIXED)
+        h.set_variants(0, 0, 2, 0)
+        x = rng.standard_normal(P.field_shape)
+        assert rel(h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy(), oracle.apply(P, x)) < 2e-5
+        if check_effective:
+            A, _ = h.effective(tol=1e-11)
+            Ao, _ = oracle.effective(P, tol=1e-13)
+            assert rel(A, Ao) < 1e-8, rel(A, Ao)
+
+
+def test_plane_batched_apply_matches_oracle():
+    """Two microstructures of one radix-3 plane grid in one batch handle: each system's
+    planes find their own phase map (FP32 plane apply against the oracle)."""
+    rng = np.random.default_rng(12)
+    shape = (16, 48, 48)
+    phs = [(rng.random(shape) < f).astype(np.uint8) for f in (0.2, 0.45)]
+    h = lsh.Handle(torch.from_numpy(np.stack(phs)).cuda(), EL, physics=lsh.ELASTIC, green=lsh.FILTERED,
+                   precision=lsh.MIXED, batch=True)
+    h.set_variants(0, 0, 2, 0)
+    x = rng.standard_normal((2, 6) + shape)
+    y = h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy()
+    for b, ph in enumerate(phs):
+        yo = oracle.apply(oracle.Problem(ph, EL, physics=1, green=1), x[b])
+        assert rel(y[b], yo) < 2e-5, b
