@@ -124,8 +124,9 @@ typedef struct lsh_solve_opts {
   int maxit;         /* iteration limit (FP64 CG iterations, or inner iterations summed) */
   int solver;        /* LSH_SOLVER_AUTO, _CG, _MINRES, _BASIC or _SYMMLQ                   */
   double inner_tol;  /* LSH_MIXED: relative residual reduction of each inner solve
-                        (<= 0 selects 0.5 sqrt(tol) within [1e-6, 1e-3]: two
-                        refinement steps)                                               */
+                        (<= 0 selects 0.5 sqrt(tol) within [1e-6, 1e-3], relaxed on
+                        later steps to half of what the least converged system of
+                        the wave still needs: two refinement steps)                   */
   int max_outer;     /* LSH_MIXED: refinement steps (<= 0 selects 30)                    */
   int check_every;   /* iterations between host convergence checks (<= 0 selects 8)     */
   int warm_start;    /* lsh_solve: tau holds the initial guess on entry                  */

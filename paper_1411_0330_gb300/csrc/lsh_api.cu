@@ -1244,7 +1244,17 @@ lsh_status solve_wave(lsh_handle* h, const Wave& w, bool warm, const lsh_solve_o
         break;
       }
       LSH_CK(cudaMemcpyAsync(h->flags, active.data(), S, cudaMemcpyHostToDevice, h->stream));
-      launch_d2f_begin(Pd.r, rdf, Pf.r, Pf.x, n, S, Pf.st, h->partials, itol, h->flags, Pf.L.ew_per_sys,
+      // default inner tolerance: relaxed on later steps to what still separates
+      // the least converged system from the target (half of it, for the FP32
+      // solve's recursive residual running ahead of the true one)
+      double itol_k = itol;
+      if (!(o && o->inner_tol > 0)) {
+        double worst = 0.0;
+        for (int s = 0; s < S; ++s)
+          if (active[s] && bb[s] > 0) worst = std::max(worst, std::sqrt(rr[s] / bb[s]));
+        if (worst > 0.0) itol_k = std::min(1e-3, std::max(itol, 0.5 * tol / worst));
+      }
+      launch_d2f_begin(Pd.r, rdf, Pf.r, Pf.x, n, S, Pf.st, h->partials, itol_k, h->flags, Pf.L.ew_per_sys,
                        h->stream);
       h->launches += 1;
       if ((stt = cg_run<float>(h, Pf, af, maxit - total_max, check, graphs, st))) return stt;
