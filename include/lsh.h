@@ -163,13 +163,16 @@ typedef struct lsh_tune_report {
                      of 4 columns; 7 register FFT in a persistent kernel that stages
                      the next tile's columns by asynchronous copies; 8 register FFT
                      in blocks of 16 columns; 9 the default register kernel loading
-                     each frequency's Gamma coefficients when it applies them      */
+                     each frequency's Gamma coefficients when it applies them; 10
+                     (plane passes only) persistent kernel on tiles of 8 columns
+                     brought in and written back by TMA, double-buffered, with the
+                     FFT and Gamma exchanges in the tile's buffer                */
   float xf_ms[2]; /* measured time of one launch per candidate (-1: not available)   */
   float x_ms[4];
   float y_ms[2];
   float z_ms[10];
   float xy_ms[2]; /* one CG iteration's passes summed: separate x/y passes, plane passes */
-  float zp_ms[5]; /* z pass on the ky-major spectrum, variants 0, 6, 8, 9, 7          */
+  float zp_ms[6]; /* z pass on the ky-major spectrum, variants 0, 6, 8, 9, 7, 10      */
 } lsh_tune_report;
 
 /* Bytes of device workspace lsh_setup needs for this problem. */
@@ -228,7 +231,7 @@ lsh_status lsh_autotune(lsh_handle *h, lsh_tune_report *rep);
 
 /* Select the FP32 forward x / inverse x / y / z pass variants by hand (numbering of lsh_tune_report;
  * no counterpart in the paper: for tests and measurements).  y_variant 2
- * selects the plane passes (x variants ignored; z variant 0, 6, 7, 8 or 9).
+ * selects the plane passes (x variants ignored; z variant 0, 6, 7, 8, 9 or 10).
  * Returns LSH_ERR_UNSUPPORTED if a variant is not available for this problem
  * (FP64 handles accept only zeros). */
 lsh_status lsh_set_variants(lsh_handle *h, int xf_variant, int x_variant, int y_variant, int z_variant);

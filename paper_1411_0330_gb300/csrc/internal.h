@@ -64,11 +64,14 @@ template <typename T> struct OpArgs {
   int ytma;           // 1: TMA y pass
   int ztma;           // 0: register z pass; 1..5: the variant of launch_zgamma_tma; 6: register, 4 columns;
                       // 7: persistent register z pass with staged prefetch; 8: register, 16 columns;
-                      // 9: register, coefficients loaded when used
+                      // 9: register, coefficients loaded when used; 10: pipelined TMA tiles on the
+                      // ky-major spectrum (kernels_zpipe.cu)
   const CUtensorMap* tmy;
   const CUtensorMap* tmz;   // z boxes of 4 columns
   const CUtensorMap* tmz8;  // z boxes of 8 columns
   const CUtensorMap* tmz16; // z boxes of 16 columns
+  const CUtensorMap* tmzp;  // ky-major spectrum, boxes of 8 columns (variant 10)
+  const CUtensorMap* tmzq;  // Nyquist columns of the ky-major spectrum, boxes of 8 ky
   int* fault;  // set by a kernel whose bounded wait ran out
   int xreg;    // FP32 inverse x pass: 0 shared-memory stages, 1 register FFT, 2 register FFT persistent,
                // 3 register FFT in blocks of 128 threads
@@ -152,6 +155,11 @@ bool encode_y_map(CUtensorMap* out, void* H, int hs, int ny, long long planes);
 bool launch_zgamma_tma(const OpArgs<float>& a, int var, const SolverState* st, cudaStream_t s);
 bool tma_z_variant_fits(const OpArgs<float>& a, int var);
 bool launch_zgamma_regp(const OpArgs<float>& a, const SolverState* st, cudaStream_t s);
+bool launch_zgamma_pipe(const OpArgs<float>& a, const SolverState* st, cudaStream_t s);
+bool encode_zpipe_maps(CUtensorMap* th, CUtensorMap* tq, void* H, void* NQ, int hs, int ny, int nz, int c,
+                       long long nsys);
+void zpipe_prepare();
+int multiprocessors();
 // double-float passes (kernels_df.cu); DF and DF2 come from df.cuh
 struct DF;
 struct DF2;

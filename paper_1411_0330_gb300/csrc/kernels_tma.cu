@@ -85,11 +85,11 @@ __global__ void __launch_bounds__(YTma<N>::THREADS) k_yfft_tma(const __grid_cons
     }
     if (cur_live) {
       const bool ok = mbar_wait(&bar[b], par[b]);
-      par[b] ^= 1;
       if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) fault = 1;
-        break;
+        break;  // par keeps the pending phase of this buffer for the final wait
       }
+      par[b] ^= 1;
       float2* T = tile[b];
       float2 v[R1];
       if (!INV) {
@@ -211,11 +211,11 @@ __global__ void __launch_bounds__(ZTma<NC, N, TZ, NB>::THREADS, ZTma<NC, N, TZ, 
     }
     if (cur_live) {
       const bool ok = mbar_wait(&bar[b], par[b]);
-      par[b] ^= 1;
       if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) fault = 1;
-        break;
+        break;  // par keeps the pending phase of this buffer for the final wait
       }
+      par[b] ^= 1;
       int s, yp, kx0;
       coords(cur, s, yp, kx0);
       float2* T = tile[b];
@@ -353,11 +353,11 @@ __global__ void __launch_bounds__(ZTma16<NC, N, CPT>::THREADS, 1)
     }
     if (cur_live) {
       const bool ok = mbar_wait(&bar[b], par[b]);
-      par[b] ^= 1;
       if (__syncthreads_or(!ok)) {
         if (threadIdx.x == 0) fault = 1;
-        break;
+        break;  // par keeps the pending phase of this buffer for the final wait
       }
+      par[b] ^= 1;
       int s, yp, kx0;
       coords(cur, s, yp, kx0);
       float2* T = tile[b];

@@ -489,7 +489,9 @@ template <typename T> struct PrecBufs {
   CUtensorMap tmz{};          // z-pass tensor maps over H (FP32), boxes of 4 and 8 columns
   CUtensorMap tmz8{};
   CUtensorMap tmz16{};
-  bool ytma_ok = false, ztma_ok = false;
+  CUtensorMap tmzp{};         // ky-major spectrum and its Nyquist columns (plane passes)
+  CUtensorMap tmzq{};
+  bool ytma_ok = false, ztma_ok = false, zpipe_ok = false;
 };
 
 }  // namespace
@@ -674,6 +676,13 @@ void init_prec(lsh_handle* h, PrecBufs<T>& P, const size_t* off_f, size_t off_H,
     P.ztma_ok = encode_z_map(&P.tmz, P.H, d.hs, d.ny, d.nz, d.c, d.Smax, 4) &&
                 encode_z_map(&P.tmz8, P.H, d.hs, d.ny, d.nz, d.c, d.Smax, 8) &&
                 encode_z_map(&P.tmz16, P.H, d.hs, d.ny, d.nz, d.c, d.Smax, 16);
+  a.tmzp = nullptr;
+  a.tmzq = nullptr;
+  if (sizeof(T) == 4 && d.plane && !h->no_tma &&
+      (P.zpipe_ok = encode_zpipe_maps(&P.tmzp, &P.tmzq, P.H, a.nq, d.hs, d.ny, d.nz, d.c, d.Smax))) {
+    a.tmzp = &P.tmzp;
+    a.tmzq = &P.tmzq;
+  }
   for (int i = 0; i < 6; ++i) a.g0[i] = (T)0;
   if (d.physics == LSH_ELASTIC_ISO) {
     const double K0 = d.ref_user[0], mu0 = d.ref_user[1], lam0 = K0 - 2.0 * mu0 / 3.0;
@@ -1468,7 +1477,10 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   set_smem_attrs<float>();
   tma_prepare();
   xreg_prepare();
-  if (d.plane) plane_prepare();
+  if (d.plane) {
+    plane_prepare();
+    zpipe_prepare();
+  }
   if (l.df) df_prepare();
   launch_gamma_table<double>(h->pd.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st,
                              d.rotated ? d.A0full : nullptr, d.rotated ? d.R : nullptr);
@@ -1712,7 +1724,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
   for (int k = 0; k < 10; ++k) r.z_ms[k] = -1.f;
   for (int k = 0; k < 2; ++k) r.xy_ms[k] = -1.f;
-  for (int k = 0; k < 5; ++k) r.zp_ms[k] = -1.f;
+  for (int k = 0; k < 6; ++k) r.zp_ms[k] = -1.f;
   const Derived& d = h->d;
   if (d.precision == LSH_MIXED) {
     PrecBufs<float>& P = h->pf;
@@ -1818,12 +1830,13 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       OpArgs<float> b = a;
       b.plane = 1;
       b.tlay = 1;
-      const int zc[5] = {0, 6, 8, 9, 7};
+      const int zc[6] = {0, 6, 8, 9, 7, 10};
       int bz = 0;
-      for (int k = 0; k < 5; ++k) {
+      for (int k = 0; k < 6; ++k) {
         b.ztma = zc[k];
         r.zp_ms[k] = timeit([&]() {
           if (zc[k] == 7) return launch_zgamma_regp(b, nullptr, s);
+          if (zc[k] == 10) return launch_zgamma_pipe(b, nullptr, s);
           launch_zgamma<float>(b, P.L, nullptr, s);
           return true;
         });
@@ -1871,19 +1884,20 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
 lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
   if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 3 || y_variant < 0 || y_variant > 2 ||
-      z_variant < 0 || z_variant > 9)
+      z_variant < 0 || z_variant > 10)
     return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;
   if (h->d.precision != LSH_MIXED)
     return (xf_variant || x_variant || y_variant || z_variant) ? LSH_ERR_UNSUPPORTED : LSH_OK;
   if (y_variant == 2) {
     // plane passes: the register z kernels on the ky-major spectrum
-    if (!h->d.plane || !(z_variant == 0 || (z_variant >= 6 && z_variant <= 9))) return LSH_ERR_UNSUPPORTED;
-    if (z_variant == 7) {
-      OpArgs<float> a = P.a;
-      a.S = 0;
-      if (!launch_zgamma_regp(a, nullptr, 0)) return LSH_ERR_UNSUPPORTED;
-    }
+    if (!h->d.plane || !(z_variant == 0 || z_variant >= 6)) return LSH_ERR_UNSUPPORTED;
+    OpArgs<float> a = P.a;
+    a.S = 0;
+    a.plane = 1;
+    a.tlay = 1;
+    if (z_variant == 7 && !launch_zgamma_regp(a, nullptr, 0)) return LSH_ERR_UNSUPPORTED;
+    if (z_variant == 10 && !launch_zgamma_pipe(a, nullptr, 0)) return LSH_ERR_UNSUPPORTED;
     P.a.plane = 1;
     P.a.tlay = 1;
     P.a.ztma = z_variant;
@@ -1895,6 +1909,7 @@ lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_
   if (xf_variant == 1 && !xfwd_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;
   if (z_variant >= 6 && !P.a.zreg) return LSH_ERR_UNSUPPORTED;
+  if (z_variant == 10) return LSH_ERR_UNSUPPORTED;  // ky-major spectrum only
   if (z_variant == 7) {
     OpArgs<float> a = P.a;
     a.S = 0;

@@ -67,7 +67,7 @@ def test_plane_apply_matches_oracle(shape, physics, green):
     P = oracle.Problem(ph, mods, physics=physics, green=green)
     x = np.random.default_rng(1).standard_normal(P.field_shape)
     yo = oracle.apply(P, x)
-    for zv in (0, 6, 7, 8, 9):
+    for zv in (0, 6, 7, 8, 9, 10):
         h.set_variants(0, 0, 2, zv)
         y = h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy()
         assert rel(y, yo) < 2e-5, zv
@@ -85,6 +85,31 @@ def test_plane_passes_agree_with_separate_passes(shape):
     h.set_variants(0, 0, 2, 0)
     y_pl = h.apply(x).cpu().numpy()
     assert rel(y_pl, y_sep) < 2e-5
+
+
+@pytest.mark.parametrize("n,green,nsys", [(32, 1, 6), (16, 0, 6), (48, 1, 3), (64, 1, 2)])
+def test_pipelined_z_pass_mixed_effective_matches_oracle(n, green, nsys):
+    """The TMA-fed z pass (variant 10) inside the mixed solver: C* against the oracle on a
+    seeded packing, with systems converging at different iterations (their tiles are
+    skipped) and waves of fewer systems than loads."""
+    ph, _, _ = ms.sphere_microstructure(n, n / 8.0, 0.25, seed=300 + n)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=green, precision=lsh.MIXED,
+                   max_systems=nsys)
+    h.set_variants(0, 0, 2, 10)
+    A, infos = h.effective(tol=1e-10)
+    Ao, _ = oracle.effective(oracle.Problem(ph, EL, physics=1, green=green), tol=1e-13)
+    assert rel(A, Ao) < 1e-8, rel(A, Ao)
+    assert all(i["status"] == 0 for i in infos)
+
+
+def test_pipelined_z_pass_needs_the_plane_passes():
+    """Variant 10 reads the ky-major spectrum: refused with the separate passes."""
+    ph, mods = _problem((16, 32, 32), 1, 5)
+    h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
+    with pytest.raises(lsh.LSHError) as e:
+        h.set_variants(1, 3, 1, 10)
+    assert e.value.status == lsh.ERR_UNSUPPORTED
+    h.set_variants(0, 0, 2, 10)
 
 
 def test_radix3_grids_refuse_separate_passes():
