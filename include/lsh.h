@@ -166,13 +166,15 @@ typedef struct lsh_tune_report {
                      each frequency's Gamma coefficients when it applies them; 10
                      (plane passes only) persistent kernel on tiles of 8 columns
                      brought in and written back by TMA, double-buffered, with the
-                     FFT and Gamma exchanges in the tile's buffer                */
+                     FFT and Gamma exchanges in the tile's buffer; 11 the same with
+                     the second FFT level and Gamma in one register phase (lengths
+                     16, 32, 48 and 96)                                             */
   float xf_ms[2]; /* measured time of one launch per candidate (-1: not available)   */
   float x_ms[4];
   float y_ms[2];
   float z_ms[10];
   float xy_ms[2]; /* one CG iteration's passes summed: separate x/y passes, plane passes */
-  float zp_ms[6]; /* z pass on the ky-major spectrum, variants 0, 6, 8, 9, 7, 10      */
+  float zp_ms[7]; /* z pass on the ky-major spectrum, variants 0, 6, 8, 9, 7, 10, 11  */
 } lsh_tune_report;
 
 /* Bytes of device workspace lsh_setup needs for this problem. */
@@ -231,7 +233,7 @@ lsh_status lsh_autotune(lsh_handle *h, lsh_tune_report *rep);
 
 /* Select the FP32 forward x / inverse x / y / z pass variants by hand (numbering of lsh_tune_report;
  * no counterpart in the paper: for tests and measurements).  y_variant 2
- * selects the plane passes (x variants ignored; z variant 0, 6, 7, 8, 9 or 10).
+ * selects the plane passes (x variants ignored; z variant 0 or 6 to 11).
  * Returns LSH_ERR_UNSUPPORTED if a variant is not available for this problem
  * (FP64 handles accept only zeros). */
 lsh_status lsh_set_variants(lsh_handle *h, int xf_variant, int x_variant, int y_variant, int z_variant);

@@ -65,7 +65,8 @@ template <typename T> struct OpArgs {
   int ztma;           // 0: register z pass; 1..5: the variant of launch_zgamma_tma; 6: register, 4 columns;
                       // 7: persistent register z pass with staged prefetch; 8: register, 16 columns;
                       // 9: register, coefficients loaded when used; 10: pipelined TMA tiles on the
-                      // ky-major spectrum (kernels_zpipe.cu)
+                      // ky-major spectrum (kernels_zpipe.cu); 11: the same with the level-b DFTs
+                      // and Gamma^h fused (P = 4 plans)
   const CUtensorMap* tmy;
   const CUtensorMap* tmz;   // z boxes of 4 columns
   const CUtensorMap* tmz8;  // z boxes of 8 columns
@@ -155,7 +156,7 @@ bool encode_y_map(CUtensorMap* out, void* H, int hs, int ny, long long planes);
 bool launch_zgamma_tma(const OpArgs<float>& a, int var, const SolverState* st, cudaStream_t s);
 bool tma_z_variant_fits(const OpArgs<float>& a, int var);
 bool launch_zgamma_regp(const OpArgs<float>& a, const SolverState* st, cudaStream_t s);
-bool launch_zgamma_pipe(const OpArgs<float>& a, const SolverState* st, cudaStream_t s);
+bool launch_zgamma_pipe(const OpArgs<float>& a, bool fused, const SolverState* st, cudaStream_t s);
 bool encode_zpipe_maps(CUtensorMap* th, CUtensorMap* tq, void* H, void* NQ, int hs, int ny, int nz, int c,
                        long long nsys);
 void zpipe_prepare();

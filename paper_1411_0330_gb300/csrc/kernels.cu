@@ -1230,7 +1230,7 @@ void launch_zgamma(const OpArgs<T>& a, const LaunchCfg& L, const SolverState* st
     // the TMA variants read the x-major layout only
     if (!a.tlay && a.ztma >= 1 && a.ztma <= 5 && launch_zgamma_tma(a, a.ztma, st, s)) return;
     if (a.ztma == 7 && launch_zgamma_regp(a, st, s)) return;
-    if (a.ztma == 10 && launch_zgamma_pipe(a, st, s)) return;
+    if ((a.ztma == 10 || a.ztma == 11) && launch_zgamma_pipe(a, a.ztma == 11, st, s)) return;
   }
   if (a.zreg) {
     int tz = 0;

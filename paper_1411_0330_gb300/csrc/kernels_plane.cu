@@ -424,6 +424,11 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyinv(Op
   load_batch(0);
   __syncthreads();
   Acc<float> acc;
+  // two phases without a voxel field (the common case): both phases' M and
+  // activity in registers, selected per voxel instead of read from the tables
+  const bool two = a.nphase <= 2 && !a.scale;
+  const float m0 = mloc[comp], m1 = a.nphase > 1 ? mloc[a.c + comp] : m0;
+  const bool act0 = aloc[0] != 0, act1 = a.nphase > 1 ? aloc[1] != 0 : act0;
 #pragma unroll 1
   for (int it0 = 0; it0 < PC::IT; it0 += B) {
     float4 xc[B];
@@ -445,19 +450,28 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyinv(Op
       const unsigned char ph[4] = {hc[b].x, hc[b].y, hc[b].z, hc[b].w};
       const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
       float ov[4];
+      if (two) {
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int pp = ph[u];
-        const bool active = aloc[pp] != 0;
-        float m = mloc[pp * a.c + comp];
-        if (a.scale) {
-          const float f = a.scale[vox + u];
-          m = a.frac ? f * mloc[a.c + comp] + (1.f - f) * mloc[comp]  // Eq. (def_ah)
-                     : 1.f / (f * m - a.ref[comp]);
+        for (int u = 0; u < 4; ++u) {
+          const bool p1 = ph[u] != 0;
+          ov[u] = (p1 ? act1 : act0) ? fmaf(p1 ? m1 : m0, xq[u], gv[u]) : 0.f;
         }
-        ov[u] = active ? m * xq[u] + gv[u] : 0.f;
-        if (MODE == 4) acc.add(xq[u] * ov[u]);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int pp = ph[u];
+          const bool active = aloc[pp] != 0;
+          float m = mloc[pp * a.c + comp];
+          if (a.scale) {
+            const float f = a.scale[vox + u];
+            m = a.frac ? f * mloc[a.c + comp] + (1.f - f) * mloc[comp]  // Eq. (def_ah)
+                       : 1.f / (f * m - a.ref[comp]);
+          }
+          ov[u] = active ? m * xq[u] + gv[u] : 0.f;
+        }
       }
+      // (p, K p): the group's four products summed in FP32, then one compensated add
+      if (MODE == 4) acc.add(fmaf(xq[3], ov[3], fmaf(xq[2], ov[2], fmaf(xq[1], ov[1], xq[0] * ov[0]))));
       *reinterpret_cast<float4*>(out + g) = make_float4(ov[0], ov[1], ov[2], ov[3]);
     }
   }

@@ -35,15 +35,19 @@
 
 namespace lsh {
 
-template <int NC, int N> struct ZPipe {
+// FUSED (P = 4 plans): one thread per (k1, column) takes the P-point DFTs of
+// all NC components, the Gamma^h product at its P frequencies k1 + R1 k2 and
+// the inverse P-point DFTs in registers; the exchange rows are then e + e / P.
+template <int NC, int N, bool FUSED = false> struct ZPipe {
   static constexpr int TZ = 8;                   // columns per tile
   static constexpr int P = RegPlan<N>::P, R1 = RegPlan<N>::R1, Q = R1 / P;
   static constexpr int THREADS = TZ * P * NC;
-  static constexpr int NX = N + N / R1;          // exchange rows per component
+  static constexpr int NX = FUSED ? N + N / P : N + N / R1;  // exchange rows per component
+  static constexpr bool FUSABLE = P == 4 && R1 * TZ <= THREADS;
   static constexpr int BUF = NC * NX * TZ;       // complex values per buffer
   static constexpr uint32_t BOX_BYTES = (uint32_t)(sizeof(float2) * NC * N * TZ);
   static constexpr size_t SMEM = 2 * sizeof(float2) * BUF + sizeof(float2) * N + 128;
-  static constexpr bool FITS = THREADS <= 1024 && SMEM <= 227 * 1024 && (NX % 2) == 0;
+  static constexpr bool FITS = THREADS <= 1024 && SMEM <= 227 * 1024 && (NX % 2) == 0 && (!FUSED || FUSABLE);
   static constexpr int MINB = (2 * SMEM <= 226 * 1024 && 2 * THREADS <= 1024) ? 2 : 1;
 };
 
@@ -53,11 +57,69 @@ template <int Q> __device__ __forceinline__ int zp_grow(int kz) {
   else return kz;
 }
 
+// The middle of the FUSED kernel: thread (k1, column li) reads element k1 P + u
+// (u < P) of every component's line from the exchange (row k1 (P + 1) + u),
+// transforms over u, applies Gamma^h_k at kz = k1 + R1 k2 to the NC components
+// of each k2, transforms back and writes the same rows.  The coefficients of
+// the next k2 load while the current ones are applied.
 template <int NC, int N>
-__global__ void __launch_bounds__(ZPipe<NC, N>::THREADS, ZPipe<NC, N>::MINB)
+__device__ __forceinline__ void zp_fused_middle(const OpArgs<float>& a, float2* B, bool nyq, int yp, int kx0) {
+  typedef ZPipe<NC, N, true> ZC;
+  constexpr int TZ = ZC::TZ, P = ZC::P, R1 = ZC::R1, NX = ZC::NX;
+  if (threadIdx.x >= R1 * TZ) return;
+  const int li = threadIdx.x & (TZ - 1), k1 = threadIdx.x / TZ;
+  float2* const base = B + k1 * (P + 1) * TZ + li;
+  const int kx = nyq ? kx0 : kx0 + li, ypos = nyq ? yp + li : yp;
+  float2 d[NC][P];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+#pragma unroll
+    for (int u = 0; u < P; ++u) d[c][u] = base[(c * NX + u) * TZ];
+    Dft<float, P, false>::run(d[c], nullptr, N);
+  }
+  if (a.onfly) {
+    const int ky = a.kofy[ypos];
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) {
+      float2 g[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) g[c] = d[c][k2];
+      gamma_trunc_onfly<float, NC>(a, kx, ky, k1 + R1 * k2, g);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) d[c][k2] = g[c];
+    }
+  } else {
+    constexpr int NCO = GammaPack<NC>::NCO;
+    const long long f0 = ((long long)k1 * a.ny + ypos) * a.ts + kx;  // frequency (kx, ky, k1)
+    const long long fs = (long long)R1 * a.ny * a.ts;                // kz step R1
+    float gc[2][NCO];
+    gamma_coef_load<float, NC>(a.gtab, f0, gc[0]);
+#pragma unroll
+    for (int k2 = 0; k2 < P; ++k2) {
+      if (k2 + 1 < P) gamma_coef_load<float, NC>(a.gtab, f0 + (k2 + 1) * fs, gc[(k2 + 1) & 1]);
+      float2 g[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) g[c] = d[c][k2];
+      if (a.fdphase) fd_rotate<float, NC>(a, kx, a.kofy[ypos], k1 + R1 * k2, g, -1.f);
+      gamma_coef_apply<float, NC>(gc[k2 & 1], g);
+      if (a.fdphase) fd_rotate<float, NC>(a, kx, a.kofy[ypos], k1 + R1 * k2, g, 1.f);
+#pragma unroll
+      for (int c = 0; c < NC; ++c) d[c][k2] = g[c];
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    Dft<float, P, true>::run(d[c], nullptr, N);
+#pragma unroll
+    for (int u = 0; u < P; ++u) base[(c * NX + u) * TZ] = d[c][u];
+  }
+}
+
+template <int NC, int N, bool FUSED>
+__global__ void __launch_bounds__(ZPipe<NC, N, FUSED>::THREADS, ZPipe<NC, N, FUSED>::MINB)
     k_zgamma_pipe(const __grid_constant__ CUtensorMap tmH, const __grid_constant__ CUtensorMap tmQ, OpArgs<float> a,
                   const SolverState* __restrict__ st, int nkt, int nregular, int total) {
-  typedef ZPipe<NC, N> ZC;
+  typedef ZPipe<NC, N, FUSED> ZC;
   constexpr int TZ = ZC::TZ, P = ZC::P, R1 = ZC::R1, Q = ZC::Q, NX = ZC::NX, THREADS = ZC::THREADS;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   // 128-byte aligned start, kept as an offset into the shared array (shared-window accesses)
@@ -124,7 +186,9 @@ __global__ void __launch_bounds__(ZPipe<NC, N>::THREADS, ZPipe<NC, N>::MINB)
   const int i = threadIdx.x & (TZ - 1), t = (threadIdx.x / TZ) % P, comp = threadIdx.x / (TZ * P);
   // per-thread bases (complex offsets within a buffer)
   const int od = (comp * N + t) * TZ + i;             // dense: x[t + P j] at od + j P TZ
-  const int oa = (comp * NX + t) * TZ + i;            // exchange, element k1 P + t
+  const int oa = (comp * NX + t) * TZ + i;            // exchange, element k1 P + t at row xrow(k1) + t
+  // exchange row offset of element k1 P + t (t < P): k1 P + k1 / Q, or k1 (P + 1) when FUSED
+  auto xrow = [](int k1) { return FUSED ? k1 * (P + 1) : k1 * P + k1 / Q; };
   const int ob = (comp * NX + t * (R1 + 1)) * TZ + i; // exchange, element (t Q + q) P + u
   // Gamma layout, frequency kz(m) = t Q + m / P + R1 (m % P): for even Q its row
   // is kz ^ (t & 1), i.e. one row up or down by the parity of m / P
@@ -155,8 +219,11 @@ __global__ void __launch_bounds__(ZPipe<NC, N>::THREADS, ZPipe<NC, N>::MINB)
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul<float>(v[k1], tw[t * k1]);
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) B[oa + (k1 * P + k1 / Q) * TZ] = v[k1];
+    for (int k1 = 0; k1 < R1; ++k1) B[oa + xrow(k1) * TZ] = v[k1];
     __syncthreads();
+    if constexpr (FUSED) {
+      zp_fused_middle<NC, N>(a, B, nyq, yp, kx0);
+    } else {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
       float2 c[P];
@@ -235,9 +302,10 @@ __global__ void __launch_bounds__(ZPipe<NC, N>::THREADS, ZPipe<NC, N>::MINB)
 #pragma unroll
       for (int u = 0; u < P; ++u) B[ob + (q * P + u) * TZ] = c[u];
     }
+    }  // !FUSED
     __syncthreads();
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) v[k1] = B[oa + (k1 * P + k1 / Q) * TZ];
+    for (int k1 = 0; k1 < R1; ++k1) v[k1] = B[oa + xrow(k1) * TZ];
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmulc<float>(v[k1], tw[t * k1]);
     Dft<float, R1, true>::run(v, tw, N);
@@ -267,13 +335,13 @@ __global__ void __launch_bounds__(ZPipe<NC, N>::THREADS, ZPipe<NC, N>::MINB)
 // ------------------------------------------------------------------ host side
 namespace {
 
-template <int NC, int N> int zpipe_blocks_per_sm() {
-  typedef ZPipe<NC, N> ZC;
+template <int NC, int N, bool FUSED> int zpipe_blocks_per_sm() {
+  typedef ZPipe<NC, N, FUSED> ZC;
   static int n = []() {
     int v = 0;
     if constexpr (ZC::FITS) {
-      cudaFuncSetAttribute(k_zgamma_pipe<NC, N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZC::SMEM);
-      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_zgamma_pipe<NC, N>, ZC::THREADS, ZC::SMEM) !=
+      cudaFuncSetAttribute(k_zgamma_pipe<NC, N, FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ZC::SMEM);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_zgamma_pipe<NC, N, FUSED>, ZC::THREADS, ZC::SMEM) !=
           cudaSuccess) {
         cudaGetLastError();
         v = 0;
@@ -284,12 +352,13 @@ template <int NC, int N> int zpipe_blocks_per_sm() {
   return n;
 }
 
-template <int NC, int N> bool launch_zpipe_n(const OpArgs<float>& a, const SolverState* st, cudaStream_t s) {
-  typedef ZPipe<NC, N> ZC;
+template <int NC, int N, bool FUSED>
+bool launch_zpipe_n(const OpArgs<float>& a, const SolverState* st, cudaStream_t s) {
+  typedef ZPipe<NC, N, FUSED> ZC;
   if constexpr (!ZC::FITS) {
     return false;
   } else {
-    const int bpsm = zpipe_blocks_per_sm<NC, N>();
+    const int bpsm = zpipe_blocks_per_sm<NC, N, FUSED>();
     if (bpsm < 1) return false;
     if (a.S < 1) return true;
     const int nkt = (a.nx / 2) / ZC::TZ;
@@ -297,21 +366,21 @@ template <int NC, int N> bool launch_zpipe_n(const OpArgs<float>& a, const Solve
     const long long total = nregular + (long long)a.S * (a.ny / ZC::TZ);
     const long long grid = std::max<long long>(1, std::min<long long>(total, (long long)multiprocessors() * bpsm));
     if (total + grid >= (1ll << 31)) return false;
-    k_zgamma_pipe<NC, N><<<(unsigned)grid, ZC::THREADS, ZC::SMEM, s>>>(*a.tmzp, *a.tmzq, a, st, nkt, (int)nregular,
-                                                                       (int)total);
+    k_zgamma_pipe<NC, N, FUSED><<<(unsigned)grid, ZC::THREADS, ZC::SMEM, s>>>(*a.tmzp, *a.tmzq, a, st, nkt,
+                                                                              (int)nregular, (int)total);
     return true;
   }
 }
 
-template <int NC> bool launch_zpipe_nc(const OpArgs<float>& a, const SolverState* st, cudaStream_t s) {
+template <int NC, bool FUSED> bool launch_zpipe_nc(const OpArgs<float>& a, const SolverState* st, cudaStream_t s) {
   switch (a.nz) {
-    case 16: return launch_zpipe_n<NC, 16>(a, st, s);
-    case 32: return launch_zpipe_n<NC, 32>(a, st, s);
-    case 48: return launch_zpipe_n<NC, 48>(a, st, s);
-    case 64: return launch_zpipe_n<NC, 64>(a, st, s);
-    case 96: return launch_zpipe_n<NC, 96>(a, st, s);
-    case 128: return launch_zpipe_n<NC, 128>(a, st, s);
-    case 256: return launch_zpipe_n<NC, 256>(a, st, s);
+    case 16: return launch_zpipe_n<NC, 16, FUSED>(a, st, s);
+    case 32: return launch_zpipe_n<NC, 32, FUSED>(a, st, s);
+    case 48: return launch_zpipe_n<NC, 48, FUSED>(a, st, s);
+    case 64: return launch_zpipe_n<NC, 64, FUSED>(a, st, s);
+    case 96: return launch_zpipe_n<NC, 96, FUSED>(a, st, s);
+    case 128: return launch_zpipe_n<NC, 128, FUSED>(a, st, s);
+    case 256: return launch_zpipe_n<NC, 256, FUSED>(a, st, s);
     default: return false;
   }
 }
@@ -332,15 +401,16 @@ PFN_cuTensorMapEncodeTiled_v12000 zp_encode_fn() {
 
 }  // namespace
 
-// Pipelined TMA z pass on the ky-major spectrum; false (nothing launched) when
+// Pipelined TMA z pass on the ky-major spectrum (fused: the P = 4 variant that
+// takes the level-b DFTs and Gamma^h in one register phase); false (nothing launched) when
 // the spectrum is not ky-major, the maps are missing, the geometry has no
 // tiling or the kernel does not fit.  With a.S = 0 it only answers whether it
 // would launch.
-bool launch_zgamma_pipe(const OpArgs<float>& a, const SolverState* st, cudaStream_t s) {
+bool launch_zgamma_pipe(const OpArgs<float>& a, bool fused, const SolverState* st, cudaStream_t s) {
   if (!a.tlay || a.nq == nullptr || a.tmzp == nullptr || a.tmzq == nullptr) return false;
   if ((a.nx & 15) != 0 || (a.ny & 7) != 0) return false;  // whole 8-column tiles of kx < nx/2 and of ky
-  if (a.c == 6) return launch_zpipe_nc<6>(a, st, s);
-  if (a.c == 3) return launch_zpipe_nc<3>(a, st, s);
+  if (a.c == 6) return fused ? launch_zpipe_nc<6, true>(a, st, s) : launch_zpipe_nc<6, false>(a, st, s);
+  if (a.c == 3) return fused ? launch_zpipe_nc<3, true>(a, st, s) : launch_zpipe_nc<3, false>(a, st, s);
   return false;
 }
 
@@ -371,19 +441,21 @@ bool encode_zpipe_maps(CUtensorMap* th, CUtensorMap* tq, void* H, void* NQ, int 
          CUDA_SUCCESS;
 }
 
-template <int NC> void zpipe_prepare_nc() {
-  zpipe_blocks_per_sm<NC, 16>();
-  zpipe_blocks_per_sm<NC, 32>();
-  zpipe_blocks_per_sm<NC, 48>();
-  zpipe_blocks_per_sm<NC, 64>();
-  zpipe_blocks_per_sm<NC, 96>();
-  zpipe_blocks_per_sm<NC, 128>();
-  zpipe_blocks_per_sm<NC, 256>();
+template <int NC, bool FUSED> void zpipe_prepare_nc() {
+  zpipe_blocks_per_sm<NC, 16, FUSED>();
+  zpipe_blocks_per_sm<NC, 32, FUSED>();
+  zpipe_blocks_per_sm<NC, 48, FUSED>();
+  zpipe_blocks_per_sm<NC, 64, FUSED>();
+  zpipe_blocks_per_sm<NC, 96, FUSED>();
+  zpipe_blocks_per_sm<NC, 128, FUSED>();
+  zpipe_blocks_per_sm<NC, 256, FUSED>();
 }
 
 void zpipe_prepare() {
-  zpipe_prepare_nc<3>();
-  zpipe_prepare_nc<6>();
+  zpipe_prepare_nc<3, false>();
+  zpipe_prepare_nc<6, false>();
+  zpipe_prepare_nc<3, true>();
+  zpipe_prepare_nc<6, true>();
 }
 
 }  // namespace lsh

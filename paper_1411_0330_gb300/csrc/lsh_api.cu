@@ -1724,7 +1724,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
   for (int k = 0; k < 2; ++k) r.y_ms[k] = -1.f;
   for (int k = 0; k < 10; ++k) r.z_ms[k] = -1.f;
   for (int k = 0; k < 2; ++k) r.xy_ms[k] = -1.f;
-  for (int k = 0; k < 6; ++k) r.zp_ms[k] = -1.f;
+  for (int k = 0; k < 7; ++k) r.zp_ms[k] = -1.f;
   const Derived& d = h->d;
   if (d.precision == LSH_MIXED) {
     PrecBufs<float>& P = h->pf;
@@ -1830,13 +1830,13 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
       OpArgs<float> b = a;
       b.plane = 1;
       b.tlay = 1;
-      const int zc[6] = {0, 6, 8, 9, 7, 10};
+      const int zc[7] = {0, 6, 8, 9, 7, 10, 11};
       int bz = 0;
-      for (int k = 0; k < 6; ++k) {
+      for (int k = 0; k < 7; ++k) {
         b.ztma = zc[k];
         r.zp_ms[k] = timeit([&]() {
           if (zc[k] == 7) return launch_zgamma_regp(b, nullptr, s);
-          if (zc[k] == 10) return launch_zgamma_pipe(b, nullptr, s);
+          if (zc[k] >= 10) return launch_zgamma_pipe(b, zc[k] == 11, nullptr, s);
           launch_zgamma<float>(b, P.L, nullptr, s);
           return true;
         });
@@ -1884,7 +1884,7 @@ lsh_status lsh_autotune(lsh_handle* h, lsh_tune_report* rep) {
 lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_variant, int z_variant) {
   if (!h) return LSH_ERR_INVALID_ARG;
   if (xf_variant < 0 || xf_variant > 1 || x_variant < 0 || x_variant > 3 || y_variant < 0 || y_variant > 2 ||
-      z_variant < 0 || z_variant > 10)
+      z_variant < 0 || z_variant > 11)
     return LSH_ERR_INVALID_ARG;
   PrecBufs<float>& P = h->pf;
   if (h->d.precision != LSH_MIXED)
@@ -1897,7 +1897,7 @@ lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_
     a.plane = 1;
     a.tlay = 1;
     if (z_variant == 7 && !launch_zgamma_regp(a, nullptr, 0)) return LSH_ERR_UNSUPPORTED;
-    if (z_variant == 10 && !launch_zgamma_pipe(a, nullptr, 0)) return LSH_ERR_UNSUPPORTED;
+    if (z_variant >= 10 && !launch_zgamma_pipe(a, z_variant == 11, nullptr, 0)) return LSH_ERR_UNSUPPORTED;
     P.a.plane = 1;
     P.a.tlay = 1;
     P.a.ztma = z_variant;
@@ -1909,7 +1909,7 @@ lsh_status lsh_set_variants(lsh_handle* h, int xf_variant, int x_variant, int y_
   if (xf_variant == 1 && !xfwd_reg_fits(P.a)) return LSH_ERR_UNSUPPORTED;
   if (y_variant == 1 && !P.ytma_ok) return LSH_ERR_UNSUPPORTED;
   if (z_variant >= 6 && !P.a.zreg) return LSH_ERR_UNSUPPORTED;
-  if (z_variant == 10) return LSH_ERR_UNSUPPORTED;  // ky-major spectrum only
+  if (z_variant >= 10) return LSH_ERR_UNSUPPORTED;  // ky-major spectrum only
   if (z_variant == 7) {
     OpArgs<float> a = P.a;
     a.S = 0;

@@ -59,7 +59,7 @@ class _TuneReport(ctypes.Structure):
     _fields_ = [("xf_variant", ctypes.c_int), ("x_variant", ctypes.c_int), ("y_variant", ctypes.c_int),
                 ("z_variant", ctypes.c_int), ("xf_ms", ctypes.c_float * 2), ("x_ms", ctypes.c_float * 4),
                 ("y_ms", ctypes.c_float * 2), ("z_ms", ctypes.c_float * 10), ("xy_ms", ctypes.c_float * 2),
-                ("zp_ms", ctypes.c_float * 6)]
+                ("zp_ms", ctypes.c_float * 7)]
 
 
 class _Info(ctypes.Structure):

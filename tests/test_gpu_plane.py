@@ -67,7 +67,14 @@ def test_plane_apply_matches_oracle(shape, physics, green):
     P = oracle.Problem(ph, mods, physics=physics, green=green)
     x = np.random.default_rng(1).standard_normal(P.field_shape)
     yo = oracle.apply(P, x)
-    for zv in (0, 6, 7, 8, 9, 10):
+    for zv in (0, 6, 7, 8, 9, 10, 11):
+        if zv == 11 and (shape[0] not in (16, 32, 48, 96) or (physics == 0 and shape[0] * 2 > 3 * 32)):
+            # the fused z pass needs a z length with a 4-thread register plan and one
+            # thread per (k1, column): R1 8 <= 8 P c, i.e. z length <= 48 for 3 components
+            with pytest.raises(lsh.LSHError) as e:
+                h.set_variants(0, 0, 2, zv)
+            assert e.value.status == lsh.ERR_UNSUPPORTED
+            continue
         h.set_variants(0, 0, 2, zv)
         y = h.apply(torch.from_numpy(x).float().cuda()).cpu().numpy()
         assert rel(y, yo) < 2e-5, zv
@@ -87,15 +94,17 @@ def test_plane_passes_agree_with_separate_passes(shape):
     assert rel(y_pl, y_sep) < 2e-5
 
 
-@pytest.mark.parametrize("n,green,nsys", [(32, 1, 6), (16, 0, 6), (48, 1, 3), (64, 1, 2)])
-def test_pipelined_z_pass_mixed_effective_matches_oracle(n, green, nsys):
-    """The TMA-fed z pass (variant 10) inside the mixed solver: C* against the oracle on a
-    seeded packing, with systems converging at different iterations (their tiles are
-    skipped) and waves of fewer systems than loads."""
+@pytest.mark.parametrize("n,green,nsys,zv", [(32, 1, 6, 10), (16, 0, 6, 10), (48, 1, 3, 10), (64, 1, 2, 10),
+                                             (32, 1, 6, 11), (16, 0, 4, 11), (48, 1, 3, 11)])
+def test_pipelined_z_pass_mixed_effective_matches_oracle(n, green, nsys, zv):
+    """The TMA-fed z passes (variant 10, and 11 with the level-b DFTs and Gamma^h fused)
+    inside the mixed solver: C* against the oracle on a seeded packing, with systems
+    converging at different iterations (their tiles are skipped) and waves of fewer
+    systems than loads."""
     ph, _, _ = ms.sphere_microstructure(n, n / 8.0, 0.25, seed=300 + n)
     h = lsh.Handle(torch.from_numpy(ph).cuda(), EL, physics=lsh.ELASTIC, green=green, precision=lsh.MIXED,
                    max_systems=nsys)
-    h.set_variants(0, 0, 2, 10)
+    h.set_variants(0, 0, 2, zv)
     A, infos = h.effective(tol=1e-10)
     Ao, _ = oracle.effective(oracle.Problem(ph, EL, physics=1, green=green), tol=1e-13)
     assert rel(A, Ao) < 1e-8, rel(A, Ao)
@@ -106,10 +115,17 @@ def test_pipelined_z_pass_needs_the_plane_passes():
     """Variant 10 reads the ky-major spectrum: refused with the separate passes."""
     ph, mods = _problem((16, 32, 32), 1, 5)
     h = lsh.Handle(torch.from_numpy(ph).cuda(), mods, physics=lsh.ELASTIC, green=lsh.FILTERED, precision=lsh.MIXED)
-    with pytest.raises(lsh.LSHError) as e:
-        h.set_variants(1, 3, 1, 10)
-    assert e.value.status == lsh.ERR_UNSUPPORTED
+    for zv in (10, 11):
+        with pytest.raises(lsh.LSHError) as e:
+            h.set_variants(1, 3, 1, zv)
+        assert e.value.status == lsh.ERR_UNSUPPORTED
     h.set_variants(0, 0, 2, 10)
+    h.set_variants(0, 0, 2, 11)  # z length 16: a 4-thread plan
+    h64 = lsh.Handle(torch.zeros((64, 32, 32), dtype=torch.uint8).cuda(), mods, physics=lsh.ELASTIC,
+                     green=lsh.FILTERED, precision=lsh.MIXED)
+    with pytest.raises(lsh.LSHError) as e:
+        h64.set_variants(0, 0, 2, 11)  # z length 64 has an 8-thread plan: no fused variant
+    assert e.value.status == lsh.ERR_UNSUPPORTED
 
 
 def test_radix3_grids_refuse_separate_passes():
