@@ -166,9 +166,9 @@ typedef struct lsh_tune_report {
                      each frequency's Gamma coefficients when it applies them; 10
                      (plane passes only) persistent kernel on tiles of 8 columns
                      brought in and written back by TMA, double-buffered, with the
-                     FFT and Gamma exchanges in the tile's buffer; 11 the same with
-                     the second FFT level and Gamma in one register phase (lengths
-                     16, 32, 48 and 96)                                             */
+                     FFT and Gamma exchanges in the tile's buffer; 11 the same on
+                     the plan N = R1 x 4 with the 4-point FFT level and Gamma in one
+                     register phase (z lengths up to 128)                           */
   float xf_ms[2]; /* measured time of one launch per candidate (-1: not available)   */
   float x_ms[4];
   float y_ms[2];

@@ -141,6 +141,41 @@ template <typename T, bool INV> struct Dft<T, 16, INV> {
   }
 };
 
+// 32 = 2 x 16: X[k] = E[k] + w32^k O[k], X[k + 16] = E[k] - w32^k O[k] with E, O
+// the 16-point DFTs of the even and odd samples (w32 = exp(-+2 i pi / 32)).
+template <typename T, bool INV> struct Dft<T, 32, INV> {
+  static __device__ __forceinline__ void run(C2<T>* a, const C2<T>* tw, int n) {
+    // cos(pi k / 16), k = 0..8 (sin(pi k / 16) = cos(pi (8 - k) / 16))
+    const T cs[9] = {(T)1.0,
+                     (T)0.98078528040323044912618223613424,
+                     (T)0.92387953251128675612818318939679,
+                     (T)0.83146961230254523707878837761791,
+                     (T)0.70710678118654752440084436210485,
+                     (T)0.55557023301960222474283081394853,
+                     (T)0.38268343236508977172845998403040,
+                     (T)0.19509032201612826784828486847702,
+                     (T)0.0};
+    C2<T> e[16], o[16];
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      e[j] = a[2 * j];
+      o[j] = a[2 * j + 1];
+    }
+    Dft<T, 16, INV>::run(e, tw, n);
+    Dft<T, 16, INV>::run(o, tw, n);
+    const T sg = INV ? (T)1 : (T)-1;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) {
+      C2<T> w;
+      if (k <= 8) w = mkc<T>(cs[k], sg * cs[8 - k]);
+      else w = mkc<T>(-cs[16 - k], sg * cs[k - 8]);
+      const C2<T> ow = k == 0 ? o[k] : cmul<T>(o[k], w);
+      a[k] = cadd<T>(e[k], ow);
+      a[k + 16] = csub<T>(e[k], ow);
+    }
+  }
+};
+
 // Direct DFT for the remaining small prime (7), from the twiddle table.
 template <typename T, bool INV> struct Dft<T, 7, INV> {
   static __device__ __forceinline__ void run(C2<T>* a, const C2<T>* tw, int n) {

@@ -65,8 +65,8 @@ template <typename T> struct OpArgs {
   int ztma;           // 0: register z pass; 1..5: the variant of launch_zgamma_tma; 6: register, 4 columns;
                       // 7: persistent register z pass with staged prefetch; 8: register, 16 columns;
                       // 9: register, coefficients loaded when used; 10: pipelined TMA tiles on the
-                      // ky-major spectrum (kernels_zpipe.cu); 11: the same with the level-b DFTs
-                      // and Gamma^h fused (P = 4 plans)
+                      // ky-major spectrum (kernels_zpipe.cu); 11: the same on the plan N = R1 x 4
+                      // with the 4-point DFTs and Gamma^h fused
   const CUtensorMap* tmy;
   const CUtensorMap* tmz;   // z boxes of 4 columns
   const CUtensorMap* tmz8;  // z boxes of 8 columns

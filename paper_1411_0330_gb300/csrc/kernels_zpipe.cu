@@ -35,15 +35,23 @@
 
 namespace lsh {
 
-// FUSED (P = 4 plans): one thread per (k1, column) takes the P-point DFTs of
-// all NC components, the Gamma^h product at its P frequencies k1 + R1 k2 and
-// the inverse P-point DFTs in registers; the exchange rows are then e + e / P.
+// FUSED: every length runs the plan N = R1 x 4 (P = 4); one thread per (k1,
+// column) takes the 4-point DFTs of all NC components, the Gamma^h product at
+// its 4 frequencies k1 + R1 k2 and the inverse 4-point DFTs in registers (the
+// (k1, column) pairs go round the block when there are more of them than
+// threads).  Its exchange needs no padding: element e sits in row
+// e ^ ((e >> 2) & 1), which splits the four rows of every warp access two and
+// two between the bank halves both when 4 threads t write k1 P + t and when 4
+// consecutive k1 read k1 P + u.
+template <int N, bool FUSED> struct ZPlan {
+  static constexpr int P = FUSED ? 4 : RegPlan<N>::P, R1 = FUSED ? N / 4 : RegPlan<N>::R1;
+};
 template <int NC, int N, bool FUSED = false> struct ZPipe {
   static constexpr int TZ = 8;                   // columns per tile
-  static constexpr int P = RegPlan<N>::P, R1 = RegPlan<N>::R1, Q = R1 / P;
+  static constexpr int P = ZPlan<N, FUSED>::P, R1 = ZPlan<N, FUSED>::R1, Q = R1 / P;
   static constexpr int THREADS = TZ * P * NC;
-  static constexpr int NX = FUSED ? N + N / P : N + N / R1;  // exchange rows per component
-  static constexpr bool FUSABLE = P == 4 && R1 * TZ <= THREADS;
+  static constexpr int NX = FUSED ? N : N + N / R1;  // exchange rows per component
+  static constexpr bool FUSABLE = R1 <= 32;      // register DFTs of up to 32 points
   static constexpr int BUF = NC * NX * TZ;       // complex values per buffer
   static constexpr uint32_t BOX_BYTES = (uint32_t)(sizeof(float2) * NC * N * TZ);
   static constexpr size_t SMEM = 2 * sizeof(float2) * BUF + sizeof(float2) * N + 128;
@@ -58,23 +66,25 @@ template <int Q> __device__ __forceinline__ int zp_grow(int kz) {
 }
 
 // The middle of the FUSED kernel: thread (k1, column li) reads element k1 P + u
-// (u < P) of every component's line from the exchange (row k1 (P + 1) + u),
+// (u < P) of every component's line from the exchange (row 4 k1 + (u ^ (k1 & 1))),
 // transforms over u, applies Gamma^h_k at kz = k1 + R1 k2 to the NC components
 // of each k2, transforms back and writes the same rows.  The coefficients of
 // the next k2 load while the current ones are applied.
 template <int NC, int N>
-__device__ __forceinline__ void zp_fused_middle(const OpArgs<float>& a, float2* B, bool nyq, int yp, int kx0) {
+__device__ __forceinline__ void zp_fused_item(const OpArgs<float>& a, float2* B, int item, bool nyq, int yp,
+                                              int kx0) {
   typedef ZPipe<NC, N, true> ZC;
   constexpr int TZ = ZC::TZ, P = ZC::P, R1 = ZC::R1, NX = ZC::NX;
-  if (threadIdx.x >= R1 * TZ) return;
-  const int li = threadIdx.x & (TZ - 1), k1 = threadIdx.x / TZ;
-  float2* const base = B + k1 * (P + 1) * TZ + li;
+  const int li = item & (TZ - 1), k1 = item / TZ, kb = k1 & 1;
+  // rows of even u one up for odd k1, rows of odd u one down
+  float2* const ev = B + (4 * k1 + kb) * TZ + li;
+  float2* const od = B + (4 * k1 - kb) * TZ + li;
   const int kx = nyq ? kx0 : kx0 + li, ypos = nyq ? yp + li : yp;
   float2 d[NC][P];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
 #pragma unroll
-    for (int u = 0; u < P; ++u) d[c][u] = base[(c * NX + u) * TZ];
+    for (int u = 0; u < P; ++u) d[c][u] = ((u & 1) ? od : ev)[(c * NX + u) * TZ];
     Dft<float, P, false>::run(d[c], nullptr, N);
   }
   if (a.onfly) {
@@ -111,7 +121,7 @@ __device__ __forceinline__ void zp_fused_middle(const OpArgs<float>& a, float2* 
   for (int c = 0; c < NC; ++c) {
     Dft<float, P, true>::run(d[c], nullptr, N);
 #pragma unroll
-    for (int u = 0; u < P; ++u) base[(c * NX + u) * TZ] = d[c][u];
+    for (int u = 0; u < P; ++u) ((u & 1) ? od : ev)[(c * NX + u) * TZ] = d[c][u];
   }
 }
 
@@ -186,9 +196,10 @@ __global__ void __launch_bounds__(ZPipe<NC, N, FUSED>::THREADS, ZPipe<NC, N, FUS
   const int i = threadIdx.x & (TZ - 1), t = (threadIdx.x / TZ) % P, comp = threadIdx.x / (TZ * P);
   // per-thread bases (complex offsets within a buffer)
   const int od = (comp * N + t) * TZ + i;             // dense: x[t + P j] at od + j P TZ
-  const int oa = (comp * NX + t) * TZ + i;            // exchange, element k1 P + t at row xrow(k1) + t
-  // exchange row offset of element k1 P + t (t < P): k1 P + k1 / Q, or k1 (P + 1) when FUSED
-  auto xrow = [](int k1) { return FUSED ? k1 * (P + 1) : k1 * P + k1 / Q; };
+  // exchange, element k1 P + t: row k1 P + k1 / Q + t, or (FUSED) 4 k1 + (t ^ (k1 & 1))
+  const int oa = (comp * NX + t) * TZ + i;
+  const int oa1 = (comp * NX + (FUSED ? (t ^ 1) : t)) * TZ + i;  // odd k1 (FUSED)
+  auto xa = [&](int k1) { return FUSED ? ((k1 & 1) ? oa1 : oa) + 4 * k1 * TZ : oa + (k1 * P + k1 / Q) * TZ; };
   const int ob = (comp * NX + t * (R1 + 1)) * TZ + i; // exchange, element (t Q + q) P + u
   // Gamma layout, frequency kz(m) = t Q + m / P + R1 (m % P): for even Q its row
   // is kz ^ (t & 1), i.e. one row up or down by the parity of m / P
@@ -219,10 +230,10 @@ __global__ void __launch_bounds__(ZPipe<NC, N, FUSED>::THREADS, ZPipe<NC, N, FUS
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmul<float>(v[k1], tw[t * k1]);
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) B[oa + xrow(k1) * TZ] = v[k1];
+    for (int k1 = 0; k1 < R1; ++k1) B[xa(k1)] = v[k1];
     __syncthreads();
     if constexpr (FUSED) {
-      zp_fused_middle<NC, N>(a, B, nyq, yp, kx0);
+      for (int item = threadIdx.x; item < R1 * TZ; item += THREADS) zp_fused_item<NC, N>(a, B, item, nyq, yp, kx0);
     } else {
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
@@ -305,7 +316,7 @@ __global__ void __launch_bounds__(ZPipe<NC, N, FUSED>::THREADS, ZPipe<NC, N, FUS
     }  // !FUSED
     __syncthreads();
 #pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1) v[k1] = B[oa + xrow(k1) * TZ];
+    for (int k1 = 0; k1 < R1; ++k1) v[k1] = B[xa(k1)];
 #pragma unroll
     for (int k1 = 1; k1 < R1; ++k1) v[k1] = cmulc<float>(v[k1], tw[t * k1]);
     Dft<float, R1, true>::run(v, tw, N);

@@ -68,9 +68,8 @@ def test_plane_apply_matches_oracle(shape, physics, green):
     x = np.random.default_rng(1).standard_normal(P.field_shape)
     yo = oracle.apply(P, x)
     for zv in (0, 6, 7, 8, 9, 10, 11):
-        if zv == 11 and (shape[0] not in (16, 32, 48, 96) or (physics == 0 and shape[0] * 2 > 3 * 32)):
-            # the fused z pass needs a z length with a 4-thread register plan and one
-            # thread per (k1, column): R1 8 <= 8 P c, i.e. z length <= 48 for 3 components
+        if zv == 11 and shape[0] > 128:
+            # the fused z pass runs the plan N = R1 x 4 with register DFTs of up to 32 points
             with pytest.raises(lsh.LSHError) as e:
                 h.set_variants(0, 0, 2, zv)
             assert e.value.status == lsh.ERR_UNSUPPORTED
@@ -95,7 +94,7 @@ def test_plane_passes_agree_with_separate_passes(shape):
 
 
 @pytest.mark.parametrize("n,green,nsys,zv", [(32, 1, 6, 10), (16, 0, 6, 10), (48, 1, 3, 10), (64, 1, 2, 10),
-                                             (32, 1, 6, 11), (16, 0, 4, 11), (48, 1, 3, 11)])
+                                             (32, 1, 6, 11), (16, 0, 4, 11), (48, 1, 3, 11), (64, 1, 6, 11)])
 def test_pipelined_z_pass_mixed_effective_matches_oracle(n, green, nsys, zv):
     """The TMA-fed z passes (variant 10, and 11 with the level-b DFTs and Gamma^h fused)
     inside the mixed solver: C* against the oracle on a seeded packing, with systems
@@ -120,11 +119,12 @@ def test_pipelined_z_pass_needs_the_plane_passes():
             h.set_variants(1, 3, 1, zv)
         assert e.value.status == lsh.ERR_UNSUPPORTED
     h.set_variants(0, 0, 2, 10)
-    h.set_variants(0, 0, 2, 11)  # z length 16: a 4-thread plan
-    h64 = lsh.Handle(torch.zeros((64, 32, 32), dtype=torch.uint8).cuda(), mods, physics=lsh.ELASTIC,
-                     green=lsh.FILTERED, precision=lsh.MIXED)
+    h.set_variants(0, 0, 2, 11)
+    h256 = lsh.Handle(torch.zeros((256, 16, 16), dtype=torch.uint8).cuda(), mods, physics=lsh.ELASTIC,
+                      green=lsh.FILTERED, precision=lsh.MIXED)
+    h256.set_variants(0, 0, 2, 10)
     with pytest.raises(lsh.LSHError) as e:
-        h64.set_variants(0, 0, 2, 11)  # z length 64 has an 8-thread plan: no fused variant
+        h256.set_variants(0, 0, 2, 11)  # z length 256 would need a 64-point register DFT
     assert e.value.status == lsh.ERR_UNSUPPORTED
 
 
