@@ -115,10 +115,12 @@ template <int N> __device__ __forceinline__ void plane_y_fwd(float2* PL, const f
     const int col = cl + rd * LPR;
     float2* cp = PL + col;
     float2 v[R1];
+    if (col == 0) {  // columns 0 and N/2 (real) as one complex column
 #pragma unroll
-    for (int j = 0; j < R1; ++j) {
-      const int y = t + P * j;
-      v[j] = col == 0 ? make_float2(PL[y * RS].x, PL[y * RS + N / 2].x) : cp[y * RS];
+      for (int j = 0; j < R1; ++j) v[j] = make_float2(PL[(t + P * j) * RS].x, PL[(t + P * j) * RS + N / 2].x);
+    } else {
+#pragma unroll
+      for (int j = 0; j < R1; ++j) v[j] = cp[(t + P * j) * RS];
     }
     __syncthreads();
     RL::template fwd_a_s<RS>(v, t, tw, cp);
@@ -157,15 +159,16 @@ template <int N> __device__ __forceinline__ void plane_y_inv(float2* PL, const f
     const int col = cl + rd * LPR;
     float2* cp = PL + col;
     float2 v[R1];
+    if (col == 0) {
 #pragma unroll
-    for (int m = 0; m < R1; ++m) {
-      const int f = RL::freq(t, m);
-      if (col == 0) {
+      for (int m = 0; m < R1; ++m) {
+        const int f = RL::freq(t, m);
         const float2 x0 = PL[f * RS], xn = PL[f * RS + N / 2];
         v[m] = make_float2(x0.x - xn.y, x0.y + xn.x);  // X0 + i XN
-      } else {
-        v[m] = cp[f * RS];
       }
+    } else {
+#pragma unroll
+      for (int m = 0; m < R1; ++m) v[m] = cp[RL::freq(t, m) * RS];
     }
     __syncthreads();
     RL::template inv_a_s<RS>(v, t, tw, cp);
@@ -303,7 +306,7 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyfwd(Op
       }
       return;
     }
-#pragma unroll 1
+#pragma unroll
     for (int it0 = 0; it0 < PC::IT; it0 += B) {
       float4 pc[B], xc[B];
 #pragma unroll
