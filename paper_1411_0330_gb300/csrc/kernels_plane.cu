@@ -40,10 +40,14 @@ namespace lsh {
 template <int N> struct PlaneCfg {
   typedef RegLine<float, N> RL;
   static constexpr int P = RL::P, R1 = RL::R1, Q = RL::Q;
-  // half-spectrum row stride: N/2 + 1 rounded up to 4 (mod 8), the handle's hs;
-  // two rows then start 8 complex values apart modulo 16 (the x-phase lines
-  // of a half-warp hit distinct banks)
-  static constexpr int RS = (N / 2 + 1 + 3) / 8 * 8 + 4;
+  // row stride of the plane in shared memory (complex values, even: 16-byte
+  // rows for the bulk copies), at least N/2 + 1.  A warp of the x phases holds
+  // 32 / P row pairs; their bases, 2 RS apart, must fall on distinct banks for
+  // the accesses along a line (stride 1 in t): RS = 4 (mod 8) for P = 8 (row
+  // pairs 8 complex values apart modulo 16), RS = 2 (mod 8) for P = 4 (4 apart).
+  // The global rows keep the handle's stride hs >= RS (32-byte rows for the z
+  // pass); a bulk copy moves the first RS values of a row.
+  static constexpr int RS = P >= 8 ? (N / 2 + 1 + 3) / 8 * 8 + 4 : (N / 2 + 6) / 8 * 8 + 2;
   static constexpr int LINES = N / 2;  // row pairs along x, packed columns along y
   static constexpr int TH = LINES * P < 256 ? LINES * P : 256;
   static constexpr int LPR = TH / P;   // lines per round
@@ -347,7 +351,7 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyfwd(Op
   __syncthreads();
   const long long slab = (long long)(s * a.c + comp) * N;
   for (int ky = threadIdx.x; ky < N; ky += TH) {
-    bulk_store_1d(a.H + ((slab + ky) * a.nz + z) * RS, PL + ky * RS, (uint32_t)(sizeof(float2) * RS));
+    bulk_store_1d(a.H + ((slab + ky) * a.nz + z) * a.hs, PL + ky * RS, (uint32_t)(sizeof(float2) * RS));
     a.nq[(long long)blockIdx.x * N + ky] = PL[ky * RS + N / 2];
   }
   bulk_commit();
@@ -383,7 +387,7 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyinv(Op
   }
   __syncthreads();
   for (int ky = threadIdx.x; ky < N; ky += TH)
-    bulk_load_1d(PL + ky * RS, a.H + ((slab + ky) * a.nz + z) * RS, (uint32_t)(sizeof(float2) * RS), &bar);
+    bulk_load_1d(PL + ky * RS, a.H + ((slab + ky) * a.nz + z) * a.hs, (uint32_t)(sizeof(float2) * RS), &bar);
   for (int u = threadIdx.x; u < N; u += TH) tw[u] = a.twx[u];
   const int ntab = a.nphase * a.c;
   for (int u = threadIdx.x; u < ntab; u += TH) mloc[u] = (a.scale && !a.frac) ? a.modtab[u] : a.mtab[u];
@@ -503,7 +507,7 @@ template <int N> void plane_attrs() {
 template <int N> bool plane_fwd_n(const OpArgs<float>& a, int mode, const float* in, float* x, const float* r,
                                   float* p, const SolverState* st, cudaStream_t s) {
   typedef PlaneCfg<N> PC;
-  if (a.hs != PC::RS) return false;
+  if (a.hs < PC::RS || (a.hs & 1) != 0) return false;
   const unsigned grid = (unsigned)((long long)a.S * a.c * a.nz);
   if (mode == 0) k_xyfwd<N, 0><<<grid, PC::TH, PC::SMEM, s>>>(a, in, x, r, p, st);
   else k_xyfwd<N, 1><<<grid, PC::TH, PC::SMEM, s>>>(a, in, x, r, p, st);
@@ -513,7 +517,7 @@ template <int N> bool plane_fwd_n(const OpArgs<float>& a, int mode, const float*
 template <int N> bool plane_inv_n(const OpArgs<float>& a, int mode, const float* xin, float* out, SolverState* st,
                                   double* partials, cudaStream_t s) {
   typedef PlaneCfg<N> PC;
-  if (a.hs != PC::RS) return false;
+  if (a.hs < PC::RS || (a.hs & 1) != 0) return false;
   const unsigned grid = (unsigned)((long long)a.S * a.c * a.nz);
   const size_t smem = plane_inv_smem<N>(a);
   if (mode == 0) {
