@@ -84,14 +84,18 @@ template <int N> __device__ __forceinline__ void plane_x_fwd(float2* PL, const f
 #pragma unroll
     for (int m = 0; m < R1; ++m) pair[RL::freq(t, m)] = v[m];
     __syncwarp();
+    // kx = t + P i lies in [P i, P (i + 1)): inside 0..N/2 for every t while
+    // P (i + 1) <= N/2, for t = 0 only at i = N / (2P), outside beyond; kx = 0
+    // pairs with itself
     float2 xa[NK], xb[NK];
 #pragma unroll
     for (int i = 0; i < NK; ++i) {
       const int kx = t + P * i;
       xa[i] = make_float2(0.f, 0.f);
       xb[i] = xa[i];
-      if (kx <= N / 2) {
-        const float2 z1 = pair[kx], z2 = pair[kx == 0 ? 0 : N - kx];
+      const bool in = P * (i + 1) <= N / 2 || (P * i <= N / 2 && kx <= N / 2);
+      if (in) {
+        const float2 z1 = pair[kx], z2 = pair[(i == 0 && t == 0) ? 0 : N - kx];
         xa[i] = make_float2(0.5f * (z1.x + z2.x), 0.5f * (z1.y - z2.y));
         xb[i] = make_float2(0.5f * (z1.y + z2.y), 0.5f * (z2.x - z1.x));
       }
@@ -100,7 +104,7 @@ template <int N> __device__ __forceinline__ void plane_x_fwd(float2* PL, const f
 #pragma unroll
     for (int i = 0; i < NK; ++i) {
       const int kx = t + P * i;
-      if (kx < RS) {
+      if (P * (i + 1) <= RS || kx < RS) {
         pair[kx] = xa[i];
         pair[RS + kx] = xb[i];
       }
@@ -204,17 +208,23 @@ template <int N> __device__ __forceinline__ void plane_x_inv(float2* PL, const f
   for (int rd = 0; rd < PC::ROUNDS; ++rd) {
     float2* pair = PL + 2 * (lr + rd * PC::LPR) * RS;
     float2 v[R1];
+    // frequency f = t Q + q + R1 u lies in [R1 u, R1 (u + 1)): below N/2 for u < P/2,
+    // read at N - f from u = P/2 on (f = N/2 included: X(N/2) of a row is real)
+    const float2* up = pair + t * Q;      // X(f) at up[q + R1 u]
+    const float2* dn = pair + N - t * Q;  // X(N - f) at dn[-(q + R1 u)]
 #pragma unroll
     for (int q = 0; q < Q; ++q)
 #pragma unroll
       for (int u = 0; u < P; ++u) {
-        const int f = t * Q + q + R1 * u;
-        const bool lo = f <= N / 2;
-        const int k = lo ? f : N - f;
-        const float sg = lo ? 1.f : -1.f;
-        const float2 xa = pair[k], xb = pair[RS + k];
+        const int c = q + R1 * u;
         // Z(f) = X_a(f) + i X_b(f), X(N - k) = conj X(k)
-        v[q * P + u] = make_float2(xa.x - sg * xb.y, sg * xa.y + xb.x);
+        if (u < P / 2) {
+          const float2 xa = up[c], xb = up[RS + c];
+          v[q * P + u] = make_float2(xa.x - xb.y, xa.y + xb.x);
+        } else {
+          const float2 xa = dn[-c], xb = dn[RS - c];
+          v[q * P + u] = make_float2(xa.x + xb.y, xb.x - xa.y);
+        }
       }
     __syncwarp();
     RL::inv_a_p(v, t, tw, pair);
