@@ -424,11 +424,12 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyinv(Op
   __syncthreads();
   plane_y_inv<N>(PL, tw);
   // the epilogue's p and phase loads go out in batches of B groups of four
-  // voxels, each batch in flight while the previous one is worked on
-  constexpr int B = PC::IT % 4 == 0 ? 4 : (PC::IT % 3 == 0 ? 3 : (PC::IT % 2 == 0 ? 2 : 1));
-  float4 xb[B];
-  uchar4 hb[B];
-  auto load_batch = [&](int it0) {
+  // voxels, each batch in flight while the previous one is worked on; two
+  // register sets take the batches in turn (no copies between them)
+  constexpr int B = PC::IT % 2 == 0 ? 2 : 1;
+  float4 xb0[B], xb1[B];
+  uchar4 hb0[B], hb1[B];
+  auto load_batch = [&](int it0, float4* xb, uchar4* hb) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int idx = threadIdx.x + (it0 + b) * TH;
@@ -438,24 +439,17 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyinv(Op
     }
   };
   plane_x_inv<N>(PL, tw);
-  load_batch(0);
+  load_batch(0, xb0, hb0);
   __syncthreads();
   Acc<float> acc;
   // two phases without a voxel field (the common case): both phases' M and
-  // activity in registers, selected per voxel instead of read from the tables
+  // activity in registers, selected per voxel instead of read from the tables;
+  // both active (A0 differs from both phases): no projection to apply
   const bool two = a.nphase <= 2 && !a.scale;
   const float m0 = mloc[comp], m1 = a.nphase > 1 ? mloc[a.c + comp] : m0;
   const bool act0 = aloc[0] != 0, act1 = a.nphase > 1 ? aloc[1] != 0 : act0;
-#pragma unroll 1
-  for (int it0 = 0; it0 < PC::IT; it0 += B) {
-    float4 xc[B];
-    uchar4 hc[B];
-#pragma unroll
-    for (int b = 0; b < B; ++b) {
-      xc[b] = xb[b];
-      hc[b] = hb[b];
-    }
-    if (it0 + B < PC::IT) load_batch(it0 + B);
+  const bool both = two && act0 && act1;
+  auto work = [&](int it0, const float4* xc, const uchar4* hc) {
 #pragma unroll
     for (int b = 0; b < B; ++b) {
       const int idx = threadIdx.x + (it0 + b) * TH;
@@ -467,7 +461,10 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyinv(Op
       const unsigned char ph[4] = {hc[b].x, hc[b].y, hc[b].z, hc[b].w};
       const float gv[4] = {g4.x, g4.y, g4.z, g4.w};
       float ov[4];
-      if (two) {
+      if (both) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ov[u] = fmaf(ph[u] != 0 ? m1 : m0, xq[u], gv[u]);
+      } else if (two) {
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const bool p1 = ph[u] != 0;
@@ -491,6 +488,14 @@ __global__ void __launch_bounds__(PlaneCfg<N>::TH, PlaneCfg<N>::MINB) k_xyinv(Op
       if (MODE == 4) acc.add(fmaf(xq[3], ov[3], fmaf(xq[2], ov[2], fmaf(xq[1], ov[1], xq[0] * ov[0]))));
       *reinterpret_cast<float4*>(out + g) = make_float4(ov[0], ov[1], ov[2], ov[3]);
     }
+  };
+#pragma unroll 1
+  for (int it0 = 0; it0 < PC::IT; it0 += 2 * B) {
+    if (it0 + B < PC::IT) load_batch(it0 + B, xb1, hb1);
+    work(it0, xb0, hb0);
+    if (it0 + B >= PC::IT) break;
+    if (it0 + 2 * B < PC::IT) load_batch(it0 + 2 * B, xb0, hb0);
+    work(it0 + B, xb1, hb1);
   }
   if (MODE == 4) {
     const double tot = block_reduce(acc);
