@@ -11,16 +11,25 @@
 // that two buffers per block leave room for a second block on the SM.  The
 // result leaves through one TMA store from the same buffer.
 //
+// Two variants.  The unfused one (variant 10) runs the register plans of
+// regfft.cuh; the c components of each frequency then meet for the Gamma^h
+// product in a layout of their own.  The fused one (variant 11) runs the plan
+// N = R1 x 4 and lets one thread per (k1, column) take the 4-point transforms
+// of all components, the product and the inverse 4-point transforms in
+// registers: two fewer exchanges and four fewer barriers per tile.
+//
 // Buffer layouts (a row is the 8 columns of one component at one position, 64
 // bytes; rows alternate between the two 64-byte halves of a 128-byte bank row):
 //   dense (the TMA box)          row c N + z
-//   transform exchange           row c NX + e + e / R1   (NX = N + N / R1)
-//   Gamma^h product              row c N + kz ^ ((kz / Q) & 1) for even Q = R1 / P,
+//   unfused: transform exchange  row c NX + e + e / R1   (NX = N + N / R1)
+//            Gamma^h product     row c N + kz ^ ((kz / Q) & 1) for even Q = R1 / P,
 //                                row c N + kz for odd Q
+//   fused: transform exchange    row c N + (e ^ ((e >> 2) & 1))
 // A warp holds the 8 columns of 4 consecutive line positions t of one
-// component; in each layout the four rows a warp touches split two and two
-// between the halves (no bank conflicts), and every offset is a compile-time
-// constant from one of a few per-thread bases.
+// component (in the fused product phase: of 4 consecutive k1); in each layout
+// the four rows a warp touches split two and two between the halves (no bank
+// conflicts), and every offset is a compile-time constant from one of a few
+// per-thread bases.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
