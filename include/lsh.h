@@ -233,7 +233,8 @@ lsh_status lsh_autotune(lsh_handle *h, lsh_tune_report *rep);
 
 /* Select the FP32 forward x / inverse x / y / z pass variants by hand (numbering of lsh_tune_report;
  * no counterpart in the paper: for tests and measurements).  y_variant 2
- * selects the plane passes (x variants ignored; z variant 0 or 6 to 11).
+ * selects the plane passes (x variants ignored; z variant 0 or 6 to 11; a handle
+ * of a plane grid starts on z variant 11 where that has a plan, else 0).
  * Returns LSH_ERR_UNSUPPORTED if a variant is not available for this problem
  * (FP64 handles accept only zeros). */
 lsh_status lsh_set_variants(lsh_handle *h, int xf_variant, int x_variant, int y_variant, int z_variant);

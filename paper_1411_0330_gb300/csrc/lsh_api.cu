@@ -1480,6 +1480,12 @@ lsh_status lsh_setup(const lsh_problem* prob, void* workspace, size_t bytes, voi
   if (d.plane) {
     plane_prepare();
     zpipe_prepare();
+    // the z pass of the plane passes without tuning: the fused TMA kernel where it
+    // has a plan (the autotuner's choice on every grid of the batched workload),
+    // else the register kernel
+    OpArgs<float> az = h->pf.a;
+    az.S = 0;
+    if (d.precision == LSH_MIXED && launch_zgamma_pipe(az, true, nullptr, 0)) h->pf.a.ztma = 11;
   }
   if (l.df) df_prepare();
   launch_gamma_table<double>(h->pd.a, d.dim, d.physics, d.green, d.ref_user, h->kofy, h->kofz, st,
