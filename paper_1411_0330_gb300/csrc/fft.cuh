@@ -196,11 +196,57 @@ template <typename T, bool INV> struct Dft<T, 7, INV> {
   }
 };
 
+// cos and sin of 2 pi m / 24 (multiples of 15 degrees) from the closed forms
+// cos 15 = (sqrt 6 + sqrt 2) / 4, sin 15 = (sqrt 6 - sqrt 2) / 4, cos 30 = sqrt 3 / 2,
+// cos 45 = sqrt 2 / 2; once the loops are unrolled m is a constant and these fold.
+__host__ __device__ constexpr double cos24(int m) {
+  constexpr double c15 = 0.96592582628906828674974319972889736763, s15 = 0.25881904510252076234889883762404832835;
+  constexpr double c30 = 0.86602540378443864676372317075293618347, c45 = 0.70710678118654752440084436210484903928;
+  switch (((m % 24) + 24) % 24) {
+    case 0: return 1.0;
+    case 1: return c15;
+    case 2: return c30;
+    case 3: return c45;
+    case 4: return 0.5;
+    case 5: return s15;
+    case 6: return 0.0;
+    case 7: return -s15;
+    case 8: return -0.5;
+    case 9: return -c45;
+    case 10: return -c30;
+    case 11: return -c15;
+    case 12: return -1.0;
+    case 13: return -c15;
+    case 14: return -c30;
+    case 15: return -c45;
+    case 16: return -0.5;
+    case 17: return -s15;
+    case 18: return 0.0;
+    case 19: return s15;
+    case 20: return 0.5;
+    case 21: return c45;
+    case 22: return c30;
+    default: return c15;
+  }
+}
+__host__ __device__ constexpr double sin24(int m) { return cos24(m - 6); }
+
 // Composite lengths R = A * B in registers (Cooley-Tukey with B-point outer
 // and A-point inner DFTs): x[B n1 + n2] -> X[k1 + A k2] =
 //   sum_n2 w_B^(n2 k2) [ w_R^(n2 k1) sum_n1 x[B n1 + n2] w_A^(n1 k1) ];
-// the twiddles w_R^m come from the line's table tw of length n (stride n / R).
+// the twiddles w_R^m are constants for R dividing 24 (the radix-3 lengths 6,
+// 12, 24), else they come from the line's table tw of length n (stride n / R).
 template <typename T, int A, int B, bool INV> struct DftAB {
+  static __device__ __forceinline__ C2<T> twiddle(const C2<T>& c, int m, const C2<T>* tw, int st) {
+    constexpr int R = A * B;
+    if constexpr (24 % R == 0) {
+      const int m24 = m * (24 / R);
+      const C2<T> w = mkc<T>((T)cos24(m24), (T)(INV ? sin24(m24) : -sin24(m24)));
+      return cmul<T>(c, w);
+    } else {
+      return INV ? cmulc<T>(c, tw[m * st]) : cmul<T>(c, tw[m * st]);
+    }
+  }
   static __device__ __forceinline__ void run(C2<T>* a, const C2<T>* tw, int n) {
     constexpr int R = A * B;
     const int st = n / R;
@@ -213,8 +259,7 @@ template <typename T, int A, int B, bool INV> struct DftAB {
       Dft<T, A, INV>::run(c, tw, n);
 #pragma unroll
       for (int k1 = 0; k1 < A; ++k1)
-        b[n2][k1] = (n2 == 0 || k1 == 0) ? c[k1]
-                                         : (INV ? cmulc<T>(c[k1], tw[n2 * k1 * st]) : cmul<T>(c[k1], tw[n2 * k1 * st]));
+        b[n2][k1] = (n2 == 0 || k1 == 0) ? c[k1] : twiddle(c[k1], n2 * k1, tw, st);
     }
 #pragma unroll
     for (int k1 = 0; k1 < A; ++k1) {
