@@ -225,8 +225,10 @@ lsh_status lsh_effective(lsh_handle *h, const lsh_solve_opts *opts, double *Asta
 /* Autotuner (no counterpart in the paper): times the candidate kernels of
  * the FP32 x passes (shared-memory stages or register FFT), y pass and z
  * pass (tile shapes, register-only or TMA-staged, one or two tile buffers) on the handle's own buffers at its full system count, and
- * keeps the fastest for the following calls.  Results do not change: the
- * candidates do the same arithmetic.  Overwrites the handle's spectrum buffer
+ * keeps the fastest for the following calls.  The candidates compute the same
+ * operator; results change at most at the rounding level of the FP32 passes
+ * (some take their sums in another order or on another FFT plan, e.g. z variant
+ * 11 on N = R1 x 4).  Overwrites the handle's spectrum buffer
  * (call it between solves, not inside one).  FP64 handles: no-op.  rep may be
  * NULL.  Synchronous. */
 lsh_status lsh_autotune(lsh_handle *h, lsh_tune_report *rep);
